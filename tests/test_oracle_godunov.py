@@ -1,0 +1,146 @@
+"""Pins of the oracle's Godunov scheme and two-shock Riemann solver (CPU only).
+
+- Riemann: equal states return themselves after one Newton iteration; where
+  both waves are shocks the two-shock solver is exact, so its star state must
+  equal the exact solution (tests/exact_riemann.py, written from Toro ch. 4);
+  supersonic states sample the upwind side.
+- Scheme: a uniform state is a fixed point (bitwise); mass, momentum and energy
+  are conserved to 1e-12 on periodic grids; with no perturbation all y-rows
+  stay identical and the y sweep is the identity (bitwise); the scheme commutes
+  with the reflection i -> N-1-i, u -> -u; the periodic Sod problem converges to
+  the exact solution (L1 error falls with N, star-region pressure within 1e-3
+  of the exact p* = 0.30313); no floors and no Newton non-convergence on the
+  Sod-like workloads.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1710_08774_gb300 import inputs as I
+from tests import exact_riemann as ER
+
+G = 1.4
+
+
+def test_riemann_equal_states():
+    for q in ([1.0, 0.3, -0.2, 1.0], [0.125, -0.7, 0.1, 0.1], [2.5, 0.0, 0.0, 3.0]):
+        s, it, nc, fh = oracle.riemann(q, q)
+        assert it == 1 and not nc and fh == 0
+        assert np.allclose(s, q, rtol=1e-14, atol=1e-15)
+
+
+@pytest.mark.parametrize("ul,ur", [(1.0, -0.5), (0.8, -1.2), (2.0, 0.5)])
+def test_riemann_two_shock_is_exact(ul, ur):
+    rl, pl, rr, pr = 1.0, 1.0, 0.8, 0.6
+    ps, us = ER.star(rl, ul, pl, rr, ur, pr)
+    assert ps > pl and ps > pr  # both waves are shocks
+    s, it, nc, _ = oracle.riemann([rl, ul, 0.1, pl], [rr, ur, -0.2, pr])
+    assert not nc
+    r_ex, u_ex, p_ex = ER.sample(0.0, rl, ul, pl, rr, ur, pr)
+    assert abs(s[3] - p_ex) <= 1e-9 * p_ex
+    assert abs(s[1] - u_ex) <= 1e-9 * max(1.0, abs(u_ex))
+    assert abs(s[0] - r_ex) <= 1e-9 * r_ex
+    assert s[2] == (0.1 if u_ex > 0 else -0.2)
+
+
+def test_riemann_supersonic_upwind():
+    # flow to the right faster than any wave: the face sees the left state
+    ql = [1.0, 5.0, 0.0, 1.0]; qr = [0.5, 5.0, 0.0, 0.4]
+    s, _, _, _ = oracle.riemann(ql, qr)
+    assert np.allclose(s, ql, rtol=1e-12)
+    ql = [1.0, -5.0, 0.0, 1.0]; qr = [0.5, -5.0, 0.0, 0.4]
+    s, _, _, _ = oracle.riemann(ql, qr)
+    assert np.allclose(s, qr, rtol=1e-12)
+
+
+def test_uniform_fixed_point_bitwise():
+    U = np.empty((4, 12, 16))
+    rho, u, v, p = 0.9, 0.3, -0.2, 0.7
+    U[0] = rho; U[1] = rho * u; U[2] = rho * v; U[3] = p / (G - 1) + 0.5 * rho * (u * u + v * v)
+    W, dts, st = oracle.godunov(U, 5)
+    assert np.array_equal(W, U)
+    assert st.floor_hits == 0 and st.newton_nonconv == 0
+
+
+def _ksum(x):
+    return math.fsum(np.asarray(x).ravel().tolist())
+
+
+def test_conservation_periodic():
+    U = I.sod_state(40, 28, seed=7)
+    W, _, st = oracle.godunov(U, 10)
+    for f in (0, 3):
+        t0, t1 = _ksum(U[f]), _ksum(W[f])
+        assert abs(t1 - t0) <= 1e-12 * abs(t0)
+    for f in (1, 2):
+        scale = _ksum(np.abs(U[f]))
+        assert abs(_ksum(W[f]) - _ksum(U[f])) <= 1e-12 * scale
+    assert st.floor_hits == 0 and st.newton_nonconv == 0
+
+
+def test_unperturbed_rows_identical_and_y_identity():
+    U = I.sod_state(32, 6, perturb=0.0)
+    W, _, _ = oracle.godunov(U, 6)
+    assert all(np.array_equal(W[:, 0], W[:, j]) for j in range(1, 6))
+    Wx, _, _ = oracle.godunov(U, 6, sweeps=1)
+    assert np.array_equal(W, Wx)
+    assert np.all(W[2] == 0.0)
+
+
+def test_reflection_symmetry():
+    U = I.sod_state(36, 20, seed=3)
+    M = U[:, :, ::-1].copy(); M[1] = -M[1]
+    W, dw, _ = oracle.godunov(U, 8)
+    Wm, dm, _ = oracle.godunov(M, 8)
+    Wm_back = Wm[:, :, ::-1].copy(); Wm_back[1] = -Wm_back[1]
+    for f in range(4):
+        scale = np.max(np.abs(W[f])) if f != 1 else np.max(np.abs(U[0]))
+        assert np.max(np.abs(Wm_back[f] - W[f])) <= 1e-12 * scale
+    assert np.allclose(dw, dm, rtol=1e-14)
+
+
+def _sod_exact(x, t):
+    # two non-interacting Riemann problems: high|low at x = 0.5, low|high at x = 0 (periodic)
+    out = np.empty((3, x.size))
+    for n, xx in enumerate(x):
+        if 0.25 <= xx <= 0.75:
+            out[:, n] = ER.sample((xx - 0.5) / t, 1.0, 0.0, 1.0, 0.125, 0.0, 0.1)
+        else:
+            xs = xx if xx < 0.5 else xx - 1.0
+            out[:, n] = ER.sample(xs / t, 0.125, 0.0, 0.1, 1.0, 0.0, 1.0)
+    return out
+
+
+def _run_sod(N, T=0.1):
+    nsteps = int(math.ceil(T / (0.4 / (2.2 * N))))
+    U = I.sod_state(N, 4, perturb=0.0)
+    W, _, st = oracle.godunov(U, nsteps, dt_fixed=T / nsteps)
+    assert st.floor_hits == 0 and st.newton_nonconv == 0
+    rho = W[0, 0]; u = W[1, 0] / rho
+    p = (G - 1) * (W[3, 0] - 0.5 * rho * u * u)
+    x = (np.arange(N) + 0.5) / N
+    return x, rho, u, p
+
+
+def test_sod_converges_to_exact():
+    errs = []
+    for N in (128, 256, 512):
+        x, rho, u, p = _run_sod(N)
+        ex = _sod_exact(x, 0.1)
+        errs.append(np.mean(np.abs(rho - ex[0])))
+        if N == 512:
+            # star region of the x = 0.5 problem lies between the contact
+            # (x = 0.5 + 0.0927) and the shock (x = 0.5 + 0.1752) at t = 0.1
+            # on the p side it extends left to the rarefaction tail (0.5 - 0.007)
+            band = (x > 0.52) & (x < 0.66)
+            assert np.max(np.abs(p[band] - 0.30313)) < 1e-3
+    assert errs[0] > errs[1] > errs[2]
+    order = math.log2(errs[0] / errs[2]) / 2
+    assert 0.6 <= order <= 1.2, (errs, order)
+
+
+def test_exact_star_pressure_sod():
+    ps, us = ER.star(1.0, 0.0, 1.0, 0.125, 0.0, 0.1)
+    assert abs(ps - 0.30313) < 1e-5 and abs(us - 0.92745) < 1e-5
