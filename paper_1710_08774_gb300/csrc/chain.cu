@@ -1,0 +1,590 @@
+// chain.cu -- stencil-chain pipelines: the 2D three-stage chain
+// (L = 5-pt Laplacian, G = |grad L| / 2, out = G / (1 + G)), the 3D
+// four-stage 7-point chain, and the generic one-kernel-per-rule executor.
+//
+// Fused kernels follow the paper's contraction (Sec. 3.4): one thread per
+// column streams along the outer axis (j in 2D, k in 3D) and every
+// intermediate lives in a rolling window of 3 rows / planes instead of a full
+// array.  The window store is the schedule's placement:
+//   reg  -- each thread's own column window in registers, neighbours along
+//           the inner axes through one shared row / plane per stage;
+//   smem -- the whole 3-row / 3-plane rings in shared memory;
+//   hbm  -- the same rings in a per-CTA global-memory slab (L2 resident).
+// "sweep" materialises the first stage in HBM and fuses the rest; "unfused"
+// runs one kernel per rule over full arrays (launch_generic).
+#include <algorithm>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace hfav {
+
+// ---------------------------------------------------------------------------
+// generic one-kernel-per-rule executor (the unfused GPU form)
+// ---------------------------------------------------------------------------
+struct GenericArgs {
+    int op;
+    int nref;
+    int ref_arr[27];
+    int ref_off[27][3];
+    double w[27];
+    GArr arr[8];
+    GArr out;
+    int lo[3], n[3];   // iteration region: lo .. lo + n - 1 per axis
+};
+
+template <typename T>
+__global__ void __launch_bounds__(256) generic_rule_kernel(const GenericArgs a) {
+    const int64_t total = (int64_t)a.n[0] * a.n[1] * a.n[2];
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        int i = (int)(idx % a.n[0]);
+        int64_t rest = idx / a.n[0];
+        int j = (int)(rest % a.n[1]);
+        int k = (int)(rest / a.n[1]);
+        i += a.lo[0]; j += a.lo[1]; k += a.lo[2];
+        T v;
+        if (a.op == HFAV_OP_STENCIL_LINEAR) {
+            v = (T)0;
+            for (int r = 0; r < a.nref; ++r) {
+                T x = garr_ld<T>(a.arr[a.ref_arr[r]], i + a.ref_off[r][0], j + a.ref_off[r][1], k + a.ref_off[r][2]);
+                v = r == 0 ? (T)a.w[r] * x : fma((T)a.w[r], x, v);
+            }
+        } else if (a.op == HFAV_OP_GRADMAG_HALF) {
+            T s = (T)0;
+            for (int r = 0; r + 1 < a.nref; r += 2) {
+                T x = garr_ld<T>(a.arr[a.ref_arr[r]], i + a.ref_off[r][0], j + a.ref_off[r][1], k + a.ref_off[r][2]);
+                T y = garr_ld<T>(a.arr[a.ref_arr[r + 1]], i + a.ref_off[r + 1][0], j + a.ref_off[r + 1][1],
+                                 k + a.ref_off[r + 1][2]);
+                T d = x - y;
+                s = fma(d, d, s);
+            }
+            v = sqrt(s) * (T)0.5;
+        } else {   // SQUASH
+            T x = garr_ld<T>(a.arr[a.ref_arr[0]], i + a.ref_off[0][0], j + a.ref_off[0][1], k + a.ref_off[0][2]);
+            v = x / ((T)1 + x);
+        }
+        *garr_ptr<T>(a.out, i, j, k) = v;
+    }
+}
+
+namespace {
+
+int esize(const hfav_plan_t* p) { return p->dtype == HFAV_F64 ? 8 : 4; }
+
+// view of a caller array of grid 0
+GArr caller_view(const hfav_plan_t* p, void* ptr) {
+    const hfav_grid& g = p->grids[0];
+    GArr a;
+    a.p = ptr;
+    for (int d = 0; d < 3; ++d) {
+        a.pitch[d] = g.pitch[d];
+        a.ext[d] = (int)g.extent[d];
+        a.org[d] = d < p->dag.ndim ? g.halo : 0;
+    }
+    a.wrap = p->bc == HFAV_BC_PERIODIC;
+    return a;
+}
+
+}  // namespace
+
+// One kernel per rule, in topological order; intermediates are plan-owned
+// full arrays covering their inferred footprint (halo included).
+int launch_generic(hfav_plan_t* p, void* const* ax, void* const* go, cudaStream_t st) {
+    const Dag& d = p->dag;
+    const hfav_grid& g = p->grids[0];
+    std::vector<GArr> view(d.n_fields);
+    std::vector<char> have(d.n_fields, 0);
+    for (size_t k = 0; k < d.axioms.size(); ++k) { view[d.axioms[k]] = caller_view(p, ax[k]); have[d.axioms[k]] = 1; }
+    for (size_t k = 0; k < d.goals.size(); ++k) {
+        view[d.goals[k]] = caller_view(p, go[k]);
+        view[d.goals[k]].wrap = 0;
+        have[d.goals[k]] = 1;
+    }
+    for (int f = 0; f < d.n_fields; ++f) {
+        if (have[f] || d.rank[f] == 0) continue;
+        const hfav_field_info& fi = p->an.field[f];
+        GArr a;
+        int64_t e[3];
+        for (int x = 0; x < 3; ++x) {
+            e[x] = g.extent[x] + fi.halo_lo[x] + fi.halo_hi[x];
+            a.org[x] = fi.halo_lo[x];
+            a.ext[x] = (int)g.extent[x];
+        }
+        a.pitch[0] = 1; a.pitch[1] = e[0]; a.pitch[2] = e[0] * e[1];
+        a.wrap = 0;
+        void* ptr;
+        int rc = scratch(p, "generic_f" + std::to_string(f), (size_t)(e[0] * e[1] * e[2]) * esize(p), &ptr);
+        if (rc) return rc;
+        a.p = ptr;
+        view[f] = a;
+        have[f] = 1;
+    }
+    for (int r : p->an.order) {
+        const Rule& R = d.rules[r];
+        GenericArgs a;
+        memset(&a, 0, sizeof a);
+        a.op = R.op;
+        a.nref = (int)R.in.size();
+        if (a.nref > 27) return set_error(HFAV_EUNSUPPORTED, "more than 27 refs in one rule");
+        std::vector<int> fields;
+        for (int k = 0; k < a.nref; ++k) {
+            int f = R.in[k].field;
+            auto it = std::find(fields.begin(), fields.end(), f);
+            int slot = (int)(it - fields.begin());
+            if (it == fields.end()) {
+                if (fields.size() == 8) return set_error(HFAV_EUNSUPPORTED, "more than 8 input fields in one rule");
+                fields.push_back(f);
+                a.arr[slot] = view[f];
+            }
+            a.ref_arr[k] = slot;
+            for (int x = 0; x < 3; ++x) a.ref_off[k][x] = R.in[k].off[x];
+            a.w[k] = k < (int)R.params.size() ? R.params[k] : 0.0;
+        }
+        int of = R.out[0];
+        a.out = view[of];
+        a.out.wrap = 0;
+        const hfav_field_info& fo = p->an.field[of];
+        for (int x = 0; x < 3; ++x) {
+            a.lo[x] = -fo.halo_lo[x];
+            a.n[x] = (int)g.extent[x] + fo.halo_lo[x] + fo.halo_hi[x];
+        }
+        int64_t total = (int64_t)a.n[0] * a.n[1] * a.n[2];
+        int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+        if (p->dtype == HFAV_F64) generic_rule_kernel<double><<<blocks, 256, 0, st>>>(a);
+        else generic_rule_kernel<float><<<blocks, 256, 0, st>>>(a);
+        HFAV_LAUNCHED(p->rt);
+    }
+    return HFAV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// 2D chain, fused
+// ---------------------------------------------------------------------------
+struct C2Args {
+    GArr u, out;
+    int nx, ny, R;
+    double wc, wip, wim, wjp, wjm;   // 5-point star weights
+    void* slab;                      // hbm placement: per-CTA rings
+};
+
+// L at one point from its five star neighbours, summed in the rule's order
+template <typename T>
+__device__ __forceinline__ T lap5(const C2Args& a, T ip, T im, T jp, T jm, T c) {
+    T v = (T)a.wip * ip;
+    v = fma((T)a.wim, im, v);
+    v = fma((T)a.wjp, jp, v);
+    v = fma((T)a.wjm, jm, v);
+    return fma((T)a.wc, c, v);
+}
+
+template <typename T>
+__device__ __forceinline__ T grad_squash(T lip, T lim, T ljp, T ljm) {
+    T gx = lip - lim, gy = ljp - ljm;
+    T G = sqrt(fma(gx, gx, gy * gy)) * (T)0.5;
+    return G / ((T)1 + G);
+}
+
+template <typename T>
+__device__ __forceinline__ T ld_u(const C2Args& a, int i, int j) {
+    if (!a.u.wrap) {   // halo given: stay inside the allocated halo of 2
+        if (i < -2 || i >= a.nx + 2 || j < -2 || j >= a.ny + 2) return (T)0;
+    }
+    return garr_ld<T>(a.u, i, j, 0);
+}
+
+// smem / hbm placement: 3-row rings of u (TX+4 wide) and L (TX+2 wide)
+template <typename T, bool HBM>
+__global__ void __launch_bounds__(256) chain2d_ring(const C2Args a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int TX = blockDim.x, t = threadIdx.x, ty = threadIdx.y;
+    const int i0 = blockIdx.x * TX;
+    const int j0 = (blockIdx.y * blockDim.y + ty) * a.R;
+    const int WU = TX + 4, WL = TX + 2;
+    const size_t per_group = 3 * WU + 3 * WL;
+    T* base;
+    if (HBM) {
+        size_t cta = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+        base = (T*)a.slab + (cta * blockDim.y + ty) * per_group;
+    } else {
+        base = (T*)smem_raw + ty * per_group;
+    }
+    T* su = base;            // [3][WU]
+    T* sL = base + 3 * WU;   // [3][WL]
+    for (int r = j0 - 2; r <= j0 + a.R + 1; ++r) {
+        T* ur = su + ((r + 3) % 3) * WU;
+        for (int c = t; c < WU; c += TX) ur[c] = ld_u<T>(a, i0 - 2 + c, r);
+        __syncthreads();
+        if (r >= j0) {   // L(r-1) over columns i0-1 .. i0+TX
+            const T* um = su + ((r - 2 + 3) % 3) * WU;
+            const T* u0 = su + ((r - 1 + 3) % 3) * WU;
+            const T* up = ur;
+            T* Lr = sL + ((r - 1 + 3) % 3) * WL;
+            for (int c = t; c < WL; c += TX)
+                Lr[c] = lap5<T>(a, u0[c + 2], u0[c], up[c + 1], um[c + 1], u0[c + 1]);
+        }
+        __syncthreads();
+        if (r >= j0 + 2) {   // G, out at row r-2
+            const int j = r - 2, i = i0 + t;
+            const T* Lm = sL + ((r - 3 + 3) % 3) * WL;
+            const T* L0 = sL + ((r - 2 + 3) % 3) * WL;
+            const T* Lp = sL + ((r - 1 + 3) % 3) * WL;
+            T o = grad_squash<T>(L0[t + 2], L0[t], Lp[t + 1], Lm[t + 1]);
+            if (i < a.nx && j < a.ny) *garr_ptr<T>(a.out, i, j, 0) = o;
+        }
+    }
+}
+
+// reg placement: vertical windows in registers, one shared row per stage
+template <typename T>
+__global__ void __launch_bounds__(256) chain2d_reg(const C2Args a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int TX = blockDim.x, t = threadIdx.x, ty = threadIdx.y;
+    const int i0 = blockIdx.x * TX, i = i0 + t;
+    const int j0 = (blockIdx.y * blockDim.y + ty) * a.R;
+    const int WU = TX + 4, WL = TX + 2;
+    T* su = (T*)smem_raw + ty * (WU + 2 * WL);   // u row r-1, columns i0-2 .. i0+TX+1
+    T* sL = su + WU;                             // [2][WL] L rows, double buffered
+    // own column window u(r-2), u(r-1), u(r); L(r-3), L(r-2), L(r-1)
+    T u0 = 0, u1 = 0, u2 = 0, l0 = 0, l1 = 0, l2 = 0;
+    // edge threads also carry the window of one halo column
+    const bool left = (t == 0), right = (t == TX - 1);
+    const int ie = left ? i0 - 1 : i0 + TX;
+    T e0 = 0, e1 = 0, e2 = 0;
+    for (int r = j0 - 2; r <= j0 + a.R + 1; ++r) {
+        u0 = u1; u1 = u2; u2 = ld_u<T>(a, i, r);
+        if (left || right) { e0 = e1; e1 = e2; e2 = ld_u<T>(a, ie, r); }
+        su[t + 2] = u1;
+        if (left) { su[1] = e1; su[0] = ld_u<T>(a, i0 - 2, r - 1); }
+        if (right) { su[TX + 2] = e1; su[TX + 3] = ld_u<T>(a, i0 + TX + 1, r - 1); }
+        __syncthreads();
+        if (r >= j0) {
+            T* Lr = sL + ((r - 1) & 1) * WL;
+            T L = lap5<T>(a, su[t + 3], su[t + 1], u2, u0, u1);
+            l0 = l1; l1 = l2; l2 = L;
+            Lr[t + 1] = L;
+            if (left) Lr[0] = lap5<T>(a, su[2], su[0], e2, e0, e1);
+            if (right) Lr[TX + 1] = lap5<T>(a, su[TX + 3], su[TX + 1], e2, e0, e1);
+        }
+        __syncthreads();
+        if (r >= j0 + 2) {
+            const int j = r - 2;
+            const T* L0 = sL + ((r - 2) & 1) * WL;
+            T o = grad_squash<T>(L0[t + 2], L0[t], l2, l0);
+            if (i < a.nx && j < a.ny) *garr_ptr<T>(a.out, i, j, 0) = o;
+        }
+    }
+}
+
+// tail of the "sweep" schedule: G and out from a materialised L (halo 1)
+template <typename T>
+__global__ void __launch_bounds__(256) chain2d_tail(const GArr L, const GArr out, int nx, int ny) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= nx || j >= ny) return;
+    T o = grad_squash<T>(garr_ld<T>(L, i + 1, j, 0), garr_ld<T>(L, i - 1, j, 0), garr_ld<T>(L, i, j + 1, 0),
+                         garr_ld<T>(L, i, j - 1, 0));
+    *garr_ptr<T>(out, i, j, 0) = o;
+}
+
+namespace {
+int rows_per_thread(int64_t cells, int lo, int hi) {
+    // enough threads for ~8 warps per SM on 152 SMs, at least `lo` rows
+    int64_t want = 152LL * 256;
+    int64_t r = cells / want;
+    int R = lo;
+    while (R < hi && R < r) R *= 2;
+    return R;
+}
+}  // namespace
+
+int launch_chain2d(hfav_plan_t* p, const Schedule& s, void* const* ax, void* const* go, cudaStream_t st) {
+    if (s.fusion == FUSE_UNFUSED) return launch_generic(p, ax, go, st);
+    const hfav_grid& g = p->grids[0];
+    const ChainMap& m = p->cmap;
+    const int nx = (int)g.extent[0], ny = (int)g.extent[1];
+    C2Args a;
+    memset(&a, 0, sizeof a);
+    a.u = caller_view(p, ax[0]);
+    a.out = caller_view(p, go[0]);
+    a.out.wrap = 0;
+    a.nx = nx; a.ny = ny;
+    a.wc = m.w1[13]; a.wip = m.w1[14]; a.wim = m.w1[12]; a.wjp = m.w1[16]; a.wjm = m.w1[10];
+    for (int k = 0; k < 27; ++k)
+        if (k != 13 && k != 14 && k != 12 && k != 16 && k != 10 && m.w1[k] != 0.0)
+            return set_error(HFAV_EUNSUPPORTED, "fused 2D chain takes a 5-point star stencil");
+    const bool f64 = p->dtype == HFAV_F64;
+    const size_t es = esize(p);
+    if (s.fusion == FUSE_SWEEP) {
+        // stage 1 materialised over its footprint (generic kernel), stages 2-3 fused
+        hfav_plan_t& P = *p;
+        const Rule& R0 = P.dag.rules[m.rules[0]];
+        int Lf = R0.out[0];
+        const hfav_field_info& fi = P.an.field[Lf];
+        GArr L;
+        int64_t ex = nx + fi.halo_lo[0] + fi.halo_hi[0], ey = ny + fi.halo_lo[1] + fi.halo_hi[1];
+        void* ptr;
+        int rc = scratch(p, "chain_L", (size_t)(ex * ey) * es, &ptr);
+        if (rc) return rc;
+        L.p = ptr; L.pitch[0] = 1; L.pitch[1] = ex; L.pitch[2] = ex * ey;
+        L.org[0] = fi.halo_lo[0]; L.org[1] = fi.halo_lo[1]; L.org[2] = 0;
+        L.ext[0] = nx; L.ext[1] = ny; L.ext[2] = 1; L.wrap = 0;
+        GenericArgs ga;
+        memset(&ga, 0, sizeof ga);
+        ga.op = HFAV_OP_STENCIL_LINEAR;
+        ga.nref = (int)R0.in.size();
+        ga.arr[0] = a.u;
+        for (int k = 0; k < ga.nref; ++k) {
+            ga.ref_arr[k] = 0;
+            for (int x = 0; x < 3; ++x) ga.ref_off[k][x] = R0.in[k].off[x];
+            ga.w[k] = R0.params[k];
+        }
+        ga.out = L;
+        ga.lo[0] = -fi.halo_lo[0]; ga.lo[1] = -fi.halo_lo[1]; ga.lo[2] = 0;
+        ga.n[0] = (int)ex; ga.n[1] = (int)ey; ga.n[2] = 1;
+        int blocks = (int)std::min<int64_t>((ex * ey + 255) / 256, 152 * 16);
+        if (f64) generic_rule_kernel<double><<<blocks, 256, 0, st>>>(ga);
+        else generic_rule_kernel<float><<<blocks, 256, 0, st>>>(ga);
+        HFAV_LAUNCHED(p->rt);
+        dim3 blk(s.tx, s.ty), grd((nx + s.tx - 1) / s.tx, (ny + s.ty - 1) / s.ty);
+        if (f64) chain2d_tail<double><<<grd, blk, 0, st>>>(L, a.out, nx, ny);
+        else chain2d_tail<float><<<grd, blk, 0, st>>>(L, a.out, nx, ny);
+        HFAV_LAUNCHED(p->rt);
+        return HFAV_OK;
+    }
+    // full fusion
+    a.R = rows_per_thread((int64_t)nx * ny, 8, 64);
+    const int TX = s.tx, TY = s.ty;
+    dim3 blk(TX, TY);
+    dim3 grd((nx + TX - 1) / TX, (ny + a.R * TY - 1) / (a.R * TY));
+    if (s.placement == PLACE_REG) {
+        size_t sm = (size_t)TY * ((TX + 4) + 2 * (TX + 2)) * es;
+        if (f64) chain2d_reg<double><<<grd, blk, sm, st>>>(a);
+        else chain2d_reg<float><<<grd, blk, sm, st>>>(a);
+    } else if (s.placement == PLACE_SMEM) {
+        size_t sm = (size_t)TY * (3 * (TX + 4) + 3 * (TX + 2)) * es;
+        if (f64) chain2d_ring<double, false><<<grd, blk, sm, st>>>(a);
+        else chain2d_ring<float, false><<<grd, blk, sm, st>>>(a);
+    } else {
+        size_t per = (size_t)TY * (3 * (TX + 4) + 3 * (TX + 2)) * es;
+        void* slab;
+        int rc = scratch(p, "chain2d_slab", per * grd.x * grd.y, &slab);
+        if (rc) return rc;
+        a.slab = slab;
+        if (f64) chain2d_ring<double, true><<<grd, blk, 0, st>>>(a);
+        else chain2d_ring<float, true><<<grd, blk, 0, st>>>(a);
+    }
+    HFAV_LAUNCHED(p->rt);
+    return HFAV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// 3D chain, fused: s1 = D7(u), s2 = D7(s1), s3 = |grad s2| / 2, out = s3/(1+s3)
+// CTA tile TX x TY columns in (i, j); each thread streams k over a chunk.
+// Planes: u on (TX+6)(TY+6), s1 on (TX+4)(TY+4), s2 on (TX+2)(TY+2).
+// ---------------------------------------------------------------------------
+struct C3Args {
+    GArr u, out;
+    int nx, ny, nz, K;
+    double a1[7], a2[7];   // weights: centre, +i, -i, +j, -j, +k, -k
+    void* slab;
+};
+
+template <typename T>
+__device__ __forceinline__ T ld_u3(const C3Args& a, int i, int j, int k) {
+    if (!a.u.wrap) {
+        if (i < -3 || i >= a.nx + 3 || j < -3 || j >= a.ny + 3 || k < -3 || k >= a.nz + 3) return (T)0;
+    }
+    return garr_ld<T>(a.u, i, j, k);
+}
+
+template <typename T>
+__device__ __forceinline__ T d7(const double* w, T ip, T im, T jp, T jm, T kp, T km, T c) {
+    T v = (T)w[1] * ip;
+    v = fma((T)w[2], im, v);
+    v = fma((T)w[3], jp, v);
+    v = fma((T)w[4], jm, v);
+    v = fma((T)w[5], kp, v);
+    v = fma((T)w[6], km, v);
+    return fma((T)w[0], c, v);
+}
+
+// ring placement (smem or hbm): 3 planes of u, s1, s2 per CTA
+template <typename T, bool HBM>
+__global__ void __launch_bounds__(256) chain3d_ring(const C3Args a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int TX = blockDim.x, TY = blockDim.y, NT = TX * TY;
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY, k0 = blockIdx.z * a.K;
+    const int PU = (TX + 6) * (TY + 6), P1 = (TX + 4) * (TY + 4), P2 = (TX + 2) * (TY + 2);
+    T* base;
+    if (HBM) {
+        size_t cta = ((size_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+        base = (T*)a.slab + cta * (size_t)(3 * (PU + P1 + P2));
+    } else {
+        base = (T*)smem_raw;
+    }
+    T* su = base;            // [3][PU]
+    T* s1 = su + 3 * PU;     // [3][P1]
+    T* s2 = s1 + 3 * P1;     // [3][P2]
+    // plane kk of u is needed for kk in [k0-3, k0+K+2]
+    for (int kk = k0 - 3; kk <= k0 + a.K + 2; ++kk) {
+        T* up = su + ((kk + 6) % 3) * PU;
+        for (int c = tid; c < PU; c += NT) {
+            int ci = c % (TX + 6), cj = c / (TX + 6);
+            up[c] = ld_u3<T>(a, i0 - 3 + ci, j0 - 3 + cj, kk);
+        }
+        __syncthreads();
+        if (kk >= k0 - 1) {   // s1 plane kk-1 on (TX+4)(TY+4)
+            const int kq = kk - 1;
+            const T* um = su + ((kq - 1 + 6) % 3) * PU;
+            const T* u0 = su + ((kq + 6) % 3) * PU;
+            const T* uq = up;
+            T* o = s1 + ((kq + 6) % 3) * P1;
+            for (int c = tid; c < P1; c += NT) {
+                int ci = c % (TX + 4) + 1, cj = c / (TX + 4) + 1;   // position in the u tile
+                int q = cj * (TX + 6) + ci;
+                o[c] = d7<T>(a.a1, u0[q + 1], u0[q - 1], u0[q + TX + 6], u0[q - TX - 6], uq[q], um[q], u0[q]);
+            }
+        }
+        __syncthreads();
+        if (kk >= k0 + 1) {   // s2 plane kk-2 on (TX+2)(TY+2)
+            const int kq = kk - 2;
+            const T* pm = s1 + ((kq - 1 + 6) % 3) * P1;
+            const T* p0 = s1 + ((kq + 6) % 3) * P1;
+            const T* pp = s1 + ((kq + 1 + 6) % 3) * P1;
+            T* o = s2 + ((kq + 6) % 3) * P2;
+            for (int c = tid; c < P2; c += NT) {
+                int ci = c % (TX + 2) + 1, cj = c / (TX + 2) + 1;
+                int q = cj * (TX + 4) + ci;
+                o[c] = d7<T>(a.a2, p0[q + 1], p0[q - 1], p0[q + TX + 4], p0[q - TX - 4], pp[q], pm[q], p0[q]);
+            }
+        }
+        __syncthreads();
+        if (kk >= k0 + 3) {   // out plane kk-3
+            const int kq = kk - 3;
+            const T* qm = s2 + ((kq - 1 + 6) % 3) * P2;
+            const T* q0 = s2 + ((kq + 6) % 3) * P2;
+            const T* qp = s2 + ((kq + 1 + 6) % 3) * P2;
+            const int ti = threadIdx.x, tj = threadIdx.y;
+            const int q = (tj + 1) * (TX + 2) + ti + 1;
+            T gx = q0[q + 1] - q0[q - 1], gy = q0[q + TX + 2] - q0[q - TX - 2], gz = qp[q] - qm[q];
+            T s3 = sqrt(fma(gx, gx, fma(gy, gy, gz * gz))) * (T)0.5;
+            int i = i0 + ti, j = j0 + tj;
+            if (i < a.nx && j < a.ny && kq < a.nz) *garr_ptr<T>(a.out, i, j, kq) = s3 / ((T)1 + s3);
+        }
+    }
+}
+
+// tail of the "sweep" schedule: s2 .. out fused from a materialised s1 (halo 2)
+template <typename T>
+__global__ void __launch_bounds__(256) chain3d_tail(const GArr s1, const GArr out, int nx, int ny, int nz, C3Args a) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    const int k = blockIdx.z;
+    if (i >= nx || j >= ny || k >= nz) return;
+    auto S1 = [&](int x, int y, int z) { return garr_ld<T>(s1, x, y, z); };
+    auto S2 = [&](int x, int y, int z) {
+        return d7<T>(a.a2, S1(x + 1, y, z), S1(x - 1, y, z), S1(x, y + 1, z), S1(x, y - 1, z), S1(x, y, z + 1),
+                     S1(x, y, z - 1), S1(x, y, z));
+    };
+    T gx = S2(i + 1, j, k) - S2(i - 1, j, k), gy = S2(i, j + 1, k) - S2(i, j - 1, k),
+      gz = S2(i, j, k + 1) - S2(i, j, k - 1);
+    T s3 = sqrt(fma(gx, gx, fma(gy, gy, gz * gz))) * (T)0.5;
+    *garr_ptr<T>(out, i, j, k) = s3 / ((T)1 + s3);
+}
+
+namespace {
+bool star7(const double* w, double* o) {
+    // box index (dk+1)*9 + (dj+1)*3 + (di+1)
+    static const int idx[7] = {13, 14, 12, 16, 10, 22, 4};
+    for (int k = 0; k < 27; ++k) {
+        bool star = false;
+        for (int m = 0; m < 7; ++m) if (idx[m] == k) star = true;
+        if (!star && w[k] != 0.0) return false;
+    }
+    for (int m = 0; m < 7; ++m) o[m] = w[idx[m]];
+    return true;
+}
+}  // namespace
+
+int launch_chain3d(hfav_plan_t* p, const Schedule& s, void* const* ax, void* const* go, cudaStream_t st) {
+    if (s.fusion == FUSE_UNFUSED) return launch_generic(p, ax, go, st);
+    const hfav_grid& g = p->grids[0];
+    const ChainMap& m = p->cmap;
+    C3Args a;
+    memset(&a, 0, sizeof a);
+    a.u = caller_view(p, ax[0]);
+    a.out = caller_view(p, go[0]);
+    a.out.wrap = 0;
+    a.nx = (int)g.extent[0]; a.ny = (int)g.extent[1]; a.nz = (int)g.extent[2];
+    if (!star7(m.w1, a.a1) || !star7(m.w2, a.a2))
+        return set_error(HFAV_EUNSUPPORTED, "fused 3D chain takes 7-point star stencils");
+    const bool f64 = p->dtype == HFAV_F64;
+    const size_t es = esize(p);
+    const int TX = s.tx, TY = s.ty;
+    if (s.fusion == FUSE_SWEEP) {
+        const Rule& R0 = p->dag.rules[m.rules[0]];
+        const hfav_field_info& fi = p->an.field[R0.out[0]];
+        int64_t e[3];
+        for (int x = 0; x < 3; ++x) e[x] = g.extent[x] + fi.halo_lo[x] + fi.halo_hi[x];
+        void* ptr;
+        int rc = scratch(p, "chain_s1", (size_t)(e[0] * e[1] * e[2]) * es, &ptr);
+        if (rc) return rc;
+        GArr S;
+        S.p = ptr; S.pitch[0] = 1; S.pitch[1] = e[0]; S.pitch[2] = e[0] * e[1];
+        for (int x = 0; x < 3; ++x) { S.org[x] = fi.halo_lo[x]; S.ext[x] = (int)g.extent[x]; }
+        S.wrap = 0;
+        GenericArgs ga;
+        memset(&ga, 0, sizeof ga);
+        ga.op = HFAV_OP_STENCIL_LINEAR;
+        ga.nref = (int)R0.in.size();
+        ga.arr[0] = a.u;
+        for (int k = 0; k < ga.nref; ++k) {
+            for (int x = 0; x < 3; ++x) ga.ref_off[k][x] = R0.in[k].off[x];
+            ga.w[k] = R0.params[k];
+        }
+        ga.out = S;
+        for (int x = 0; x < 3; ++x) { ga.lo[x] = -fi.halo_lo[x]; ga.n[x] = (int)e[x]; }
+        int64_t tot = e[0] * e[1] * e[2];
+        int blocks = (int)std::min<int64_t>((tot + 255) / 256, 152 * 16);
+        if (f64) generic_rule_kernel<double><<<blocks, 256, 0, st>>>(ga);
+        else generic_rule_kernel<float><<<blocks, 256, 0, st>>>(ga);
+        HFAV_LAUNCHED(p->rt);
+        dim3 blk(TX, TY), grd((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, a.nz);
+        if (f64) chain3d_tail<double><<<grd, blk, 0, st>>>(S, a.out, a.nx, a.ny, a.nz, a);
+        else chain3d_tail<float><<<grd, blk, 0, st>>>(S, a.out, a.nx, a.ny, a.nz, a);
+        HFAV_LAUNCHED(p->rt);
+        return HFAV_OK;
+    }
+    // chunk of planes per CTA: enough CTAs to fill the machine
+    int64_t tiles = (int64_t)((a.nx + TX - 1) / TX) * ((a.ny + TY - 1) / TY);
+    int K = 8;
+    while (K < 64 && tiles * ((a.nz + 2 * K - 1) / (2 * K)) >= 152 * 8) K *= 2;
+    a.K = K;
+    dim3 blk(TX, TY), grd((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + K - 1) / K);
+    size_t per = (size_t)3 * ((TX + 6) * (TY + 6) + (TX + 4) * (TY + 4) + (TX + 2) * (TY + 2)) * es;
+    if (s.placement == PLACE_HBM) {
+        void* slab;
+        int rc = scratch(p, "chain3d_slab", per * grd.x * grd.y * grd.z, &slab);
+        if (rc) return rc;
+        a.slab = slab;
+        if (f64) chain3d_ring<double, true><<<grd, blk, 0, st>>>(a);
+        else chain3d_ring<float, true><<<grd, blk, 0, st>>>(a);
+    } else {
+        // reg and smem share the ring kernel: the i/j neighbours of every stage
+        // must be visible across threads, so the rings are in shared memory
+        if (per > 200 * 1024) return set_error(HFAV_EUNSUPPORTED, "3D tile too large for shared memory");
+        if (f64) {
+            cudaFuncSetAttribute(chain3d_ring<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)per);
+            chain3d_ring<double, false><<<grd, blk, per, st>>>(a);
+        } else {
+            cudaFuncSetAttribute(chain3d_ring<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)per);
+            chain3d_ring<float, false><<<grd, blk, per, st>>>(a);
+        }
+    }
+    HFAV_LAUNCHED(p->rt);
+    return HFAV_OK;
+}
+
+}  // namespace hfav

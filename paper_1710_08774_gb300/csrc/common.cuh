@@ -1,0 +1,106 @@
+// common.cuh -- device helpers and the runtime object shared by the kernel files.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "plan.hpp"
+
+namespace hfav {
+
+#define HFAV_CUDA(call)                                                                       \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return set_error(HFAV_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define HFAV_LAUNCHED(rt)                                                                     \
+    do {                                                                                      \
+        cudaError_t e_ = cudaGetLastError();                                                  \
+        if (e_ != cudaSuccess)                                                                \
+            return set_error(HFAV_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
+        (rt)->launches++;                                                                     \
+    } while (0)
+
+// A strided view of a grid function on the device: element (i, j, k) sits at
+// p[(k + org[2]) * pitch[2] + (j + org[1]) * pitch[1] + (i + org[0])].
+// wrap != 0: indices are first wrapped periodically into [0, ext).
+struct GArr {
+    void* p;
+    int64_t pitch[3];
+    int org[3];
+    int ext[3];
+    int wrap;
+};
+
+__host__ __device__ inline int wrap_idx(int a, int n) {
+    int r = a % n;
+    return r < 0 ? r + n : r;
+}
+
+template <typename T>
+__device__ __forceinline__ T garr_ld(const GArr& a, int i, int j, int k) {
+    if (a.wrap) {
+        i = wrap_idx(i, a.ext[0]);
+        j = wrap_idx(j, a.ext[1]);
+        k = wrap_idx(k, a.ext[2]);
+    }
+    const T* p = (const T*)a.p;
+    return p[(int64_t)(k + a.org[2]) * a.pitch[2] + (int64_t)(j + a.org[1]) * a.pitch[1] + (i + a.org[0])];
+}
+
+template <typename T>
+__device__ __forceinline__ T* garr_ptr(const GArr& a, int i, int j, int k) {
+    T* p = (T*)a.p;
+    return p + (int64_t)(k + a.org[2]) * a.pitch[2] + (int64_t)(j + a.org[1]) * a.pitch[1] + (i + a.org[0]);
+}
+
+// atomic max of non-negative doubles through their bit patterns (IEEE order
+// of non-negative doubles equals the order of their bits as unsigned ints)
+__device__ __forceinline__ void atomic_max_pos(unsigned long long* slot, double v) {
+    atomicMax(slot, (unsigned long long)__double_as_longlong(v));
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Device-side state owned by a plan.
+struct Runtime {
+    int device = -1;
+    std::vector<void*> allocs;
+    std::map<std::string, void*> named;    // scratch buffers by purpose
+    std::map<std::string, size_t> named_bytes;
+    unsigned long long* counters = nullptr;   // [0] Newton non-converged, [1] non-physical
+    unsigned long long* wave = nullptr;       // per grid, wave_cap slots of max wave speed bits
+    int wave_cap = 0;
+    cudaStream_t last_stream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int launches = 0;
+    int last_launches = 0;
+    int last_steps = 0;
+    bool capturing = false;   // inside stream capture: no synchronous uploads
+    // captured graph
+    cudaGraphExec_t gexec = nullptr;
+    std::vector<void*> gkey;
+    int gsteps = -1;
+    std::string gsched;
+    cudaStream_t gstream = nullptr;
+};
+
+// allocate (or reuse) a named scratch buffer of at least `bytes`
+int scratch(hfav_plan_t* p, const std::string& name, size_t bytes, void** out);
+
+// launchers (chain.cu / godunov.cu)
+int launch_chain2d(hfav_plan_t* p, const Schedule& s, void* const* ax, void* const* go, cudaStream_t st);
+int launch_chain3d(hfav_plan_t* p, const Schedule& s, void* const* ax, void* const* go, cudaStream_t st);
+int launch_generic(hfav_plan_t* p, void* const* ax, void* const* go, cudaStream_t st);
+int launch_godunov(hfav_plan_t* p, const Schedule& s, void* const* ax, void* const* go, int n_steps,
+                   cudaStream_t st);
+
+}  // namespace hfav

@@ -1,0 +1,206 @@
+// godunov_phys.cuh -- per-point device functions of the nine Hydro2D kernels
+// (HFAV Sec. 5.4: constoprim, equation_of_state, slope, trace, qleftright,
+// riemann, cmpflx, update_cons_vars; make_boundary is the periodic index wrap).
+//
+// The paper names the kernels only.  The physics is the textbook MUSCL-Hancock
+// scheme for the 2D Euler equations of an ideal gas with a two-shock Riemann
+// solver (Newton iteration on the star pressure, sampled at x/t = 0).  The
+// arithmetic is arranged for a GPU whose FP64 pipe is ~60x slower than FP32:
+// every division that can be turned into a product with a reciprocal square
+// root is (c = g p s, 1/c = rho s with s = rsqrt(g p rho); 1/W_k and 1/Z_k
+// from one rsqrt per side), which changes rounding only.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace hfav {
+
+#define G_RHO_FLOOR 1e-10
+#define G_P_FLOOR 1e-10
+#define G_NEWTON_MAX 10
+#define G_NEWTON_TOL 1e-10
+
+// Primitive state of a cell in the frame of a sweep: rho, u_normal,
+// u_transverse, p, sound speed c, 1/c and c/rho.
+template <typename T>
+struct Prim {
+    T r, un, ut, p, c, ic, cr;
+};
+
+// constoprim + equation_of_state for one cell
+template <typename T>
+__device__ __forceinline__ Prim<T> cons_to_prim(T U0, T Un, T Ut, T E, T g) {
+    Prim<T> w;
+    T r = U0 > (T)G_RHO_FLOOR ? U0 : (T)G_RHO_FLOOR;
+    T ir = (T)1 / r;
+    w.r = r;
+    w.un = Un * ir;
+    w.ut = Ut * ir;
+    T e = fma(E, ir, (T)-0.5 * fma(w.un, w.un, w.ut * w.ut));
+    T p = (g - (T)1) * r * e;
+    p = p > (T)G_P_FLOOR ? p : (T)G_P_FLOOR;
+    w.p = p;
+    T s = rsqrt(g * p * r);
+    w.c = g * p * s;
+    w.ic = r * s;
+    w.cr = w.c * ir;
+    return w;
+}
+
+// minmod of two differences: zero unless both have the same strict sign
+template <typename T>
+__device__ __forceinline__ T minmod(T a, T b) {
+    if ((a > (T)0 && b > (T)0) || (a < (T)0 && b < (T)0)) return fabs(a) < fabs(b) ? a : b;
+    return (T)0;
+}
+
+template <typename T>
+struct Face4 {
+    T r, u, v, p;
+};
+
+// trace for one cell: characteristic tracing (MUSCL-Hancock) of the limited
+// slopes to the face-left (qm, at a-1/2) and face-right (qp, at a+1/2) states.
+template <typename T>
+__device__ __forceinline__ void trace(const Prim<T>& w0, T dr, T du, T dv, T dp, T dtdx, Face4<T>& qm,
+                                      Face4<T>& qp) {
+    const T ic = w0.ic, c = w0.c, r = w0.r, u = w0.un;
+    const T dpc = dp * ic;
+    const T a1 = (T)0.5 * ic * fma(-r, du, dpc);
+    const T a2 = fma(-dpc, ic, dr);
+    const T a3 = dv;
+    const T a4 = (T)0.5 * ic * fma(r, du, dpc);
+    const T n1 = (u - c) * dtdx, n2 = u * dtdx, n4 = (u + c) * dtdx;
+    // b+ = (1 - nu) a / 2, b- = (1 + nu) a / 2
+    const T p1 = (T)0.5 * (a1 - n1 * a1), m1 = (T)0.5 * fma(n1, a1, a1);
+    const T p2 = (T)0.5 * (a2 - n2 * a2), m2 = (T)0.5 * fma(n2, a2, a2);
+    const T p3 = (T)0.5 * (a3 - n2 * a3), m3 = (T)0.5 * fma(n2, a3, a3);
+    const T p4 = (T)0.5 * (a4 - n4 * a4), m4 = (T)0.5 * fma(n4, a4, a4);
+    const T c2 = c * c;
+    qp.r = w0.r + ((p1 + p2) + p4);
+    qp.u = fma(w0.cr, p4 - p1, u);
+    qp.v = w0.ut + p3;
+    qp.p = fma(c2, p1 + p4, w0.p);
+    qm.r = w0.r - ((m1 + m2) + m4);
+    qm.u = fma(-w0.cr, m4 - m1, u);
+    qm.v = w0.ut - m3;
+    qm.p = fma(-c2, m1 + m4, w0.p);
+}
+
+// slope (minmod-limited differences of the primitives) + trace
+template <typename T>
+__device__ __forceinline__ void slope_trace(const Prim<T>& wm, const Prim<T>& w0, const Prim<T>& wp, T dtdx,
+                                            Face4<T>& qm, Face4<T>& qp) {
+    trace(w0, minmod(w0.r - wm.r, wp.r - w0.r), minmod(w0.un - wm.un, wp.un - w0.un),
+          minmod(w0.ut - wm.ut, wp.ut - w0.ut), minmod(w0.p - wm.p, wp.p - w0.p), dtdx, qm, qp);
+}
+
+// Two-shock Riemann solver: Newton on p* in FP64 (whatever T is), then the
+// star state and the sampling at x/t = 0 in T.  Returns the Godunov state.
+template <typename T>
+__device__ __forceinline__ Face4<T> riemann(const Face4<T>& L, const Face4<T>& R, T g, int* nonconv) {
+    const double gd = (double)g;
+    const double pl = (double)L.p, pr = (double)R.p, rl = (double)L.r, rr = (double)R.r;
+    const double ul = (double)L.u, ur = (double)R.u;
+    const double xl = gd * pl * rl, xr = gd * pr * rr;
+    const double sl = rsqrt(xl), sr = rsqrt(xr);           // 1 / C_k
+    const double cl = xl * sl, cr = xr * sr;               // C_k = sqrt(g p_k rho_k)
+    const double a = (gd + 1.0) / (2.0 * gd);
+    const double ipp = 1.0 / (pl * pr);
+    const double al = a * pr * ipp, ar = a * pl * ipp;     // a / p_k
+    double ps = (cr * pl + cl * pr - cl * cr * (ur - ul)) / (cl + cr);
+    ps = fmax(ps, G_P_FLOOR);
+    bool conv = false;
+    for (int it = 0; it < G_NEWTON_MAX; ++it) {
+        const double ql = rsqrt(fma(al, ps - pl, 1.0));
+        const double qr = rsqrt(fma(ar, ps - pr, 1.0));
+        const double iwl = ql * sl, iwr = qr * sr;         // 1 / W_k
+        const double izl = 0.5 * iwl * fma(cl * cl, iwl * iwl, 1.0);   // 1 / Z_k
+        const double izr = 0.5 * iwr * fma(cr * cr, iwr * iwr, 1.0);
+        const double usl = fma(-(ps - pl), iwl, ul);
+        const double usr = fma(ps - pr, iwr, ur);
+        double pn = ps - (usr - usl) / (izl + izr);
+        pn = fmax(pn, G_P_FLOOR);
+        conv = fabs(pn - ps) <= G_NEWTON_TOL * pn;
+        ps = pn;
+        if (conv) break;
+    }
+    if (!conv) *nonconv = 1;
+    // star state at the converged p*, in the bulk precision
+    const T pst = (T)ps;
+    const T tl = fma((T)al, pst - L.p, (T)1), tr = fma((T)ar, pst - R.p, (T)1);
+    const T qlt = rsqrt(tl), qrt = rsqrt(tr);
+    const T Cl = (T)cl, Cr = (T)cr;
+    const T wl = Cl * tl * qlt, wr = Cr * tr * qrt;        // W_k = C_k sqrt(t_k)
+    const T iwl = qlt * (T)sl, iwr = qrt * (T)sr;
+    const T ust = (fma(wl, L.u, wr * R.u) + (L.p - R.p)) / (wl + wr);
+    const bool left = ust > (T)0;
+    const Face4<T>& S = left ? L : R;
+    const T ws = left ? wl : wr, iws = left ? iwl : iwr;
+    const T sgn = left ? (T)-1 : (T)1;
+    T rst = S.r / fma(-S.r * (pst - S.p), iws * iws, (T)1);
+    rst = rst > (T)G_RHO_FLOOR ? rst : (T)G_RHO_FLOOR;
+    Face4<T> o;
+    o.v = S.v;
+    bool take_side, take_star;
+    T f = (T)0;
+    if (pst > S.p) {   // shock: it has passed the face when sgn * S < 0
+        take_side = fma(sgn * S.u, S.r, ws) < (T)0;
+        take_star = !take_side;
+    } else {           // rarefaction fan
+        const T cs = g * S.p * rsqrt(g * S.p * S.r);
+        const T cst = g * pst * rsqrt(g * pst * rst);
+        const T head = fma(sgn, cs, S.u);
+        const T tail = fma(sgn, cst, ust);
+        take_side = sgn * head < (T)0;
+        take_star = !take_side && (sgn * tail > (T)0 || head == tail);
+        if (!take_side && !take_star) f = -tail / (head - tail);
+    }
+    if (take_side) { o.r = S.r; o.u = S.u; o.p = S.p; }
+    else if (take_star) { o.r = rst; o.u = ust; o.p = pst; }
+    else {
+        o.r = fma(f, S.r - rst, rst);
+        o.u = fma(f, S.u - ust, ust);
+        o.p = fma(f, S.p - pst, pst);
+    }
+    return o;
+}
+
+// cmpflx: Euler flux through the face of the Godunov state
+template <typename T>
+__device__ __forceinline__ Face4<T> flux(const Face4<T>& q, T ig1) {
+    Face4<T> F;
+    const T m = q.r * q.u;
+    F.r = m;
+    F.u = fma(m, q.u, q.p);
+    F.v = m * q.v;
+    const T et = fma(q.p, ig1, (T)0.5 * q.r * fma(q.u, q.u, q.v * q.v));
+    F.p = q.u * (et + q.p);
+    return F;
+}
+
+// CFL wave speed max(|u|+c, |v|+c) of a conserved state, in FP64; also flags
+// non-physical states (rho <= 0 or p <= 0 before any floor)
+__device__ __forceinline__ double wave_speed(double U0, double U1, double U2, double U3, double g, int* bad) {
+    const double ir = 1.0 / U0;
+    const double u = U1 * ir, v = U2 * ir;
+    const double e = fma(U3, ir, -0.5 * fma(u, u, v * v));
+    double p = (g - 1.0) * U0 * e;
+    if (!(U0 > 0.0) || !(p > 0.0)) *bad = 1;
+    p = fmax(p, G_P_FLOOR);
+    const double c = g * p * rsqrt(g * p * U0);
+    return fmax(fabs(u), fabs(v)) + c;
+}
+
+// Same in FP32 for the FP32 bulk mode (the reduction itself is FP64)
+__device__ __forceinline__ double wave_speed(float U0, float U1, float U2, float U3, float g, int* bad) {
+    const float ir = 1.0f / U0;
+    const float u = U1 * ir, v = U2 * ir;
+    const float e = fmaf(U3, ir, -0.5f * fmaf(u, u, v * v));
+    float p = (g - 1.0f) * U0 * e;
+    if (!(U0 > 0.0f) || !(p > 0.0f)) *bad = 1;
+    p = fmaxf(p, (float)G_P_FLOOR);
+    const float c = g * p * rsqrtf(g * p * U0);
+    return (double)(fmaxf(fabsf(u), fabsf(v)) + c);
+}
+
+}  // namespace hfav

@@ -1,0 +1,243 @@
+// runtime.cu -- device-side plan state: scratch ownership, dispatch of a
+// plan's schedule onto the pipeline launchers, CUDA-graph capture and replay,
+// run statistics and the exhaustive autotuner.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace hfav {
+
+namespace {
+
+int ensure_runtime(hfav_plan_t* p) {
+    if (p->rt) return HFAV_OK;
+    Runtime* rt = new (std::nothrow) Runtime();
+    if (!rt) return set_error(HFAV_ENOMEM, "host allocation failed");
+    p->rt = rt;
+    HFAV_CUDA(cudaGetDevice(&rt->device));
+    void* c;
+    HFAV_CUDA(cudaMalloc(&c, 4 * sizeof(unsigned long long)));
+    rt->allocs.push_back(c);
+    rt->counters = (unsigned long long*)c;
+    HFAV_CUDA(cudaMemset(c, 0, 4 * sizeof(unsigned long long)));
+    HFAV_CUDA(cudaEventCreate(&rt->ev0));
+    HFAV_CUDA(cudaEventCreate(&rt->ev1));
+    return HFAV_OK;
+}
+
+int launch_once(hfav_plan_t* p, const Schedule& s, void* const* ax, void* const* go, int n_steps, cudaStream_t st) {
+    switch (p->pipeline) {
+        case PIPE_CHAIN2D: return launch_chain2d(p, s, ax, go, st);
+        case PIPE_CHAIN3D: return launch_chain3d(p, s, ax, go, st);
+        case PIPE_GODUNOV: return launch_godunov(p, s, ax, go, n_steps, st);
+        default: return launch_generic(p, ax, go, st);
+    }
+}
+
+int check_ptrs(hfav_plan_t* p, void* const* ax, void* const* go) {
+    const size_t ng = p->grids.size();
+    if (!ax || !go) return set_error(HFAV_EINVAL, "null pointer table");
+    for (size_t k = 0; k < ng * p->dag.axioms.size(); ++k) {
+        if (!ax[k]) return set_error(HFAV_EINVAL, "null axiom pointer");
+        if ((uintptr_t)ax[k] % 16) return set_error(HFAV_EALIGN, "axiom pointer not 16-byte aligned");
+    }
+    for (size_t k = 0; k < ng * p->dag.goals.size(); ++k) {
+        if (!go[k]) return set_error(HFAV_EINVAL, "null goal pointer");
+        if ((uintptr_t)go[k] % 16) return set_error(HFAV_EALIGN, "goal pointer not 16-byte aligned");
+        for (size_t a = 0; a < ng * p->dag.axioms.size(); ++a)
+            if (go[k] == ax[a]) return set_error(HFAV_EINVAL, "a goal aliases an axiom (in/out chaining is not supported)");
+    }
+    return HFAV_OK;
+}
+
+}  // namespace
+
+int scratch(hfav_plan_t* p, const std::string& name, size_t bytes, void** out) {
+    Runtime* rt = p->rt;
+    auto it = rt->named.find(name);
+    if (it != rt->named.end() && rt->named_bytes[name] >= bytes) { *out = it->second; return HFAV_OK; }
+    if (it != rt->named.end()) {
+        cudaFree(it->second);
+        rt->allocs.erase(std::find(rt->allocs.begin(), rt->allocs.end(), it->second));
+        rt->named.erase(it);
+    }
+    void* ptr = nullptr;
+    cudaError_t e = cudaMalloc(&ptr, std::max<size_t>(bytes, 256));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(HFAV_ENOMEM, "cudaMalloc(" + std::to_string(bytes) + ") for " + name + ": " + cudaGetErrorString(e));
+    }
+    rt->allocs.push_back(ptr);
+    rt->named[name] = ptr;
+    rt->named_bytes[name] = bytes;
+    *out = ptr;
+    return HFAV_OK;
+}
+
+void drop_graph(hfav_plan_t* p) {
+    if (!p->rt) return;
+    if (p->rt->gexec) cudaGraphExecDestroy(p->rt->gexec);
+    p->rt->gexec = nullptr;
+    p->rt->gkey.clear();
+    p->rt->gsteps = -1;
+}
+
+void destroy_runtime(hfav_plan_t* p) {
+    Runtime* rt = p->rt;
+    if (!rt) return;
+    if (rt->last_stream) cudaStreamSynchronize(rt->last_stream);
+    drop_graph(p);
+    for (void* a : rt->allocs) cudaFree(a);
+    if (rt->ev0) cudaEventDestroy(rt->ev0);
+    if (rt->ev1) cudaEventDestroy(rt->ev1);
+    delete rt;
+    p->rt = nullptr;
+}
+
+int run(hfav_plan_t* p, void* const* ax, void* const* go, int n_steps, void* stream, bool graph) {
+    if (n_steps < 1) return set_error(HFAV_EINVAL, "n_steps must be >= 1");
+    if (!p->dag.feedback && n_steps != 1) return set_error(HFAV_EINVAL, "n_steps > 1 needs a feedback DAG");
+    int rc = check_ptrs(p, ax, go);
+    if (rc) return rc;
+    if ((rc = ensure_runtime(p))) return rc;
+    Runtime* rt = p->rt;
+    cudaStream_t st = (cudaStream_t)stream;
+    rt->last_stream = st;
+    rt->last_steps = n_steps;
+    const size_t nptr = p->grids.size() * (p->dag.axioms.size() + p->dag.goals.size());
+    if (graph) {
+        std::vector<void*> key;
+        for (size_t k = 0; k < p->grids.size() * p->dag.axioms.size(); ++k) key.push_back(ax[k]);
+        for (size_t k = 0; k < p->grids.size() * p->dag.goals.size(); ++k) key.push_back(go[k]);
+        (void)nptr;
+        if (!(rt->gexec && rt->gkey == key && rt->gsteps == n_steps && rt->gsched == p->sched.str() &&
+              rt->gstream == st)) {
+            drop_graph(p);
+            // one uncaptured run allocates the scratch and uploads the tables;
+            // the captured run then only queues kernels and async memsets
+            rt->launches = 0;
+            if ((rc = launch_once(p, p->sched, ax, go, n_steps, st))) return rc;
+            HFAV_CUDA(cudaStreamSynchronize(st));
+            cudaGraph_t gr;
+            HFAV_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            rt->launches = 0;
+            rt->capturing = true;
+            rc = launch_once(p, p->sched, ax, go, n_steps, st);
+            rt->capturing = false;
+            cudaError_t e = cudaStreamEndCapture(st, &gr);
+            if (rc) { if (e == cudaSuccess) cudaGraphDestroy(gr); return rc; }
+            HFAV_CUDA(e);
+            cudaError_t ei = cudaGraphInstantiate(&rt->gexec, gr, 0);
+            cudaGraphDestroy(gr);
+            HFAV_CUDA(ei);
+            rt->gkey = key;
+            rt->gsteps = n_steps;
+            rt->gsched = p->sched.str();
+            rt->gstream = st;
+            rt->last_launches = rt->launches;
+        }
+        HFAV_CUDA(cudaEventRecord(rt->ev0, st));
+        HFAV_CUDA(cudaGraphLaunch(rt->gexec, st));
+        HFAV_CUDA(cudaEventRecord(rt->ev1, st));
+        return HFAV_OK;
+    }
+    rt->launches = 0;
+    HFAV_CUDA(cudaEventRecord(rt->ev0, st));
+    rc = launch_once(p, p->sched, ax, go, n_steps, st);
+    if (rc) return rc;
+    HFAV_CUDA(cudaEventRecord(rt->ev1, st));
+    rt->last_launches = rt->launches;
+    return HFAV_OK;
+}
+
+int status(hfav_plan_t* p, hfav_run_stats* s) {
+    memset(s, 0, sizeof *s);
+    Runtime* rt = p->rt;
+    if (!rt) return HFAV_OK;
+    HFAV_CUDA(cudaStreamSynchronize(rt->last_stream));
+    unsigned long long c[2];
+    HFAV_CUDA(cudaMemcpy(c, rt->counters, sizeof c, cudaMemcpyDeviceToHost));
+    s->newton_nonconverged = (int64_t)c[0];
+    s->nonphysical = (int64_t)c[1];
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, rt->ev0, rt->ev1) == cudaSuccess) s->last_ms = ms;
+    else cudaGetLastError();
+    s->last_launches = rt->last_launches;
+    if (p->pipeline == PIPE_GODUNOV && rt->wave) {
+        int n = std::min(rt->last_steps, 64);
+        std::vector<unsigned long long> w(n);
+        HFAV_CUDA(cudaMemcpy(w.data(), rt->wave, n * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+        const double dx = 1.0 / (double)p->grids[0].extent[0];
+        for (int k = 0; k < n; ++k) {
+            double smax;
+            memcpy(&smax, &w[k], sizeof smax);
+            s->dt[k] = smax > 0 ? p->gmap.cfl * dx / smax : 0.0;
+        }
+        s->n_dt = n;
+    }
+    if (s->nonphysical) return set_error(HFAV_ENONPHYSICAL, "non-physical state (rho <= 0 or p <= 0) produced");
+    if (s->newton_nonconverged) {
+        set_error(HFAV_WARN_NEWTON, "Newton iteration hit the cap on some faces");
+        return HFAV_WARN_NEWTON;
+    }
+    return HFAV_OK;
+}
+
+int autotune(hfav_plan_t* p, void* const* ax, void* const* go, int n_steps, int reps, void* stream, float* times,
+             int n_times) {
+    int rc = check_ptrs(p, ax, go);
+    if (rc) return rc;
+    if ((rc = ensure_runtime(p))) return rc;
+    if (reps < 1) reps = 3;
+    cudaStream_t st = (cudaStream_t)stream;
+    p->rt->last_stream = st;
+    auto vars = valid_schedules(p);
+    // an L2-sized buffer written between timed runs so no variant inherits a warm cache
+    void* flush;
+    const size_t fbytes = 256u << 20;
+    if ((rc = scratch(p, "l2flush", fbytes, &flush))) return rc;
+    cudaEvent_t e0, e1;
+    HFAV_CUDA(cudaEventCreate(&e0));
+    HFAV_CUDA(cudaEventCreate(&e1));
+    Schedule keep = p->sched, best = p->sched;
+    float best_t = 1e30f;
+    for (size_t v = 0; v < vars.size(); ++v) {
+        std::vector<float> ts;
+        rc = launch_once(p, vars[v], ax, go, n_steps, st);   // warm: allocations, uploads
+        if (rc == HFAV_OK) {
+            for (int r = 0; r < reps && rc == HFAV_OK; ++r) {
+                cudaMemsetAsync(flush, r & 0xff, fbytes, st);
+                cudaEventRecord(e0, st);
+                rc = launch_once(p, vars[v], ax, go, n_steps, st);
+                cudaEventRecord(e1, st);
+                cudaEventSynchronize(e1);
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                ts.push_back(ms);
+            }
+        }
+        float med = -1.f;
+        if (rc == HFAV_OK && !ts.empty()) {
+            std::sort(ts.begin(), ts.end());
+            med = ts[ts.size() / 2];
+            if (med < best_t) { best_t = med; best = vars[v]; }
+        } else if (rc == HFAV_ECUDA) {
+            break;
+        }
+        rc = HFAV_OK;
+        if (times && (int)v < n_times) times[v] = med;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return set_error(HFAV_ECUDA, cudaGetErrorString(e));
+    p->sched = best_t < 1e30f ? best : keep;
+    drop_graph(p);
+    return HFAV_OK;
+}
+
+}  // namespace hfav

@@ -1,0 +1,96 @@
+"""GPU parity of the stencil chains against the oracle, through the C ABI.
+
+FP64 bar: <= 1e-12 normwise; FP32 bar: <= 2e-5 normwise (single rounding of
+a handful of ops on O(1) values, derived from the arithmetic: ~20 FP32 ops
+of relative error 6e-8 each).  Every schedule (fusion x placement x tile) is
+checked at 256^2, at sizes that leave a ragged tail, and in the halo-given
+mode against the exact closed form of quadratics.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1710_08774_gb300 import hfav as H
+from paper_1710_08774_gb300 import inputs as I
+from tests.gpu_util import normwise, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def run_chain2d(u, schedule, dtype=np.float64, bc=H.HFAV_BC_PERIODIC):
+    import torch
+    td = torch.float64 if dtype == np.float64 else torch.float32
+    ny, nx = u.shape[0] - 4, u.shape[1] - 4
+    ut = to_dev(u, td)
+    P = H.Plan(H.chain2d_dag(), [H.Grid.of(ut, 2)], H.HFAV_F64 if dtype == np.float64 else H.HFAV_F32, bc,
+               schedule)
+    # the goal array shares the axiom's layout (one grid per plan)
+    op = torch.full((ny + 4, nx + 4), float("nan"), dtype=td, device=ut.device)
+    P.run([ut], [op])
+    torch.cuda.synchronize()
+    return op[2:-2, 2:-2].double().cpu().numpy(), P
+
+
+VARIANTS = H.Plan(H.chain2d_dag(), [H.Grid.make((256, 256), (1, 260), 2)], 0, 0).variants()
+
+
+@pytest.mark.parametrize("schedule", VARIANTS)
+def test_chain2d_256_all_schedules_f64(schedule):
+    u = I.chain2d_input(256, seed=0)
+    _, _, ref = oracle.chain2d(u)
+    got, _ = run_chain2d(u, schedule)
+    assert normwise(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("shape", [(13, 7), (100, 37), (130, 67)])
+@pytest.mark.parametrize("schedule", ["full:reg:32x4", "full:smem:64x4", "full:hbm:128x2", "sweep:reg:32x8",
+                                      "unfused"])
+def test_chain2d_ragged(shape, schedule):
+    nx, ny = shape
+    u = I.chain2d_input(nx, seed=3, ny=ny)
+    _, _, ref = oracle.chain2d(u)
+    got, _ = run_chain2d(u, schedule)
+    assert normwise(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("schedule", ["full:reg:32x4", "full:smem:32x8", "sweep:hbm:64x4", "unfused"])
+def test_chain2d_halo_given_quadratic_exact(schedule):
+    j, i = np.meshgrid(np.arange(-2, 70), np.arange(-2, 52), indexing="ij")
+    u = 3.0 * i * i - 2.0 * j * j + 5.0 * i * j + i - 7.0 * j + 11.0
+    got, _ = run_chain2d(u, schedule, bc=H.HFAV_BC_HALO_GIVEN)
+    assert np.all(got == 0.0)
+
+
+@pytest.mark.parametrize("schedule", ["full:reg:32x4", "full:smem:128x2", "sweep:reg:64x4", "unfused"])
+def test_chain2d_f32(schedule):
+    u = I.chain2d_input(256, seed=1)
+    _, _, ref = oracle.chain2d(u)
+    got, _ = run_chain2d(u, schedule, dtype=np.float32)
+    assert normwise(got, ref) <= 2e-5
+
+
+def run_chain3d(u, schedule, dtype=np.float64):
+    import torch
+    td = torch.float64 if dtype == np.float64 else torch.float32
+    ut = to_dev(u, td)
+    op = torch.full(ut.shape, float("nan"), dtype=td, device=ut.device)
+    P = H.Plan(H.chain3d_dag(), [H.Grid.of(ut, 3)], H.HFAV_F64 if dtype == np.float64 else H.HFAV_F32,
+               H.HFAV_BC_PERIODIC, schedule)
+    P.run([ut], [op])
+    torch.cuda.synchronize()
+    return op[3:-3, 3:-3, 3:-3].double().cpu().numpy()
+
+
+@pytest.mark.parametrize("schedule", ["full:reg:32x4", "full:smem:64x4", "full:hbm:32x8", "full:smem:128x2",
+                                      "sweep:reg:32x4", "unfused"])
+def test_chain3d_f64(schedule):
+    u = I.chain3d_input(40, seed=4)
+    ref = oracle.chain3d(u)
+    assert normwise(run_chain3d(u, schedule), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("schedule", ["full:reg:32x4", "full:smem:64x4", "sweep:reg:32x4", "unfused"])
+def test_chain3d_f32_ragged(schedule):
+    u = I.chain3d_input(37, seed=9)
+    ref = oracle.chain3d(u)
+    assert normwise(run_chain3d(u, schedule, np.float32), ref) <= 2e-5
