@@ -278,6 +278,15 @@ int hfav_autotune(hfav_plan_t* plan, void* const* axiom_ptrs, void* const* goal_
 /* Valid schedule strings of the plan, '\n'-separated; returns the count. */
 int hfav_plan_variants(const hfav_plan_t* plan, char* buf, size_t n);
 
+/* Per-kernel timing: when enabled, every later hfav_run records a CUDA event
+ * after each kernel launch (not inside a captured graph).  hfav_kernel_times
+ * synchronises on the last event and writes, per distinct kernel of the last
+ * run, its name ('\n'-separated into names), total device time (ms, the time
+ * between the events that bracket each launch on the stream) and launch
+ * count.  Returns the number of kernels. */
+int hfav_plan_timing(hfav_plan_t* plan, int enable);
+int hfav_kernel_times(hfav_plan_t* plan, char* names, size_t n_names, double* ms, int* counts, int max_kernels);
+
 void hfav_free(hfav_plan_t* plan);
 
 const char* hfav_last_error(void);

@@ -205,6 +205,29 @@ int hfav_autotune(hfav_plan_t* p, void* const* ax, void* const* go, int n_steps,
     return autotune(p, ax, go, n_steps, reps, stream, times, n_times);
 }
 
+int hfav_plan_timing(hfav_plan_t* p, int enable) {
+    if (!p || p->analysis_only) return set_error(HFAV_EINVAL, "not an executable plan");
+    return set_timing(p, enable);
+}
+
+int hfav_kernel_times(hfav_plan_t* p, char* names, size_t n_names, double* ms, int* counts, int max_kernels) {
+    if (!p || !names || !ms || !counts || max_kernels < 1) return set_error(HFAV_EINVAL, "bad argument");
+    std::vector<std::string> nm;
+    std::vector<double> t;
+    std::vector<int> c;
+    int rc = kernel_times(p, &nm, &t, &c);
+    if (rc) return rc;
+    std::string all;
+    int k = 0;
+    for (; k < (int)nm.size() && k < max_kernels; ++k) {
+        all += nm[k] + "\n";
+        ms[k] = t[k];
+        counts[k] = c[k];
+    }
+    rc = copy_out(all, names, n_names);
+    return rc ? rc : k;
+}
+
 void hfav_free(hfav_plan_t* p) {
     if (!p) return;
     destroy_runtime(p);

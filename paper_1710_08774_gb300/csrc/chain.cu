@@ -153,7 +153,7 @@ int launch_generic(hfav_plan_t* p, void* const* ax, void* const* go, cudaStream_
         int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
         if (p->dtype == HFAV_F64) generic_rule_kernel<double><<<blocks, 256, 0, st>>>(a);
         else generic_rule_kernel<float><<<blocks, 256, 0, st>>>(a);
-        HFAV_LAUNCHED(p->rt);
+        HFAV_LAUNCHED(p->rt, "generic_rule_kernel", st);
     }
     return HFAV_OK;
 }
@@ -345,11 +345,11 @@ int launch_chain2d(hfav_plan_t* p, const Schedule& s, void* const* ax, void* con
         int blocks = (int)std::min<int64_t>((ex * ey + 255) / 256, 152 * 16);
         if (f64) generic_rule_kernel<double><<<blocks, 256, 0, st>>>(ga);
         else generic_rule_kernel<float><<<blocks, 256, 0, st>>>(ga);
-        HFAV_LAUNCHED(p->rt);
+        HFAV_LAUNCHED(p->rt, "generic_rule_kernel", st);
         dim3 blk(s.tx, s.ty), grd((nx + s.tx - 1) / s.tx, (ny + s.ty - 1) / s.ty);
         if (f64) chain2d_tail<double><<<grd, blk, 0, st>>>(L, a.out, nx, ny);
         else chain2d_tail<float><<<grd, blk, 0, st>>>(L, a.out, nx, ny);
-        HFAV_LAUNCHED(p->rt);
+        HFAV_LAUNCHED(p->rt, "chain2d_tail", st);
         return HFAV_OK;
     }
     // full fusion
@@ -374,7 +374,7 @@ int launch_chain2d(hfav_plan_t* p, const Schedule& s, void* const* ax, void* con
         if (f64) chain2d_ring<double, true><<<grd, blk, 0, st>>>(a);
         else chain2d_ring<float, true><<<grd, blk, 0, st>>>(a);
     }
-    HFAV_LAUNCHED(p->rt);
+    HFAV_LAUNCHED(p->rt, "chain2d_fused", st);
     return HFAV_OK;
 }
 
@@ -550,11 +550,11 @@ int launch_chain3d(hfav_plan_t* p, const Schedule& s, void* const* ax, void* con
         int blocks = (int)std::min<int64_t>((tot + 255) / 256, 152 * 16);
         if (f64) generic_rule_kernel<double><<<blocks, 256, 0, st>>>(ga);
         else generic_rule_kernel<float><<<blocks, 256, 0, st>>>(ga);
-        HFAV_LAUNCHED(p->rt);
+        HFAV_LAUNCHED(p->rt, "generic_rule_kernel", st);
         dim3 blk(TX, TY), grd((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, a.nz);
         if (f64) chain3d_tail<double><<<grd, blk, 0, st>>>(S, a.out, a.nx, a.ny, a.nz, a);
         else chain3d_tail<float><<<grd, blk, 0, st>>>(S, a.out, a.nx, a.ny, a.nz, a);
-        HFAV_LAUNCHED(p->rt);
+        HFAV_LAUNCHED(p->rt, "chain3d_tail", st);
         return HFAV_OK;
     }
     // chunk of planes per CTA: enough CTAs to fill the machine
@@ -583,7 +583,7 @@ int launch_chain3d(hfav_plan_t* p, const Schedule& s, void* const* ax, void* con
             chain3d_ring<float, false><<<grd, blk, per, st>>>(a);
         }
     }
-    HFAV_LAUNCHED(p->rt);
+    HFAV_LAUNCHED(p->rt, "chain3d_fused", st);
     return HFAV_OK;
 }
 

@@ -18,12 +18,15 @@ namespace hfav {
             return set_error(HFAV_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
-#define HFAV_LAUNCHED(rt)                                                                     \
+// after every kernel launch: check it, count it and, when per-kernel timing
+// is on, record an event so consecutive events bracket each kernel
+#define HFAV_LAUNCHED(rt, name, st)                                                           \
     do {                                                                                      \
         cudaError_t e_ = cudaGetLastError();                                                  \
         if (e_ != cudaSuccess)                                                                \
             return set_error(HFAV_ECUDA, std::string("kernel launch: ") + cudaGetErrorString(e_)); \
         (rt)->launches++;                                                                     \
+        if ((rt)->timing && !(rt)->capturing) kt_mark((rt), (name), (st));                    \
     } while (0)
 
 // A strided view of a grid function on the device: element (i, j, k) sits at
@@ -85,13 +88,23 @@ struct Runtime {
     int last_launches = 0;
     int last_steps = 0;
     bool capturing = false;   // inside stream capture: no synchronous uploads
+    // per-kernel timing (events recorded after each launch of a plain run)
+    bool timing = false;
+    std::vector<cudaEvent_t> kpool;
+    std::vector<std::string> kname;   // name of the kernel ending at event k (k >= 1)
+    size_t kused = 0;
     // captured graph
     cudaGraphExec_t gexec = nullptr;
     std::vector<void*> gkey;
     int gsteps = -1;
     std::string gsched;
     cudaStream_t gstream = nullptr;
+    cudaStream_t own = nullptr;          // capture stream when the caller passes the legacy stream
+    cudaEvent_t join0 = nullptr, join1 = nullptr;
 };
+
+// record the next timing event (event 0 is recorded at the start of a run)
+void kt_mark(Runtime* rt, const char* name, cudaStream_t st);
 
 // allocate (or reuse) a named scratch buffer of at least `bytes`
 int scratch(hfav_plan_t* p, const std::string& name, size_t bytes, void** out);

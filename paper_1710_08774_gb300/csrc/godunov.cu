@@ -887,7 +887,7 @@ static int run_godunov_t(hfav_plan_t* p, const Schedule& s, void* const* ax, voi
     {
         dim3 grd(std::max(1, std::min(64, (int)(xit.size() / 4 + 1))), ng);
         gcfl_reduce<T><<<grd, 256, 0, st>>>(tabs + t0, ng, 0, gm.gamma, rt->counters, 0);
-        HFAV_LAUNCHED(rt);
+        HFAV_LAUNCHED(rt, "gcfl_reduce", st);
     }
     if (s.fusion == FUSE_UNFUSED) {
         if (ng != 1) return set_error(HFAV_EUNSUPPORTED, "unfused form runs one grid");
@@ -915,26 +915,26 @@ static int run_godunov_t(hfav_plan_t* p, const Schedule& s, void* const* ax, voi
             const GGrid<T>* ty_ = tabs + steps[step].y;   // x-swept -> state(step+1)
             if (step > 0) {   // CFL as its own nest over the state entering the step
                 gcfl_reduce<T><<<dim3(64, 1), 256, 0, st>>>(tx_, 1, step, gm.gamma, rt->counters, 0);
-                HFAV_LAUNCHED(rt);
+                HFAV_LAUNCHED(rt, "gcfl_reduce", st);
             }
             for (int dir = 0; dir < 2; ++dir) {
                 const GGrid<T>* G = dir == 0 ? tx_ : ty_;
                 GGrid<T> Gh = host[dir == 0 ? steps[step].x : steps[step].y];
-                u_make_boundary<T><<<blocks, 256, 0, st>>>(Gh, A); HFAV_LAUNCHED(rt);
-                u_constoprim<T><<<blocks, 256, 0, st>>>(A, dir); HFAV_LAUNCHED(rt);
-                u_eos<T><<<blocks, 256, 0, st>>>(A, dir, g); HFAV_LAUNCHED(rt);
-                u_slope<T><<<blocks, 256, 0, st>>>(A, dir); HFAV_LAUNCHED(rt);
-                u_trace<T><<<blocks, 256, 0, st>>>(A, dir, G, step, gm.cfl); HFAV_LAUNCHED(rt);
-                u_qleftright<T><<<blocks, 256, 0, st>>>(A, dir); HFAV_LAUNCHED(rt);
-                u_riemann<T><<<blocks, 256, 0, st>>>(A, dir, g, rt->counters); HFAV_LAUNCHED(rt);
-                u_cmpflx<T><<<blocks, 256, 0, st>>>(A, dir, ig1); HFAV_LAUNCHED(rt);
-                u_update<T><<<blocks, 256, 0, st>>>(A, dir, G, step, gm.cfl); HFAV_LAUNCHED(rt);
+                u_make_boundary<T><<<blocks, 256, 0, st>>>(Gh, A); HFAV_LAUNCHED(rt, "u_make_boundary", st);
+                u_constoprim<T><<<blocks, 256, 0, st>>>(A, dir); HFAV_LAUNCHED(rt, "u_constoprim", st);
+                u_eos<T><<<blocks, 256, 0, st>>>(A, dir, g); HFAV_LAUNCHED(rt, "u_eos", st);
+                u_slope<T><<<blocks, 256, 0, st>>>(A, dir); HFAV_LAUNCHED(rt, "u_slope", st);
+                u_trace<T><<<blocks, 256, 0, st>>>(A, dir, G, step, gm.cfl); HFAV_LAUNCHED(rt, "u_trace", st);
+                u_qleftright<T><<<blocks, 256, 0, st>>>(A, dir); HFAV_LAUNCHED(rt, "u_qleftright", st);
+                u_riemann<T><<<blocks, 256, 0, st>>>(A, dir, g, rt->counters); HFAV_LAUNCHED(rt, "u_riemann", st);
+                u_cmpflx<T><<<blocks, 256, 0, st>>>(A, dir, ig1); HFAV_LAUNCHED(rt, "u_cmpflx", st);
+                u_update<T><<<blocks, 256, 0, st>>>(A, dir, G, step, gm.cfl); HFAV_LAUNCHED(rt, "u_update", st);
             }
         }
         // the wave speed of the final state (for the dt history / status)
         gcfl_reduce<T><<<dim3(64, 1), 256, 0, st>>>(tabs + steps[n_steps - 1].y, 1, n_steps, gm.gamma,
                                                    rt->counters, 1);
-        HFAV_LAUNCHED(rt);
+        HFAV_LAUNCHED(rt, "gcfl_reduce", st);
         return HFAV_OK;
     }
     // persistent grids: the SMs times the resident CTAs of each kernel
@@ -987,9 +987,9 @@ static int run_godunov_t(hfav_plan_t* p, const Schedule& s, void* const* ax, voi
                 gsweep_x<T, true><<<gx, NT, 0, st>>>(tabs + steps[step].x, (const int2*)dxit, (int)xit.size(), Smax, C);
             else
                 gsweep_x<T, false><<<gx, NT, xsm, st>>>(tabs + steps[step].x, (const int2*)dxit, (int)xit.size(), Smax, C);
-            HFAV_LAUNCHED(rt);
+            HFAV_LAUNCHED(rt, "gsweep_x", st);
             ykern<<<gy, dim3(TX, TY), ysm, st>>>(tabs + steps[step].y, (const int2*)dyit, (int)yit.size(), C);
-            HFAV_LAUNCHED(rt);
+            HFAV_LAUNCHED(rt, "gsweep_y", st);
         }
         return HFAV_OK;
     }
@@ -1011,7 +1011,7 @@ static int run_godunov_t(hfav_plan_t* p, const Schedule& s, void* const* ax, voi
         for (int step = 0; step < n_steps; ++step) {
             C.step = step;
             fk<<<gf, dim3(TX, TY), fsm, st>>>(tabs + steps[step].full, (const int2*)dyit, (int)yit.size(), C);
-            HFAV_LAUNCHED(rt);
+            HFAV_LAUNCHED(rt, "gfull", st);
         }
     }
     return HFAV_OK;

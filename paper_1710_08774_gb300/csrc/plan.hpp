@@ -107,4 +107,6 @@ int autotune(hfav_plan_t* p, void* const* ax, void* const* go, int n_steps, int 
              float* times, int n_times);
 void destroy_runtime(hfav_plan_t* p);
 void drop_graph(hfav_plan_t* p);
+int kernel_times(hfav_plan_t* p, std::vector<std::string>* names, std::vector<double>* ms, std::vector<int>* counts);
+int set_timing(hfav_plan_t* p, int on);
 }  // namespace hfav

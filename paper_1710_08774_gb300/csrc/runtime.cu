@@ -55,6 +55,18 @@ int check_ptrs(hfav_plan_t* p, void* const* ax, void* const* go) {
 
 }  // namespace
 
+void kt_mark(Runtime* rt, const char* name, cudaStream_t st) {
+    if (rt->kused == rt->kpool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return; }
+        rt->kpool.push_back(e);
+        rt->kname.push_back("");
+    }
+    rt->kname[rt->kused] = name;
+    cudaEventRecord(rt->kpool[rt->kused], st);
+    rt->kused++;
+}
+
 int scratch(hfav_plan_t* p, const std::string& name, size_t bytes, void** out) {
     Runtime* rt = p->rt;
     auto it = rt->named.find(name);
@@ -93,6 +105,10 @@ void destroy_runtime(hfav_plan_t* p) {
     for (void* a : rt->allocs) cudaFree(a);
     if (rt->ev0) cudaEventDestroy(rt->ev0);
     if (rt->ev1) cudaEventDestroy(rt->ev1);
+    for (cudaEvent_t e : rt->kpool) cudaEventDestroy(e);
+    if (rt->join0) cudaEventDestroy(rt->join0);
+    if (rt->join1) cudaEventDestroy(rt->join1);
+    if (rt->own) cudaStreamDestroy(rt->own);
     delete rt;
     p->rt = nullptr;
 }
@@ -109,6 +125,19 @@ int run(hfav_plan_t* p, void* const* ax, void* const* go, int n_steps, void* str
     rt->last_steps = n_steps;
     const size_t nptr = p->grids.size() * (p->dag.axioms.size() + p->dag.goals.size());
     if (graph) {
+        // the legacy default stream cannot be captured: capture on a plan-owned
+        // stream ordered after / before the caller's stream with two events
+        cudaStream_t caller = st;
+        if (st == nullptr || st == cudaStreamLegacy) {
+            if (!rt->own) {
+                HFAV_CUDA(cudaStreamCreateWithFlags(&rt->own, cudaStreamNonBlocking));
+                HFAV_CUDA(cudaEventCreateWithFlags(&rt->join0, cudaEventDisableTiming));
+                HFAV_CUDA(cudaEventCreateWithFlags(&rt->join1, cudaEventDisableTiming));
+            }
+            HFAV_CUDA(cudaEventRecord(rt->join0, caller));
+            HFAV_CUDA(cudaStreamWaitEvent(rt->own, rt->join0, 0));
+            st = rt->own;
+        }
         std::vector<void*> key;
         for (size_t k = 0; k < p->grids.size() * p->dag.axioms.size(); ++k) key.push_back(ax[k]);
         for (size_t k = 0; k < p->grids.size() * p->dag.goals.size(); ++k) key.push_back(go[k]);
@@ -142,9 +171,16 @@ int run(hfav_plan_t* p, void* const* ax, void* const* go, int n_steps, void* str
         HFAV_CUDA(cudaEventRecord(rt->ev0, st));
         HFAV_CUDA(cudaGraphLaunch(rt->gexec, st));
         HFAV_CUDA(cudaEventRecord(rt->ev1, st));
+        if (st != caller) {
+            HFAV_CUDA(cudaEventRecord(rt->join1, st));
+            HFAV_CUDA(cudaStreamWaitEvent(caller, rt->join1, 0));
+            rt->last_stream = st;
+        }
         return HFAV_OK;
     }
     rt->launches = 0;
+    rt->kused = 0;
+    if (rt->timing) kt_mark(rt, "", st);
     HFAV_CUDA(cudaEventRecord(rt->ev0, st));
     rc = launch_once(p, p->sched, ax, go, n_steps, st);
     if (rc) return rc;
@@ -237,6 +273,29 @@ int autotune(hfav_plan_t* p, void* const* ax, void* const* go, int n_steps, int 
     if (e != cudaSuccess) return set_error(HFAV_ECUDA, cudaGetErrorString(e));
     p->sched = best_t < 1e30f ? best : keep;
     drop_graph(p);
+    return HFAV_OK;
+}
+
+int kernel_times(hfav_plan_t* p, std::vector<std::string>* names, std::vector<double>* ms, std::vector<int>* counts) {
+    Runtime* rt = p->rt;
+    names->clear(); ms->clear(); counts->clear();
+    if (!rt || rt->kused < 2) return HFAV_OK;
+    HFAV_CUDA(cudaEventSynchronize(rt->kpool[rt->kused - 1]));
+    for (size_t k = 1; k < rt->kused; ++k) {
+        float t = 0.f;
+        HFAV_CUDA(cudaEventElapsedTime(&t, rt->kpool[k - 1], rt->kpool[k]));
+        auto it = std::find(names->begin(), names->end(), rt->kname[k]);
+        if (it == names->end()) { names->push_back(rt->kname[k]); ms->push_back(t); counts->push_back(1); }
+        else { size_t i = it - names->begin(); (*ms)[i] += t; (*counts)[i] += 1; }
+    }
+    return HFAV_OK;
+}
+
+int set_timing(hfav_plan_t* p, int on) {
+    int rc = ensure_runtime(p);
+    if (rc) return rc;
+    p->rt->timing = on != 0;
+    p->rt->kused = 0;
     return HFAV_OK;
 }
 

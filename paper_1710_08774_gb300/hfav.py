@@ -32,7 +32,7 @@ SYMBOLS = ["hfav_plan", "hfav_analyze", "hfav_plan_groups", "hfav_plan_field", "
            "hfav_plan_set_schedule", "hfav_plan_schedule", "hfav_plan_dump", "hfav_plan_features", "hfav_run",
            "hfav_run_graph", "hfav_status", "hfav_autotune", "hfav_plan_variants", "hfav_free", "hfav_last_error",
            "hfav_version", "hfav_mlp_n_params", "hfav_mlp_forward", "hfav_mlp_work_floats", "hfav_mlp_loss_grad",
-           "hfav_mlp_adam", "hfav_mlp_train", "hfav_model_choose"]
+           "hfav_mlp_adam", "hfav_mlp_train", "hfav_model_choose", "hfav_plan_timing", "hfav_kernel_times"]
 
 
 class HfavError(RuntimeError):
@@ -143,6 +143,9 @@ def load(path=None):
                             P, P, P, P], ctypes.c_int),
         "hfav_model_choose": ([P, P, ctypes.c_int, fp, fp, fp, ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t],
                               ctypes.c_int),
+        "hfav_plan_timing": ([P, ctypes.c_int], ctypes.c_int),
+        "hfav_kernel_times": ([P, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double), ip,
+                               ctypes.c_int], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -413,6 +416,18 @@ class Plan:
         rc = check(load().hfav_status(self.h, ctypes.byref(st)))
         return dict(rc=rc, newton_nonconverged=st.newton_nonconverged, nonphysical=st.nonphysical,
                     dt=list(st.dt[:st.n_dt]), last_ms=st.last_ms, last_launches=st.last_launches)
+
+    def timing(self, on=True):
+        check(load().hfav_plan_timing(self.h, int(bool(on))))
+
+    def kernel_times(self):
+        """{kernel name: (total ms, launches)} of the last run with timing on."""
+        names = ctypes.create_string_buffer(1 << 14)
+        ms = (ctypes.c_double * 64)()
+        cnt = (ctypes.c_int * 64)()
+        n = check(load().hfav_kernel_times(self.h, names, len(names), ms, cnt, 64))
+        nm = names.value.decode().split("\n")
+        return {nm[k]: (ms[k], cnt[k]) for k in range(n)}
 
     def autotune(self, axioms, goals, n_steps=1, reps=3, stream=None):
         vs = self.variants()
