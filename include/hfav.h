@@ -287,6 +287,34 @@ int hfav_plan_variants(const hfav_plan_t* plan, char* buf, size_t n);
 int hfav_plan_timing(hfav_plan_t* plan, int enable);
 int hfav_kernel_times(hfav_plan_t* plan, char* names, size_t n_names, double* ms, int* counts, int max_kernels);
 
+/*
+ * hfav_chain2d_static: the 2D three-stage chain (L = weighted 5-point star of u,
+ * G = |central gradient of L| / 2, out = G / (1 + G)) computed without any
+ * device allocation, for callers that cannot allocate device memory once they
+ * are running (a host application whose pool owns the device's memory, a
+ * latency-critical loop that must avoid cudaMalloc's implicit synchronisation,
+ * a caller without a plan).  The paper has no counterpart: it is a deployment
+ * variant of the chain's "sweep" schedule, whose materialised L lives here in a
+ * file-scope device array of HFAV_STATIC_SCRATCH_BYTES = 16 MiB instead of a
+ * plan-owned buffer.
+ *   u, out   : device arrays of the same layout: (ny + 2 halo) rows of pitch
+ *              elements, interior at (halo, halo); out's halo is not written.
+ *   bc       : HFAV_BC_PERIODIC (halo never read) or HFAV_BC_HALO_GIVEN
+ *              (halo >= 2, read as given).
+ *   weights  : host array of 5 weights of u(i+1), u(i-1), u(j+1), u(j-1),
+ *              u(i, j), or NULL for (1, 1, 1, 1, -4).
+ *   stream   : cudaStream_t (NULL = legacy stream); asynchronous.
+ * Limits and behaviour: (nx + 2) * (ny + 2) * 8 bytes must fit the 16 MiB
+ * array, else HFAV_EINVAL and no device work.  The array is held by every GPU
+ * that loads the library until the process exits.  The first call on a device
+ * looks up the array's address on that device (make it before any stream
+ * capture).  All calls share the array and each overwrites all of L it reads;
+ * calls whose device work overlaps race.  Allocates nothing (no cudaMalloc,
+ * cudaFree or allocating library call).
+ */
+int hfav_chain2d_static(const double* u, int64_t nx, int64_t ny, int64_t pitch, int halo, int bc,
+                        const double* weights, double* out, void* stream);
+
 void hfav_free(hfav_plan_t* plan);
 
 const char* hfav_last_error(void);
