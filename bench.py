@@ -143,6 +143,23 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_once(args):
+    """One plan.run of the Godunov workload (the case ncu captures)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1710_08774_gb300 import hfav as H
+    from paper_1710_08774_gb300 import inputs as I
+    td = torch.float64 if args.dtype == "f64" else torch.float32
+    U = I.sod_state(args.n, args.n, seed=SEED)
+    ins = [torch.from_numpy(U[f].copy()).cuda().to(td) for f in range(4)]
+    outs = [torch.empty_like(t) for t in ins]
+    plan = H.Plan(H.godunov_dag(cfl=CFL), [H.Grid.of(ins[0], 0)], H.HFAV_F64 if args.dtype == "f64" else H.HFAV_F32,
+                  H.HFAV_BC_PERIODIC, args.schedule or "sweep:reg:32x4")
+    plan.run(ins, outs, args.tsteps)
+    print(json.dumps(plan.status()))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -151,9 +168,16 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--schedule", default=None, help="fixed fused schedule (default: autotuned)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--once", action="store_true",
+                    help="profiling case: build the plan and run it once (no timing, no JSON)")
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
+    ap.add_argument("--n", type=int, default=NX)
+    ap.add_argument("--tsteps", type=int, default=TSTEPS)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.once:
+        return run_once(args)
 
     import torch
     ws, rank, local = dist_env()

@@ -315,6 +315,13 @@ int hfav_kernel_times(hfav_plan_t* plan, char* names, size_t n_names, double* ms
 int hfav_chain2d_static(const double* u, int64_t nx, int64_t ny, int64_t pitch, int halo, int bc,
                         const double* weights, double* out, void* stream);
 
+/* Diagnostic: the FP64 reciprocal and quotient the Godunov kernels use in
+ * place of IEEE division (hardware estimate refined by two Newton-Raphson
+ * steps; quotient with one residual correction).  For n doubles x (device):
+ * rcp_out[k] = 1/x[k], quot_out[k] = 1.5/x[k] (device arrays).  Tests hold
+ * them to within 2 ulp of IEEE division. */
+int hfav_selftest_arith(const double* x, int64_t n, double* rcp_out, double* quot_out, void* stream);
+
 void hfav_free(hfav_plan_t* plan);
 
 const char* hfav_last_error(void);

@@ -120,61 +120,82 @@ __device__ __forceinline__ Face4<T> shfl_face(const Face4<T>& q, int src) {
 template <typename T>
 __global__ void __launch_bounds__(256) gsweep_xw(const GGrid<T>* __restrict__ grids, const int2* __restrict__ items,
                                                  int n_items, const GCommon C) {
+    // one CTA per row; its A warps split the row into A arcs of equal length
+    // (rows with nx % (32 A) != 0 use one arc).  Arc w streams the faces of
+    // cells a0-1 .. a0+La-2; the face of its last cell is the first face of
+    // arc w+1 and the qm of that face's right state is arc w+1's first trace:
+    // both cross through shared memory.
+    __shared__ Face4<T> s_qm[8], s_F[8];
     const int lane = threadIdx.x & 31;
-    const int wid = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int w = threadIdx.x >> 5;
+    const int A = blockDim.x >> 5;
     const T g = (T)C.gamma, ig1 = (T)(1.0 / (C.gamma - 1.0));
     int nonconv = 0;
-    for (int item = wid; item < n_items; item += nw) {
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int2 it = items[item];
         const GGrid<T>& G = grids[it.x];
         const int j = it.y, nx = G.nx;
         const bool exact = (nx & 31) == 0;
-        const int nf = exact ? nx : nx + 1;           // faces of cells -1 .. nf-2
+        const int arcs = (exact && nx % (32 * A) == 0) ? A : 1;
+        const bool active = w < arcs;
+        const int La = exact ? nx / arcs : nx;
+        const int a0 = active ? w * La : 0;
+        const int nf = exact ? La : nx + 1;           // faces of cells a0-1 .. a0+nf-2
         const int nch = (nf + 31) >> 5;
         const T dtdx = (T)dtdx_of(G, C.step, C.cfl);
         auto load_prim = [&](int i) {
             const int iw = wrap_idx(i, nx);
             return cons_to_prim(ldg_src(G, 0, iw, j), ldg_src(G, 1, iw, j), ldg_src(G, 2, iw, j), ldg_src(G, 3, iw, j), g);
         };
-        Prim<T> Wold = load_prim(-33 + lane);          // chunk -1 (only lane 31, cell -2, is used)
-        Prim<T> carryW = shfl_prim(Wold, 31);
-        Wold = load_prim(-1 + lane);                   // chunk 0
-        Face4<T> qmOld, qpOld, qmSave, Fsave, carryF;
-        int trace_cell_old = 0;
+        Prim<T> Wold, carryW;
+        if (active) {
+            Wold = load_prim(a0 - 33 + lane);          // chunk -1 (only lane 31, cell a0-2, is used)
+            carryW = shfl_prim(Wold, 31);
+            Wold = load_prim(a0 - 1 + lane);           // chunk 0
+        }
+        Face4<T> qmOld, qpOld, qmNext, Fsave, carryF;
         for (int s = 1; s <= nch + 1; ++s) {
-            // W of chunk s (not needed at the last step of the exact form)
-            Prim<T> Wcur = Wold;
             const bool wstep = !(exact && s == nch + 1);
-            if (wstep) Wcur = load_prim(32 * s - 1 + lane);
-            // trace of chunk s-1 (exact form: the chunk nch is the saved chunk 0)
+            Prim<T> Wcur = Wold;
             Face4<T> qmNew, qpNew;
-            if (wstep) {
+            if (active && wstep) {
+                Wcur = load_prim(a0 + 32 * s - 1 + lane);
                 Prim<T> wl = shfl_prim(Wold, (lane + 31) & 31);
                 if (lane == 0) wl = carryW;
                 Prim<T> wr = shfl_prim(Wold, (lane + 1) & 31);
                 Prim<T> w0n = shfl_prim(Wcur, 0);
                 if (lane == 31) wr = w0n;
-                slope_trace(wl, Wold, wr, dtdx, qmNew, qpNew);
-                if (s == 1) qmSave = shfl_face(qmNew, 0);
+                slope_trace(wl, Wold, wr, dtdx, qmNew, qpNew);   // cells of chunk s-1
                 carryW = shfl_prim(Wold, 31);
+                if (s == 1 && exact) {
+                    Face4<T> q0 = shfl_face(qmNew, 0);   // qm of cell a0-1
+                    if (lane == 0) s_qm[w] = q0;
+                }
             }
-            // faces and updates of chunk s-2
-            if (s >= 2) {
+            if (s == 1) {
+                __syncthreads();
+                if (active && exact) qmNext = s_qm[(w + 1) % arcs];   // qm of cell a0+La-1
+            }
+            if (active && s >= 2) {
                 const int v = s - 2;
-                const int cell = 32 * v - 1 + lane;
+                const int cell = a0 + 32 * v - 1 + lane;
                 Face4<T> qR = shfl_face(qmOld, (lane + 1) & 31);
-                Face4<T> q0n = (exact && s == nch + 1) ? qmSave : shfl_face(qmNew, 0);
+                Face4<T> q0n = (exact && s == nch + 1) ? qmNext : shfl_face(qmNew, 0);
                 if (lane == 31) qR = q0n;
                 int nc_local = 0;
                 Face4<T> F = flux(riemann(qpOld, qR, g, &nc_local), ig1);
-                if (cell <= nf - 2) nonconv |= nc_local;
-                if (v == 0) Fsave = shfl_face(F, 0);   // face of cell -1
+                if (32 * v - 1 + lane <= nf - 2) nonconv |= nc_local;
+                if (v == 0) {
+                    Fsave = shfl_face(F, 0);   // face of cell a0-1
+                    if (lane == 0) s_F[w] = Fsave;
+                }
                 Face4<T> Fl = shfl_face(F, (lane + 31) & 31);
                 if (lane == 0) Fl = carryF;
                 carryF = shfl_face(F, 31);
-                // update cell with left face Fl and right face F
-                const bool upd = cell >= 0 && cell < (exact ? nx - 1 : nx) && !(v == 0 && lane == 0);
+                // update with left face Fl and right face F (cell a0-1 belongs
+                // to the previous arc; in exact form the arc's last cell waits
+                // for the next arc's first face)
+                const bool upd = (32 * v - 1 + lane >= 0) && cell < (exact ? a0 + La - 1 : nx) && cell >= 0;
                 if (upd) {
                     st_dst(G, 0, cell, j, fma(-dtdx, F.r - Fl.r, ldg_src(G, 0, cell, j)));
                     st_dst(G, 1, cell, j, fma(-dtdx, F.u - Fl.u, ldg_src(G, 1, cell, j)));
@@ -184,16 +205,19 @@ __global__ void __launch_bounds__(256) gsweep_xw(const GGrid<T>* __restrict__ gr
             }
             qmOld = qmNew; qpOld = qpNew;
             Wold = Wcur;
-            (void)trace_cell_old;
         }
-        // exact form: cell nx-1 between the last face (carryF) and the face of cell -1
-        if (exact && lane == 0) {
-            const int cell = nx - 1;
-            st_dst(G, 0, cell, j, fma(-dtdx, Fsave.r - carryF.r, ldg_src(G, 0, cell, j)));
-            st_dst(G, 1, cell, j, fma(-dtdx, Fsave.u - carryF.u, ldg_src(G, 1, cell, j)));
-            st_dst(G, 2, cell, j, fma(-dtdx, Fsave.v - carryF.v, ldg_src(G, 2, cell, j)));
-            st_dst(G, 3, cell, j, fma(-dtdx, Fsave.p - carryF.p, ldg_src(G, 3, cell, j)));
+        __syncthreads();
+        // exact form: the last cell of the arc, between the arc's last face
+        // (carryF) and the next arc's first face
+        if (active && exact && lane == 0) {
+            const Face4<T> Fr = s_F[(w + 1) % arcs];
+            const int cell = a0 + La - 1;
+            st_dst(G, 0, cell, j, fma(-dtdx, Fr.r - carryF.r, ldg_src(G, 0, cell, j)));
+            st_dst(G, 1, cell, j, fma(-dtdx, Fr.u - carryF.u, ldg_src(G, 1, cell, j)));
+            st_dst(G, 2, cell, j, fma(-dtdx, Fr.v - carryF.v, ldg_src(G, 2, cell, j)));
+            st_dst(G, 3, cell, j, fma(-dtdx, Fr.p - carryF.p, ldg_src(G, 3, cell, j)));
         }
+        __syncthreads();
     }
     unsigned any_nc = __ballot_sync(0xffffffffu, nonconv);
     if (lane == 0 && any_nc) atomicAdd(&C.counters[0], (unsigned long long)__popc(any_nc));
@@ -748,7 +772,7 @@ int state_ptrs(hfav_plan_t* p, int kind, int g, void* const* ax, void* const* go
 
 // grid decomposition (x segments, y strips / chunks) for one schedule
 template <typename T>
-void decompose(const hfav_plan_t* p, const Schedule& s, int g, GGrid<T>& G, int Smax) {
+void decompose(const hfav_plan_t* p, const Schedule& s, int g, GGrid<T>& G, int Smax, int yR) {
     const hfav_grid& H = p->grids[g];
     const int nx = (int)H.extent[0], ny = (int)H.extent[1];
     G.nx = nx; G.ny = ny;
@@ -762,16 +786,34 @@ void decompose(const hfav_plan_t* p, const Schedule& s, int g, GGrid<T>& G, int 
         while ((k * 32 - 2) * nseg < nx) ++k;
         G.xS = k * 32 - 2; G.xseg = nseg; G.xfull = 0;
     }
-    // y: rows per thread so that the whole batch gives about 8 warps per SM
-    double cells = 0;
-    for (auto& q : p->grids) cells += (double)q.extent[0] * q.extent[1];
     const int W = s.fusion == FUSE_FULL ? s.tx - 2 : s.tx;
-    int R = (int)(cells / ((double)kSMs * 32 * 8));
-    R = std::max(8, std::min(R, 256));
-    R = std::min(R, std::max(4, ny));
+    int R = std::min(yR, std::max(4, ny));
     G.yR = R;
     G.ystrips = (nx + W - 1) / W;
     G.ychunks = (ny + R - 1) / R;
+}
+
+// Rows per y item.  A y item is TX/32 warps streaming R rows (plus a 4-row
+// prologue whose faces, traces and states are recomputed).  On a part whose
+// FP64 pipe is the bottleneck the pass ends when the busiest SM sub-partition
+// (608 of them) has drained its warps, so R is chosen to minimise
+// ceil(warps / 608) * (R + 1.5), with a penalty when fewer than two warps per
+// sub-partition are left to hide latency.
+int choose_yR(const hfav_plan_t* p, const Schedule& s) {
+    const int W = s.fusion == FUSE_FULL ? s.tx - 2 : s.tx;
+    const int wpi = s.tx / 32;
+    double best = 1e30;
+    int bestR = 16;
+    for (int R = 8; R <= 256; ++R) {
+        int64_t warps = 0;
+        for (auto& g : p->grids)
+            warps += (int64_t)((g.extent[0] + W - 1) / W) * ((g.extent[1] + R - 1) / R) * wpi;
+        const int64_t slots = (int64_t)kSMs * 4;
+        const int64_t q = (warps + slots - 1) / slots;
+        const double cost = q * (R + 1.5) / (q >= 2 ? 1.0 : 0.6);
+        if (cost < best - 1e-9) { best = cost; bestR = R; }
+    }
+    return bestR;
 }
 
 // largest staged x segment whose staging stays within ~100 KB (two CTAs per SM)
@@ -795,6 +837,7 @@ static int run_godunov_t(hfav_plan_t* p, const Schedule& s, void* const* ax, voi
     const size_t es = sizeof(T);
     const GodunovMap& gm = p->gmap;
     const int Smax = smax_for(p, es);
+    const int yR = choose_yR(p, s);
     // wave slots: n_steps + 1 per grid
     if (rt->wave_cap < n_steps + 1 || !rt->wave) {
         int cap = std::max(n_steps + 1, 128);
@@ -833,7 +876,7 @@ static int run_godunov_t(hfav_plan_t* p, const Schedule& s, void* const* ax, voi
             for (int f = 0; f < 4; ++f) { G.src[f] = sp[f]; G.dst[f] = dp[f]; }
             G.spitch = spitch; G.dpitch = dpitch; G.shalo = shalo; G.dhalo = dhalo;
             G.wave = rt->wave + (size_t)g * rt->wave_cap;
-            decompose<T>(p, s, g, G, Smax);
+            decompose<T>(p, s, g, G, Smax, yR);
             host.push_back(G);
         }
         tix[key] = at;
@@ -953,11 +996,19 @@ static int run_godunov_t(hfav_plan_t* p, const Schedule& s, void* const* ax, voi
             return p->grids[a.x].extent[0] > p->grids[b.x].extent[0];
         });
         void* dxrows = nullptr;
+        // arcs per row: enough row-arc warps for ~6 per SM sub-partition
+        int xarcs = 1;
+        {
+            int64_t rows = (int64_t)xrows.size();
+            int minnx = 1 << 30;
+            for (auto& q : p->grids) minnx = std::min<int>(minnx, (int)q.extent[0]);
+            while (xarcs < 8 && rows * xarcs < (int64_t)kSMs * 4 * 6 && minnx >= 32 * 2 * xarcs * 2) xarcs *= 2;
+        }
         if (s.placement == PLACE_REG) {
             if ((rc = scratch(p, "gxrows", xrows.size() * sizeof(int2), &dxrows))) return rc;
             if (!rt->capturing)
                 HFAV_CUDA(cudaMemcpy(dxrows, xrows.data(), xrows.size() * sizeof(int2), cudaMemcpyHostToDevice));
-            HFAV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occx, gsweep_xw<T>, NT, 0));
+            HFAV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occx, gsweep_xw<T>, 32 * xarcs, 0));
         } else if (s.placement == PLACE_HBM) {
             HFAV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occx, gsweep_x<T, true>, NT, 0));
         } else {
@@ -971,7 +1022,7 @@ static int run_godunov_t(hfav_plan_t* p, const Schedule& s, void* const* ax, voi
         occx = std::max(occx, 1); occy = std::max(occy, 1);
         int gx;
         if (s.placement == PLACE_REG)
-            gx = (int)std::min<int64_t>(((int64_t)xrows.size() * 32 + NT - 1) / NT, (int64_t)kSMs * occx);
+            gx = (int)std::min<int64_t>((int64_t)xrows.size(), (int64_t)kSMs * occx);
         else
             gx = (int)std::min<int64_t>((int64_t)xit.size(), (int64_t)kSMs * occx);
         int gy = (int)std::min<int64_t>(((int64_t)yit.size() + TY - 1) / TY, (int64_t)kSMs * occy);
@@ -982,7 +1033,7 @@ static int run_godunov_t(hfav_plan_t* p, const Schedule& s, void* const* ax, voi
         for (int step = 0; step < n_steps; ++step) {
             C.step = step;
             if (s.placement == PLACE_REG)
-                gsweep_xw<T><<<gx, NT, 0, st>>>(tabs + steps[step].x, (const int2*)dxrows, (int)xrows.size(), C);
+                gsweep_xw<T><<<gx, 32 * xarcs, 0, st>>>(tabs + steps[step].x, (const int2*)dxrows, (int)xrows.size(), C);
             else if (s.placement == PLACE_HBM)
                 gsweep_x<T, true><<<gx, NT, 0, st>>>(tabs + steps[step].x, (const int2*)dxit, (int)xit.size(), Smax, C);
             else
@@ -1024,3 +1075,28 @@ int launch_godunov(hfav_plan_t* p, const Schedule& s, void* const* ax, void* con
 }
 
 }  // namespace hfav
+
+// ---------------------------------------------------------------------------
+// diagnostic: the Newton-refined reciprocal and quotient of the kernels on an
+// array, so tests can hold them against IEEE division
+// ---------------------------------------------------------------------------
+namespace hfav {
+__global__ void selftest_arith_k(const double* __restrict__ x, int64_t n, double* __restrict__ r,
+                                 double* __restrict__ q) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        r[k] = rcp_nr(x[k]);
+        q[k] = div_nr(1.5, x[k]);
+    }
+}
+}  // namespace hfav
+
+extern "C" int hfav_selftest_arith(const double* x, int64_t n, double* rcp_out, double* quot_out, void* stream) {
+    using namespace hfav;
+    if (!x || !rcp_out || !quot_out || n < 0) return set_error(HFAV_EINVAL, "bad argument");
+    if (n == 0) return HFAV_OK;
+    int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    selftest_arith_k<<<blocks, 256, 0, (cudaStream_t)stream>>>(x, n, rcp_out, quot_out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(HFAV_ECUDA, cudaGetErrorString(e));
+    return HFAV_OK;
+}

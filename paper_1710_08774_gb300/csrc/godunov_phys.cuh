@@ -19,6 +19,58 @@ namespace hfav {
 #define G_NEWTON_MAX 10
 #define G_NEWTON_TOL 1e-10
 
+// ---- arithmetic helpers that keep work off the FP64 pipe ------------------
+// On this part the FP64 pipe issues ~1/58 of the FP32 rate, so compares,
+// floors and sign tests of doubles go through their bit patterns on the
+// integer pipe, and reciprocals use the hardware estimate refined by
+// Newton-Raphson (each step r <- r + r (1 - b r) squares the relative error;
+// the estimate has ~2^-23, two steps reach the last bits of a double).
+
+// x < y for doubles that are not NaN, as signed 64-bit compares of the bits
+__device__ __forceinline__ bool dlt(double x, double y) {
+    long long a = __double_as_longlong(x), b = __double_as_longlong(y);
+    // negative doubles order reversed as integers: flip their magnitude bits
+    a ^= (a >> 63) & 0x7fffffffffffffffLL;
+    b ^= (b >> 63) & 0x7fffffffffffffffLL;
+    return a < b;
+}
+__device__ __forceinline__ bool dlt(float x, float y) { return x < y; }
+// max(x, floor) for a positive floor
+__device__ __forceinline__ double dfloor(double x, double fl) { return dlt(x, fl) ? fl : x; }
+__device__ __forceinline__ float dfloor(float x, float fl) { return x < fl ? fl : x; }
+// |x| < |y|
+__device__ __forceinline__ bool dabslt(double x, double y) {
+    unsigned long long a = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
+    unsigned long long b = (unsigned long long)__double_as_longlong(y) & 0x7fffffffffffffffULL;
+    return a < b;
+}
+__device__ __forceinline__ bool dabslt(float x, float y) { return fabsf(x) < fabsf(y); }
+// sign classes: > 0, < 0
+__device__ __forceinline__ bool dpos(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool dneg(double x) { return __double_as_longlong(x) < 0 && (__double_as_longlong(x) & 0x7fffffffffffffffLL) != 0; }
+__device__ __forceinline__ bool dpos(float x) { return x > 0.f; }
+__device__ __forceinline__ bool dneg(float x) { return x < 0.f; }
+
+__device__ __forceinline__ double rcp_est(double b) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(b));
+    return r;
+}
+// reciprocal to within an ulp or two (two Newton-Raphson steps)
+__device__ __forceinline__ double rcp_nr(double b) {
+    double r = rcp_est(b);
+    r = fma(r, fma(-b, r, 1.0), r);
+    return fma(r, fma(-b, r, 1.0), r);
+}
+__device__ __forceinline__ float rcp_nr(float b) { return 1.0f / b; }
+// quotient a / b: a * (1/b) with one residual correction
+__device__ __forceinline__ double div_nr(double a, double b) {
+    const double r = rcp_nr(b);
+    const double q = a * r;
+    return fma(r, fma(-b, q, a), q);
+}
+__device__ __forceinline__ float div_nr(float a, float b) { return a / b; }
+
 // Primitive state of a cell in the frame of a sweep: rho, u_normal,
 // u_transverse, p, sound speed c, 1/c and c/rho.
 template <typename T>
@@ -30,14 +82,14 @@ struct Prim {
 template <typename T>
 __device__ __forceinline__ Prim<T> cons_to_prim(T U0, T Un, T Ut, T E, T g) {
     Prim<T> w;
-    T r = U0 > (T)G_RHO_FLOOR ? U0 : (T)G_RHO_FLOOR;
-    T ir = (T)1 / r;
+    T r = dfloor(U0, (T)G_RHO_FLOOR);
+    T ir = rcp_nr(r);
     w.r = r;
     w.un = Un * ir;
     w.ut = Ut * ir;
     T e = fma(E, ir, (T)-0.5 * fma(w.un, w.un, w.ut * w.ut));
     T p = (g - (T)1) * r * e;
-    p = p > (T)G_P_FLOOR ? p : (T)G_P_FLOOR;
+    p = dfloor(p, (T)G_P_FLOOR);
     w.p = p;
     T s = rsqrt(g * p * r);
     w.c = g * p * s;
@@ -49,7 +101,7 @@ __device__ __forceinline__ Prim<T> cons_to_prim(T U0, T Un, T Ut, T E, T g) {
 // minmod of two differences: zero unless both have the same strict sign
 template <typename T>
 __device__ __forceinline__ T minmod(T a, T b) {
-    if ((a > (T)0 && b > (T)0) || (a < (T)0 && b < (T)0)) return fabs(a) < fabs(b) ? a : b;
+    if ((dpos(a) && dpos(b)) || (dneg(a) && dneg(b))) return dabslt(a, b) ? a : b;
     return (T)0;
 }
 
@@ -104,11 +156,11 @@ __device__ __forceinline__ Face4<T> riemann(const Face4<T>& L, const Face4<T>& R
     const double xl = gd * pl * rl, xr = gd * pr * rr;
     const double sl = rsqrt(xl), sr = rsqrt(xr);           // 1 / C_k
     const double cl = xl * sl, cr = xr * sr;               // C_k = sqrt(g p_k rho_k)
-    const double a = (gd + 1.0) / (2.0 * gd);
-    const double ipp = 1.0 / (pl * pr);
+    const double a = 0.5 * (gd + 1.0) * rcp_nr(gd);
+    const double ipp = rcp_nr(pl * pr);
     const double al = a * pr * ipp, ar = a * pl * ipp;     // a / p_k
-    double ps = (cr * pl + cl * pr - cl * cr * (ur - ul)) / (cl + cr);
-    ps = fmax(ps, G_P_FLOOR);
+    double ps = div_nr(cr * pl + cl * pr - cl * cr * (ur - ul), cl + cr);
+    ps = dfloor(ps, G_P_FLOOR);
     bool conv = false;
     for (int it = 0; it < G_NEWTON_MAX; ++it) {
         const double ql = rsqrt(fma(al, ps - pl, 1.0));
@@ -118,9 +170,15 @@ __device__ __forceinline__ Face4<T> riemann(const Face4<T>& L, const Face4<T>& R
         const double izr = 0.5 * iwr * fma(cr * cr, iwr * iwr, 1.0);
         const double usl = fma(-(ps - pl), iwl, ul);
         const double usr = fma(ps - pr, iwr, ur);
-        double pn = ps - (usr - usl) / (izl + izr);
-        pn = fmax(pn, G_P_FLOOR);
-        conv = fabs(pn - ps) <= G_NEWTON_TOL * pn;
+        // the Newton correction itself needs no last-bit accuracy: one
+        // refinement of the estimate is enough (the fixed point is set by
+        // usr == usl, not by this quotient)
+        const double den = izl + izr;
+        double rd = rcp_est(den);
+        rd = fma(rd, fma(-den, rd, 1.0), rd);
+        double pn = fma(-(usr - usl), rd, ps);
+        pn = dfloor(pn, G_P_FLOOR);
+        conv = !dlt(G_NEWTON_TOL * pn, fabs(pn - ps));
         ps = pn;
         if (conv) break;
     }
@@ -132,28 +190,28 @@ __device__ __forceinline__ Face4<T> riemann(const Face4<T>& L, const Face4<T>& R
     const T Cl = (T)cl, Cr = (T)cr;
     const T wl = Cl * tl * qlt, wr = Cr * tr * qrt;        // W_k = C_k sqrt(t_k)
     const T iwl = qlt * (T)sl, iwr = qrt * (T)sr;
-    const T ust = (fma(wl, L.u, wr * R.u) + (L.p - R.p)) / (wl + wr);
-    const bool left = ust > (T)0;
+    const T ust = div_nr(fma(wl, L.u, wr * R.u) + (L.p - R.p), wl + wr);
+    const bool left = dpos(ust);
     const Face4<T>& S = left ? L : R;
     const T ws = left ? wl : wr, iws = left ? iwl : iwr;
     const T sgn = left ? (T)-1 : (T)1;
-    T rst = S.r / fma(-S.r * (pst - S.p), iws * iws, (T)1);
-    rst = rst > (T)G_RHO_FLOOR ? rst : (T)G_RHO_FLOOR;
+    T rst = div_nr(S.r, fma(-S.r * (pst - S.p), iws * iws, (T)1));
+    rst = dfloor(rst, (T)G_RHO_FLOOR);
     Face4<T> o;
     o.v = S.v;
     bool take_side, take_star;
     T f = (T)0;
-    if (pst > S.p) {   // shock: it has passed the face when sgn * S < 0
-        take_side = fma(sgn * S.u, S.r, ws) < (T)0;
+    if (dlt(S.p, pst)) {   // shock: it has passed the face when sgn * S < 0
+        take_side = dneg(fma(sgn * S.u, S.r, ws));
         take_star = !take_side;
     } else {           // rarefaction fan
         const T cs = g * S.p * rsqrt(g * S.p * S.r);
         const T cst = g * pst * rsqrt(g * pst * rst);
         const T head = fma(sgn, cs, S.u);
         const T tail = fma(sgn, cst, ust);
-        take_side = sgn * head < (T)0;
-        take_star = !take_side && (sgn * tail > (T)0 || head == tail);
-        if (!take_side && !take_star) f = -tail / (head - tail);
+        take_side = left ? dpos(head) : dneg(head);
+        take_star = !take_side && ((left ? dneg(tail) : dpos(tail)) || head == tail);
+        if (!take_side && !take_star) f = div_nr(-tail, head - tail);
     }
     if (take_side) { o.r = S.r; o.u = S.u; o.p = S.p; }
     else if (take_star) { o.r = rst; o.u = ust; o.p = pst; }
@@ -181,14 +239,14 @@ __device__ __forceinline__ Face4<T> flux(const Face4<T>& q, T ig1) {
 // CFL wave speed max(|u|+c, |v|+c) of a conserved state, in FP64; also flags
 // non-physical states (rho <= 0 or p <= 0 before any floor)
 __device__ __forceinline__ double wave_speed(double U0, double U1, double U2, double U3, double g, int* bad) {
-    const double ir = 1.0 / U0;
+    const double ir = rcp_nr(U0);
     const double u = U1 * ir, v = U2 * ir;
     const double e = fma(U3, ir, -0.5 * fma(u, u, v * v));
     double p = (g - 1.0) * U0 * e;
-    if (!(U0 > 0.0) || !(p > 0.0)) *bad = 1;
-    p = fmax(p, G_P_FLOOR);
+    if (!dpos(U0) || !dpos(p)) *bad = 1;
+    p = dfloor(p, G_P_FLOOR);
     const double c = g * p * rsqrt(g * p * U0);
-    return fmax(fabs(u), fabs(v)) + c;
+    return (dabslt(u, v) ? fabs(v) : fabs(u)) + c;
 }
 
 // Same in FP32 for the FP32 bulk mode (the reduction itself is FP64)
