@@ -1,14 +1,19 @@
-"""Benchmark: 2D Euler Godunov step, FP64, 1024 x 1024, 10 time steps per bench step.
+"""Benchmark of the HFAV hot path on one GB300.
 
-One bench step = hfav_run of 10 Godunov time steps (CFL 0.5, x then y sweep,
-periodic, Sod-like state with 1% seeded perturbations) on device-resident
-state.  The fused schedule is picked by the project's autotuner among the
-fused variants during warm-up; the unfused form (every Hydro2D kernel its own
-launch over materialised arrays) is timed the same way.
+Default workload (the headline): the 2D Euler Godunov step, FP64,
+1024 x 1024, 10 time steps per bench step, CFL 0.5, x then y sweep, periodic,
+Sod-like state with 1% seeded perturbations, fused (the fusion schedule the
+project's autotuner picks among the fused variants) vs the unfused form
+(every Hydro2D kernel its own launch over materialised arrays).
 
-Prints one JSON line (rank 0).  Under torchrun each rank runs its own replica
-(the path has no data exchange on one grid that this build shards: "replicas
-only"), value = all ranks' cell updates / max time.
+Other workloads (``--workload``): the FP32-bulk Godunov at 4096^2, the batch
+of 64 uneven FP32 grids for 100 steps through a captured CUDA graph, the 2D
+three-stage chain at 256^2 FP64 and the 3D four-stage chain at 512^3 FP32.
+
+Prints one JSON line per workload (rank 0).  Under torchrun each rank runs
+its own replica (one grid is not sharded by this build: "replicas only");
+value = all ranks' cell updates / max time.  ``--impl reference`` times the
+CPU oracle on a bounded sample of the same workload.
 """
 import argparse
 import json
@@ -19,29 +24,27 @@ import sys
 import threading
 import time
 
-import numpy as np
-
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-NX = NY = 1024
-TSTEPS = 10
-CFL = 0.5
-SEED = 1
 METRIC = "Gcell-updates/s and % HBM roofline, fused vs unfused on 1 GB300 at stated tolerance"
 UNIT = "Gcell-updates/s"
-WORKLOAD = "godunov2d_fp64_1024x1024_10steps"
-# FP64 operations of the method per cell and sweep, counted from its
-# definition (each +, -, *, /, sqrt one flop; Newton iterations per face `it`):
+CFL = 0.5
+PEAK_FP64_GFLOPS = 1187.0      # DFMA rate measured on this GB300 pool by the repo's FP64 probe (nominal 1250)
+PEAK_FP32_GFLOPS = 68700.0     # FFMA rate measured by the same probe
+
+
+# FP64 operations of the method, counted from its definition (each +, -, *,
+# /, sqrt one flop; `it` Newton iterations per face): per cell and sweep
 # constoprim 8, eos 6, slope 12, trace 64, riemann 40 + 40 it, cmpflx 13,
 # update 12 -> 155 + 40 it; the CFL wave speed adds 16 per cell and step.
-def flops_per_cell_sweep(it):
+def godunov_flops_sweep(it):
     return 155.0 + 40.0 * it
 
 
-CFL_FLOPS = 16.0
-PEAK_FP64_GFLOPS = 1187.0      # DFMA throughput measured on this GB300 pool by the repo's FP64 probe
-NOMINAL_FP64_GFLOPS = 1250.0   # nominal FP64 rate of GB300
+GODUNOV_CFL_FLOPS = 16.0
+CHAIN2D_FLOPS = 14.0     # L 5, G 7 (2 sub, 2 mul, add, sqrt, halve), out 2
+CHAIN3D_FLOPS = 26.0     # s1 7, s2 7, s3 10, out 2
 
 
 def peaks():
@@ -52,33 +55,28 @@ def peaks():
 
 
 class Clocks:
-    """nvidia-smi sampled during the timed region."""
+    """nvidia-smi sampled every 200 ms during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
          "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
          "clocks_event_reasons.sw_power_cap")
 
     def __init__(self, dev=0):
-        self.dev = dev
-        self.lines = []
-        self.p = None
+        self.dev, self.lines, self.p = dev, [], None
 
     def start(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
                                        "--format=csv,noheader,nounits", "-lms", "200"],
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
-            self.t = threading.Thread(target=self._read, daemon=True)
-            self.t.start()
+            threading.Thread(target=lambda: [self.lines.append(l.strip()) for l in self.p.stdout],
+                             daemon=True).start()
         except Exception:
             self.p = None
-
-    def _read(self):
-        for ln in self.p.stdout:
-            self.lines.append(ln.strip())
 
     def stop(self):
         if not self.p:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
         self.p.terminate()
         try:
             self.p.wait(timeout=5)
@@ -86,7 +84,7 @@ class Clocks:
             self.p.kill()
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ln in list(self.lines):
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -102,224 +100,427 @@ class Clocks:
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
 
 
-def oracle_sample(n=512, tsteps=TSTEPS):
-    """The oracle (plain C, one thread) on an n x n sample of the workload."""
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+class Workload:
+    """A plan plus its device inputs; `step()` is one bench step."""
+    name = ""
+    dtype = "f64"
+    graph = False
+    fused_prefix = ("full", "sweep")
+
+    def cells_per_step(self):
+        raise NotImplementedError
+
+
+class Godunov(Workload):
+    def __init__(self, H, I, torch, dev, n, dtype, tsteps, seed=1):
+        self.name = f"godunov2d_{'fp64' if dtype == 'f64' else 'fp32bulk'}_{n}x{n}_{tsteps}steps"
+        self.dtype, self.n, self.tsteps = dtype, n, tsteps
+        td = torch.float64 if dtype == "f64" else torch.float32
+        U = I.sod_state(n, n, seed=seed)
+        self.host = U
+        self.ins = [torch.from_numpy(U[f].copy()).to(dev).to(td) for f in range(4)]
+        self.outs = [torch.empty_like(t) for t in self.ins]
+        self.hdt = H.HFAV_F64 if dtype == "f64" else H.HFAV_F32
+        self.grids = [H.Grid.of(self.ins[0], 0)]
+        self.plan = H.Plan(H.godunov_dag(cfl=CFL), self.grids, self.hdt, H.HFAV_BC_PERIODIC, "sweep:reg:32x4")
+        self.esize = 8 if dtype == "f64" else 4
+
+    def unfused_plan(self, H):
+        return H.Plan(H.godunov_dag(cfl=CFL), self.grids, self.hdt, H.HFAV_BC_PERIODIC, "unfused")
+
+    def run(self, plan):
+        plan.run(self.ins, self.outs, self.tsteps, graph=self.graph)
+
+    def cells_per_step(self):
+        return self.n * self.n * self.tsteps
+
+    def compulsory_bytes(self, sched):
+        per = 8 * self.esize * (2 if sched.startswith("sweep") else 1)   # 4 fields read + written per pass
+        return per * self.n * self.n * self.tsteps
+
+    def kernel_work(self, kernel, it):
+        """(bound, algorithmic work per launch, unit) of one launch of `kernel`."""
+        cells = self.n * self.n
+        if self.dtype == "f64":
+            per = {"gsweep_x": godunov_flops_sweep(it), "gsweep_y": godunov_flops_sweep(it) + GODUNOV_CFL_FLOPS,
+                   "gfull": 2 * godunov_flops_sweep(it) + GODUNOV_CFL_FLOPS}.get(kernel, godunov_flops_sweep(it))
+        else:   # FP64 work of the FP32-bulk form: the Newton iteration, ~36 flops per iteration and face
+            per = {"gsweep_x": 36.0 * it, "gsweep_y": 36.0 * it, "gfull": 72.0 * it}.get(kernel, 36.0 * it)
+        return "alu", per * cells, "GFLOP/s", PEAK_FP64_GFLOPS, "FP64 DFMA rate measured by the repo's probe"
+
+    def io(self):
+        return self.host, self.ins, self.outs
+
+
+class Batch(Godunov):
+    graph = True
+
+    def __init__(self, H, I, torch, dev, n_grids=64, tsteps=100, seed=3):
+        self.name = f"godunov2d_batch{n_grids}_fp32bulk_{tsteps}steps_graph"
+        self.dtype, self.tsteps = "f32", tsteps
+        self.sides = I.batch_sides(n_grids, seed=seed)
+        self.ins, self.outs, self.grids = [], [], []
+        for g, (nx, ny) in enumerate(self.sides):
+            U = I.sod_state(nx, ny, seed=seed, grid=g)
+            t = [torch.from_numpy(U[f].copy()).to(dev).float() for f in range(4)]
+            self.ins.append(t)
+            self.outs.append([torch.empty_like(x) for x in t])
+            self.grids.append(H.Grid.of(t[0], 0))
+        self.hdt = H.HFAV_F32
+        self.plan = H.Plan(H.godunov_dag(cfl=CFL), self.grids, self.hdt, H.HFAV_BC_PERIODIC, "sweep:reg:32x4")
+        self.esize = 4
+        self.cells = sum(nx * ny for nx, ny in self.sides)
+
+    def unfused_plan(self, H):
+        return None
+
+    def cells_per_step(self):
+        return self.cells * self.tsteps
+
+    def compulsory_bytes(self, sched):
+        return 8 * 4 * (2 if sched.startswith("sweep") else 1) * self.cells * self.tsteps
+
+    def kernel_work(self, kernel, it):
+        per = {"gsweep_x": 36.0 * it, "gsweep_y": 36.0 * it, "gfull": 72.0 * it}.get(kernel, 36.0 * it)
+        return "alu", per * self.cells, "GFLOP/s", PEAK_FP64_GFLOPS, "FP64 DFMA rate measured by the repo's probe"
+
+    def io(self):
+        return None, None, None
+
+
+class Chain(Workload):
+    fused_prefix = ("full", "sweep")
+
+    def __init__(self, H, I, torch, dev, dims, n, dtype, seed):
+        self.dims, self.n, self.dtype = dims, n, dtype
+        self.name = f"chain{dims}d_{'fp64' if dtype == 'f64' else 'fp32'}_{'x'.join([str(n)] * dims)}"
+        td = torch.float64 if dtype == "f64" else torch.float32
+        if dims == 2:
+            u = I.chain2d_input(n, seed=seed)
+            dag, halo = H.chain2d_dag(), 2
+        else:
+            import numpy as np
+            u = I.chain3d_input(n, seed=seed, dtype=np.float32 if dtype == "f32" else np.float64)
+            dag, halo = H.chain3d_dag(), 3
+        self.u = torch.from_numpy(u).to(dev).to(td)
+        self.out = torch.empty_like(self.u)
+        self.dag = dag
+        self.hdt = H.HFAV_F64 if dtype == "f64" else H.HFAV_F32
+        self.grids = [H.Grid.of(self.u, halo)]
+        self.plan = H.Plan(dag, self.grids, self.hdt, H.HFAV_BC_PERIODIC, "full:reg:32x4")
+        self.esize = 8 if dtype == "f64" else 4
+
+    def unfused_plan(self, H):
+        return H.Plan(self.dag, self.grids, self.hdt, H.HFAV_BC_PERIODIC, "unfused")
+
+    def run(self, plan):
+        plan.run([self.u], [self.out], 1)
+
+    def cells_per_step(self):
+        return self.n ** self.dims
+
+    def compulsory_bytes(self, sched):
+        return 2 * self.esize * self.n ** self.dims
+
+    def kernel_work(self, kernel, it):
+        cells = self.n ** self.dims
+        if self.dtype == "f32":
+            return "hbm", 2 * self.esize * cells / 1e0, "GB/s", peaks().get("hbm_gbs", 6787.6), \
+                "measured copy bandwidth (MEASURED_PEAKS.json)"
+        fl = CHAIN2D_FLOPS if self.dims == 2 else CHAIN3D_FLOPS
+        return "alu", fl * cells, "GFLOP/s", PEAK_FP64_GFLOPS, "FP64 DFMA rate measured by the repo's probe"
+
+    def io(self):
+        return None, None, None
+
+
+WORKLOADS = ["godunov1024_f64", "godunov4096_f32", "batch64_f32", "chain2d256_f64", "chain3d512_f32"]
+
+
+def make(name, H, I, torch, dev):
+    if name == "godunov1024_f64":
+        return Godunov(H, I, torch, dev, 1024, "f64", 10)
+    if name == "godunov4096_f32":
+        return Godunov(H, I, torch, dev, 4096, "f32", 10)
+    if name == "batch64_f32":
+        return Batch(H, I, torch, dev)
+    if name == "chain2d256_f64":
+        return Chain(H, I, torch, dev, 2, 256, "f64", 0)
+    if name == "chain3d512_f32":
+        return Chain(H, I, torch, dev, 3, 512, "f32", 4)
+    raise SystemExit(f"unknown workload {name}")
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (reported baseline and the reference arm)
+# ---------------------------------------------------------------------------
+def oracle_sample(workload, n=None):
+    """(value in the metric's unit, seconds, Newton iterations per face, sample text)."""
+    import numpy as np
     import oracle
     from paper_1710_08774_gb300 import inputs as I
-    U = I.sod_state(n, n, seed=SEED)
+    oracle.build()
+    if workload.startswith("godunov") or workload.startswith("batch"):
+        n = n or 512
+        U = I.sod_state(n, n, seed=1)
+        t0 = time.perf_counter()
+        _, _, st = oracle.godunov(U, 10, cfl=CFL)
+        dt = time.perf_counter() - t0
+        return n * n * 10 / dt / 1e9, dt, st.newton_iters / max(st.faces, 1), \
+            f"{n}x{n} Sod-like seed 1, 10 steps, single thread"
+    if workload.startswith("chain2d"):
+        n = n or 2048
+        u = I.chain2d_input(n, seed=0)
+        t0 = time.perf_counter()
+        oracle.chain2d(u)
+        dt = time.perf_counter() - t0
+        return n * n / dt / 1e9, dt, 0.0, f"{n}x{n} u~U[0,1), single thread"
+    n = n or 160
+    u = I.chain3d_input(n, seed=4)
     t0 = time.perf_counter()
-    _, _, st = oracle.godunov(U, tsteps, cfl=CFL)
+    oracle.chain3d(u)
     dt = time.perf_counter() - t0
-    return n * n * tsteps / dt / 1e9, dt, st.newton_iters / max(st.faces, 1)
+    return n ** 3 / dt / 1e9, dt, 0.0, f"{n}^3 u~N(0,1), single thread"
 
 
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
         return
-    import oracle
-    oracle.build()
-    n = 512
+    name = args.workload
     for _ in range(args.warmup):
-        oracle_sample(n)
-    vals, secs = [], []
+        oracle_sample(name)
+    secs, vals, sample = [], [], ""
     for _ in range(args.steps):
-        v, dt, _ = oracle_sample(n)
+        v, dt, _, sample = oracle_sample(name)
         vals.append(v); secs.append(dt)
-    value = n * n * TSTEPS * len(secs) / sum(secs) / 1e9
+    value = statistics.mean(vals)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": f"{n}x{n}, {TSTEPS} steps per bench step"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": f"{n}x{n} Sod-like seed {SEED}, {TSTEPS} steps, single thread"},
+            "config": {"workload": name, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
 def run_once(args):
-    """One plan.run of the Godunov workload (the case ncu captures)."""
+    """One plan.run of a workload (the case ncu captures)."""
     import torch
     import __graft_entry__
     __graft_entry__.build()
     from paper_1710_08774_gb300 import hfav as H
     from paper_1710_08774_gb300 import inputs as I
-    td = torch.float64 if args.dtype == "f64" else torch.float32
-    U = I.sod_state(args.n, args.n, seed=SEED)
-    ins = [torch.from_numpy(U[f].copy()).cuda().to(td) for f in range(4)]
-    outs = [torch.empty_like(t) for t in ins]
-    plan = H.Plan(H.godunov_dag(cfl=CFL), [H.Grid.of(ins[0], 0)], H.HFAV_F64 if args.dtype == "f64" else H.HFAV_F32,
-                  H.HFAV_BC_PERIODIC, args.schedule or "sweep:reg:32x4")
-    plan.run(ins, outs, args.tsteps)
-    print(json.dumps(plan.status()))
+    w = make(args.workload, H, I, torch, torch.device("cuda:0"))
+    if args.schedule:
+        w.plan.schedule = args.schedule
+    w.run(w.plan)
+    torch.cuda.synchronize()
+    print(json.dumps({"workload": w.name, "schedule": w.plan.schedule}))
 
 
-def main():
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--schedule", default=None, help="fixed fused schedule (default: autotuned)")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--once", action="store_true",
-                    help="profiling case: build the plan and run it once (no timing, no JSON)")
-    ap.add_argument("--dtype", default="f64", choices=["f64", "f32"])
-    ap.add_argument("--n", type=int, default=NX)
-    ap.add_argument("--tsteps", type=int, default=TSTEPS)
-    args = ap.parse_args()
-    if args.impl == "reference":
-        return run_reference(args)
-    if args.once:
-        return run_once(args)
-
-    import torch
-    ws, rank, local = dist_env()
-    if ws > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    dev = torch.device(f"cuda:{local}" if ws > 1 else "cuda:0")
-    torch.cuda.set_device(dev)
-
-    import __graft_entry__
-    __graft_entry__.build()
-    from paper_1710_08774_gb300 import hfav as H
-    from paper_1710_08774_gb300 import inputs as I
-
-    U = I.sod_state(NX, NY, seed=SEED)
-    ins = [torch.from_numpy(U[f].copy()).to(dev) for f in range(4)]
-    outs = [torch.empty_like(t) for t in ins]
-    grid = H.Grid.of(ins[0], 0)
-    plan = H.Plan(H.godunov_dag(cfl=CFL), [grid], H.HFAV_F64, H.HFAV_BC_PERIODIC, "sweep:reg:32x4")
+# ---------------------------------------------------------------------------
+# timing protocol
+# ---------------------------------------------------------------------------
+def bench(args, name, torch, H, I, dev, ws, rank, local):
+    w = make(name, H, I, torch, dev)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
 
-    # warm-up + autotune among fused schedules
+    # the project's autotuner over the fused variants (all tiles and placements)
     if args.schedule:
         best = args.schedule
     else:
-        times = plan.autotune(ins, outs, TSTEPS, reps=2)
-        fused = {k: v for k, v in times.items() if not k.startswith("unfused") and v > 0}
+        times = w.plan.autotune(*_axg(w), n_steps=min(_nsteps(w), 4), reps=2)
+        fused = {k: v for k, v in times.items() if k.startswith(w.fused_prefix) and v > 0}
         best = min(fused, key=fused.get)
-    plan.schedule = best
+    w.plan.schedule = best
     for _ in range(max(args.warmup, 3)):
-        plan.run(ins, outs, TSTEPS)
+        w.run(w.plan)
     torch.cuda.synchronize(dev)
 
-    def timed(p, K, timing=False):
+    def timed(plan, K, timing=False):
         ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-        ktimes = {}
-        launches = 0
-        if timing:
-            p.timing(True)
+        ktimes, launches = {}, 0
+        if timing and not w.graph:
+            plan.timing(True)
         if ws > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
         for k in range(K):
             flush.fill_(k & 0xff)            # L2 flush between timed steps
             ev[k][0].record(stream)
-            p.run(ins, outs, TSTEPS)
+            w.run(plan)
             ev[k][1].record(stream)
-            if timing:
-                for nm, (ms, c) in p.kernel_times().items():
-                    a = ktimes.setdefault(nm, [0.0, 0])
-                    a[0] += ms; a[1] += c
-            launches += p.status()["last_launches"]
+            if timing and not w.graph:
+                for nm, (ms, c) in plan.kernel_times().items():
+                    a = ktimes.setdefault(nm, [0.0, 0]); a[0] += ms; a[1] += c
+            launches += plan.status()["last_launches"]
         torch.cuda.synchronize(dev)
         if ws > 1:
             torch.distributed.barrier()
-        if timing:
-            p.timing(False)
-        ms = [a.elapsed_time(b) for a, b in ev]
-        return ms, ktimes, launches
+        if timing and not w.graph:
+            plan.timing(False)
+        return [a.elapsed_time(b) for a, b in ev], ktimes, launches
 
     clk = Clocks(local)
     clk.start()
-    ms, ktimes, launches = timed(plan, args.steps, timing=True)
+    ms, ktimes, launches = timed(w.plan, args.steps, timing=True)
     clocks = clk.stop()
-    st = plan.status()
+    st = w.plan.status()
     total_ms = sum(ms)
     if ws > 1:
         t = torch.tensor([total_ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         total_ms = float(t.item())
-    cells = NX * NY
-    value = ws * cells * TSTEPS * args.steps / (total_ms * 1e-3) / 1e9
+    value = ws * w.cells_per_step() * args.steps / (total_ms * 1e-3) / 1e9
 
-    # unfused GPU form, same workload and protocol
-    uplan = H.Plan(H.godunov_dag(cfl=CFL), [grid], H.HFAV_F64, H.HFAV_BC_PERIODIC, "unfused")
-    for _ in range(2):
-        uplan.run(ins, outs, TSTEPS)
-    ums, _, _ = timed(uplan, args.steps)
-    uvalue = cells * TSTEPS * args.steps / (sum(ums) * 1e-3) / 1e9
+    extra = {}
+    up = w.unfused_plan(H)
+    if up is not None:
+        for _ in range(2):
+            w.run(up)
+        ums, _, _ = timed(up, args.steps)
+        uvalue = w.cells_per_step() * args.steps / (sum(ums) * 1e-3) / 1e9
+        extra["unfused"] = {"value": uvalue, "ms_per_step": sum(ums) / len(ums)}
+        extra["speedup_vs_unfused"] = value / ws / uvalue
+        del up
+    if w.graph:
+        # the same batch through plain launches (no graph), for the launch overhead
+        w.graph = False
+        for _ in range(2):
+            w.run(w.plan)
+        pms, ktimes, _ = timed(w.plan, max(2, args.steps // 2), timing=True)
+        w.graph = True
+        extra["no_graph"] = {"value": w.cells_per_step() * len(pms) / (sum(pms) * 1e-3) / 1e9,
+                             "ms_per_step": sum(pms) / len(pms)}
 
     # end to end through the public API: pinned host state in, result out
-    hin = [torch.from_numpy(U[f].copy()).pin_memory() for f in range(4)]
-    hout = [torch.empty_like(h).pin_memory() for h in hin]
-    e2e_ms = []
-    for k in range(args.steps + 1):
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        for f in range(4):
-            ins[f].copy_(hin[f], non_blocking=True)
-        plan.run(ins, outs, TSTEPS)
-        for f in range(4):
-            hout[f].copy_(outs[f], non_blocking=True)
-        torch.cuda.synchronize(dev)
-        if k:
-            e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_value = cells * TSTEPS * len(e2e_ms) / (sum(e2e_ms) * 1e-3) / 1e9
-    bytes_io = 4 * cells * 8
+    e2e = None
+    host, ins, outs = w.io()
+    if host is not None:
+        hin = [torch.from_numpy(host[f].copy()).to(ins[0].dtype).pin_memory() for f in range(4)]
+        hout = [torch.empty_like(h).pin_memory() for h in hin]
+        e2e_ms = []
+        for k in range(args.steps + 1):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            for f in range(4):
+                ins[f].copy_(hin[f], non_blocking=True)
+            w.run(w.plan)
+            for f in range(4):
+                hout[f].copy_(outs[f], non_blocking=True)
+            torch.cuda.synchronize(dev)
+            if k:
+                e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        nbytes = sum(h.numel() * h.element_size() for h in hin)
+        e2e = {"value": w.cells_per_step() * len(e2e_ms) / (sum(e2e_ms) * 1e-3) / 1e9, "unit": UNIT,
+               "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+    else:
+        u, out = getattr(w, "u", None), getattr(w, "out", None)
+        if u is not None:
+            hu = u.cpu().pin_memory(); ho = torch.empty_like(hu).pin_memory()
+            e2e_ms = []
+            for k in range(args.steps + 1):
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                u.copy_(hu, non_blocking=True)
+                w.run(w.plan)
+                ho.copy_(out, non_blocking=True)
+                torch.cuda.synchronize(dev)
+                if k:
+                    e2e_ms.append(1e3 * (time.perf_counter() - t0))
+            nb = hu.numel() * hu.element_size()
+            e2e = {"value": w.cells_per_step() * len(e2e_ms) / (sum(e2e_ms) * 1e-3) / 1e9, "unit": UNIT,
+                   "h2d_bytes_per_step": nb, "d2h_bytes_per_step": nb}
 
-    # roofline of the dominant kernel (per-launch device time from the in-run events)
-    dom = max(ktimes, key=lambda k: ktimes[k][0])
-    dom_ms = ktimes[dom][0] / ktimes[dom][1]
-    cpu = None
-    it_avg = 2.08
+    cpu, it_avg = None, 2.06
     if rank == 0 and not args.no_cpu_baseline:
-        import oracle
-        oracle.build()
-        v, secs, it_avg = oracle_sample(512)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"512x512 Sod-like seed {SEED}, {TSTEPS} steps ({secs:.1f} s, single thread)"}
-    per_cell = {"gsweep_x": flops_per_cell_sweep(it_avg), "gsweep_y": flops_per_cell_sweep(it_avg) + CFL_FLOPS,
-                "gfull": 2 * flops_per_cell_sweep(it_avg) + CFL_FLOPS}.get(dom, flops_per_cell_sweep(it_avg))
-    achieved = per_cell * cells / (dom_ms * 1e-3) / 1e9
-    pk = peaks()
-    hbm = pk.get("hbm_gbs", 6787.6)
-    fused_bytes = (128 if best.startswith("sweep") else 64) * cells * TSTEPS   # compulsory, per bench step
-    hbm_frac = fused_bytes / (total_ms / args.steps * 1e-3) / 1e9 / hbm
+        v, secs, it, sample = oracle_sample(name)
+        it_avg = it or it_avg
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"{sample} ({secs:.1f} s)"}
+
+    roof = None
+    if ktimes:
+        dom = max(ktimes, key=lambda k: ktimes[k][0])
+        dom_ms = ktimes[dom][0] / ktimes[dom][1]
+        bound, work, unit, peak, src = w.kernel_work(dom, it_avg)
+        achieved = work / (dom_ms * 1e-3) / 1e9
+        roof = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
+                "frac": achieved / peak, "traffic": None, "peak_source": src, "launch_ms": dom_ms,
+                "work_per_launch": work}
+    hbm = peaks().get("hbm_gbs", 6787.6)
+    cb = w.compulsory_bytes(best)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "grid": [NX, NY], "time_steps_per_step": TSTEPS, "cfl": CFL,
-                   "schedule": best, "l2": "flushed (256 MiB write) between timed steps",
+        "dtype": w.dtype, "data": "synthetic",
+        "config": {"workload": w.name, "schedule": best, "l2": "flushed (256 MiB write) between timed steps",
                    "parallelism": "replicas" if ws > 1 else "single GPU"},
-        "unfused": {"value": uvalue, "ms_per_step": sum(ums) / len(ums)},
-        "speedup_vs_unfused": value / ws / uvalue,
-        "hbm_roofline": {"compulsory_bytes_per_step": fused_bytes, "frac": hbm_frac, "peak_gbs": hbm,
-                         "note": "of measured copy bandwidth; FP64 arithmetic, not HBM, binds this workload"},
-        "roofline": {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": PEAK_FP64_GFLOPS,
-                     "unit": "GFLOP/s", "frac": achieved / PEAK_FP64_GFLOPS, "traffic": None,
-                     "peak_source": "FP64 DFMA rate measured by the repo's probe (nominal 1250)",
-                     "flops_per_cell": per_cell, "newton_iters_per_face": it_avg, "launch_ms": dom_ms},
+        **extra,
+        "hbm_roofline": {"compulsory_bytes_per_step": cb, "frac": cb / (total_ms / args.steps * 1e-3) / 1e9 / hbm,
+                         "peak_gbs": hbm, "of": "measured"},
+        "roofline": roof,
         "kernels": {k: {"ms_total": v[0], "launches": v[1]} for k, v in ktimes.items()},
         "cpu_baseline": cpu,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bytes_io, "d2h_bytes_per_step": bytes_io},
+        "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clocks,
         "status": {"newton_nonconverged": st["newton_nonconverged"], "nonphysical": st["nonphysical"]},
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def _axg(w):
+    if isinstance(w, Chain):
+        return [w.u], [w.out]
+    return w.ins, w.outs
+
+
+def _nsteps(w):
+    return 1 if isinstance(w, Chain) else w.tsteps
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="godunov1024_f64", choices=WORKLOADS + ["all"])
+    ap.add_argument("--schedule", default=None, help="fixed schedule (default: autotuned among fused ones)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--once", action="store_true", help="profiling case: build the plan and run it once")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        if args.workload == "all":
+            args.workload = "godunov1024_f64"
+        return run_reference(args)
+    if args.once:
+        return run_once(args)
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        torch.cuda.set_device(local)
+        torch.distributed.init_process_group("nccl")
+    dev = torch.device(f"cuda:{local}" if ws > 1 else "cuda:0")
+    torch.cuda.set_device(dev)
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1710_08774_gb300 import hfav as H
+    from paper_1710_08774_gb300 import inputs as I
+    names = WORKLOADS if args.workload == "all" else [args.workload]
+    for nm in names:
+        bench(args, nm, torch, H, I, dev, ws, rank, local)
+        torch.cuda.empty_cache()
     if ws > 1:
         torch.distributed.destroy_process_group()
 
