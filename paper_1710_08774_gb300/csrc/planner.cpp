@@ -779,45 +779,74 @@ std::string dump_json(const hfav_plan_t* p) {
     return o.str();
 }
 
-// Features for the learned schedule model (all O(1) floats, log-scaled sizes).
+// Features for the learned schedule model.  They are the terms of a simple
+// cost model of the schedule -- logs of the times its compulsory HBM bytes,
+// its FP64 and FP32 operations (with the tile's halo recompute) and its
+// on-chip staging would take at this GPU's measured rates, its launch count
+// -- plus one-hot fusion / placement and the tile shape.  Expressed in time,
+// they carry over between DAG families and dimensions (a 2D training set and
+// a 3D held-out chain) better than raw sizes do.
 void features(const hfav_plan_t* p, const Schedule& s, float* f) {
     for (int k = 0; k < HFAV_N_FEATURES; ++k) f[k] = 0.f;
     const Dag& d = p->dag;
     double cells = 0;
     for (auto& g : p->grids) cells += (double)g.extent[0] * g.extent[1] * g.extent[2];
     if (cells <= 0) cells = 1;
-    int n_inter = 0, n_rolling = 0;
-    for (auto& fi : p->an.field) {
+    const bool f64 = p->dtype == HFAV_F64;
+    const double es = f64 ? 8.0 : 4.0;
+    int n_inter = 0;
+    for (auto& fi : p->an.field)
         if (fi.storage == HFAV_STORE_ROLLING || fi.storage == HFAV_STORE_HBM) n_inter++;
-        if (fi.storage == HFAV_STORE_ROLLING) n_rolling++;
+    const double R = p->an.max_radius;
+    const int depth = p->an.max_depth;
+    const int tiled = d.ndim - 1;   // axes the CTA tile covers (the stream axis is not tiled)
+    double ops64 = 0, ops32 = 0, bytes = 0, staged = 0, launches = 1, halo = 0;
+    if (p->pipeline == PIPE_GODUNOV) {
+        const double it = 2.06, sweep = 155.0 + 40.0 * it;
+        if (f64) ops64 = 2 * sweep + 16;
+        else { ops64 = 2 * 36.0 * it; ops32 = 2 * sweep + 16 - ops64; }
+        bytes = s.fusion == FUSE_FULL ? 8 * es : s.fusion == FUSE_SWEEP ? 16 * es : 74 * es;
+        staged = s.fusion == FUSE_UNFUSED ? 0 : 13 * es;
+        launches = s.fusion == FUSE_FULL ? 1 : s.fusion == FUSE_SWEEP ? 2 : 19;
+        halo = s.fusion == FUSE_FULL ? 2.0 : 0.5;
+    } else {
+        const double ops = p->pipeline == PIPE_CHAIN3D ? 26.0 : p->pipeline == PIPE_CHAIN2D ? 14.0 : 8.0 * d.rules.size();
+        (f64 ? ops64 : ops32) = ops;
+        const double io = (double)(d.axioms.size() + d.goals.size()) * es;
+        bytes = s.fusion == FUSE_FULL ? io : s.fusion == FUSE_SWEEP ? io + 2 * es : io + 2 * es * n_inter;
+        // values staged on chip per cell: every stencil reference of a fused stage
+        double refs = 0;
+        for (auto& r : d.rules) refs += r.in.size();
+        staged = s.fusion == FUSE_UNFUSED ? 0 : refs * es;
+        launches = s.fusion == FUSE_FULL ? 1 : s.fusion == FUSE_SWEEP ? 2 : (double)d.rules.size();
+        halo = s.fusion == FUSE_FULL ? R * (depth - 1) : s.fusion == FUSE_SWEEP ? R : 0.0;
     }
-    double esz = p->dtype == HFAV_F64 ? 8.0 : 4.0;
-    double compulsory = (double)(d.axioms.size() + d.goals.size()) * esz;   // bytes per cell
-    double unfused_bytes = compulsory + 2.0 * n_inter * esz;
-    double bytes = s.fusion == FUSE_UNFUSED ? unfused_bytes
-                   : s.fusion == FUSE_SWEEP ? compulsory * 2.0 : compulsory;
-    // recompute ratio of a TX x TY tile with halo r along both tiled axes
-    double r = p->an.max_radius * (p->an.max_depth > 1 ? p->an.max_depth - 1 : 1);
-    double tx = s.tx, ty = s.ty;
-    double recompute = s.fusion == FUSE_UNFUSED ? 1.0 : ((tx + 2 * r) * (ty * 8 + 2 * r)) / (tx * ty * 8);
-    bool fp64_heavy = p->pipeline == PIPE_GODUNOV || p->dtype == HFAV_F64;
-    f[0] = (float)p->an.max_depth / 10.f;
-    f[1] = (float)p->an.max_radius / 3.f;
-    f[2] = (float)d.n_fields / 32.f;
-    f[3] = (float)(std::log2(cells) / 20.0);
-    f[4] = p->dtype == HFAV_F64 ? 1.f : 0.f;
+    double rec = 1.0;
+    if (s.fusion != FUSE_UNFUSED) {
+        rec = (s.tx + 2 * halo) / s.tx;
+        if (tiled >= 2) rec *= (s.ty + 2 * halo) / s.ty;
+    }
+    const double us = 1e6;
+    const double t_hbm = bytes * cells / 6.8e12 * us;
+    const double t64 = ops64 * rec * cells / 5.9e11 * us;
+    const double t32 = ops32 * rec * cells / 6.9e13 * us;
+    const double t_chip = staged * rec * cells / 3.0e13 * us;
+    f[0] = (float)(std::log2(cells) / 24.0);
+    f[1] = (float)(std::log2(1.0 + t_hbm) / 16.0);
+    f[2] = (float)(std::log2(1.0 + t64) / 16.0);
+    f[3] = (float)(std::log2(1.0 + t32) / 16.0);
+    f[4] = (float)(std::log2(1.0 + t_chip) / 16.0);
     f[5] = s.fusion == FUSE_FULL ? 1.f : 0.f;
     f[6] = s.fusion == FUSE_SWEEP ? 1.f : 0.f;
     f[7] = s.fusion == FUSE_UNFUSED ? 1.f : 0.f;
     f[8] = s.placement == PLACE_REG ? 1.f : 0.f;
     f[9] = s.placement == PLACE_SMEM ? 1.f : 0.f;
-    f[10] = (float)(std::log2(tx) / 7.0);
-    f[11] = (float)(std::log2(ty) / 3.0);
-    f[12] = (float)(std::log2(bytes * cells) / 36.0);
-    f[13] = (float)recompute - 1.f;
-    f[14] = (float)d.ndim / 3.f;
-    f[15] = fp64_heavy ? 1.f : 0.f;
-    (void)n_rolling;
+    f[10] = (float)(std::log2(launches) / 5.0);
+    f[11] = (float)(std::log2((double)s.tx * s.ty) / 8.0);
+    f[12] = (float)(std::log2((double)s.tx / s.ty) / 6.0);
+    f[13] = (float)(std::log2(rec) / 2.0);
+    f[14] = (float)R / 3.f;
+    f[15] = f64 ? 1.f : 0.f;
 }
 
 }  // namespace hfav

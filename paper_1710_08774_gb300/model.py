@@ -1,0 +1,206 @@
+"""Learned schedule model: corpus collection, training and schedule choice.
+
+The model is the 3-layer MLP of ``csrc/mlp.cu`` (16 plan features -> 64 ->
+64 -> 1, ReLU, FP32) predicting the natural log of a schedule's time per
+time step.  Everything numeric runs in the library's CUDA kernels:
+
+  * the timings of the corpus come from ``hfav_autotune`` (every valid
+    schedule of a plan, CUDA events, L2 flushed between repetitions);
+  * the features of a (plan, schedule) pair from ``hfav_plan_features``;
+  * training is ``hfav_mlp_train`` (full-batch MSE, Adam) on the GPU;
+  * the choice is ``hfav_model_choose`` (forward over every valid schedule,
+    argmin installed as the plan's schedule).
+
+This module only lays out the corpus (which workloads of the 2D chain and
+Godunov families, at which sizes) and moves arrays between them.  The
+corpus stores workload descriptors and measured times, not features, so
+features are recomputed from the planner when the model is trained.
+"""
+import csv
+import os
+
+import numpy as np
+
+from . import hfav as H
+from . import inputs as I
+
+DATA = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data")
+CORPUS = os.path.join(DATA, "corpus_gb300.csv")
+HIDDEN = 64
+FIELDS = ["family", "dtype", "nx", "ny", "nz", "n_grids", "steps", "schedule", "ms"]
+
+
+# ---------------------------------------------------------------------------
+# workloads of the training families (2D chain, Godunov, batches of Godunov)
+# ---------------------------------------------------------------------------
+def corpus_workloads():
+    w = []
+    for dt in ("f64", "f32"):
+        for n in (64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048, 3072, 4096, 6144, 8192):
+            w.append(("chain2d", dt, n, n, 1, 1, 1))
+        for nx, ny in ((4096, 256), (256, 4096), (2048, 512)):
+            w.append(("chain2d", dt, nx, ny, 1, 1, 1))
+    for n in (64, 96, 128, 192, 256, 384, 512, 768, 1024, 1536, 2048):
+        w.append(("godunov", "f64", n, n, 1, 1, 2))
+    for n in (64, 128, 256, 512, 1024, 2048, 4096):
+        w.append(("godunov", "f32", n, n, 1, 1, 2))
+    for nx, ny in ((128, 2048), (2048, 128), (1000, 300)):
+        w.append(("godunov", "f64", nx, ny, 1, 1, 2))
+        w.append(("godunov", "f32", nx, ny, 1, 1, 2))
+    for seed in (11, 12, 13):
+        w.append(("batch", "f32", seed, 0, 1, 8, 2))
+    return w
+
+
+def _dag(family):
+    return {"chain2d": H.chain2d_dag, "chain3d": H.chain3d_dag}.get(family, H.godunov_dag)()
+
+
+def plan_for(family, dtype, nx, ny, nz, n_grids, device_arrays=False):
+    """Plan of a workload; with device_arrays also the (axioms, goals) tensors."""
+    hdt = H.HFAV_F64 if dtype == "f64" else H.HFAV_F32
+    if family in ("chain2d", "chain3d"):
+        halo = 2 if family == "chain2d" else 3
+        shape = (ny + 2 * halo, nx + 2 * halo) if family == "chain2d" else \
+            (nz + 2 * halo, ny + 2 * halo, nx + 2 * halo)
+        grid = H.Grid.make([nx, ny, nz][:len(shape)], [1] + [int(np.prod(shape[len(shape) - a:])) for a in
+                                                              range(1, len(shape))], halo)
+        plan = H.Plan(_dag(family), [grid], hdt, H.HFAV_BC_PERIODIC, "full:reg:32x4")
+        if not device_arrays:
+            return plan, None
+        import torch
+        td = torch.float64 if dtype == "f64" else torch.float32
+        if family == "chain2d":
+            u = torch.from_numpy(I.chain2d_input(nx, seed=0, ny=ny)).to(td).cuda()
+        else:
+            u = torch.from_numpy(I.chain3d_input(nx, seed=4, dtype=np.float32 if dtype == "f32" else np.float64)).cuda()
+        return plan, ([u], [torch.empty_like(u)])
+    if family == "batch":
+        sides = I.batch_sides(n_grids, seed=nx, lo=128, hi=1024)
+    else:
+        sides = [(nx, ny)]
+    grids = [H.Grid.make((a, b), (1, a), 0) for a, b in sides]
+    plan = H.Plan(H.godunov_dag(), grids, hdt, H.HFAV_BC_PERIODIC, "sweep:reg:32x4")
+    if not device_arrays:
+        return plan, None
+    import torch
+    td = torch.float64 if dtype == "f64" else torch.float32
+    ins, outs = [], []
+    for g, (a, b) in enumerate(sides):
+        U = I.sod_state(a, b, seed=1, grid=g)
+        t = [torch.from_numpy(U[f].copy()).to(td).cuda() for f in range(4)]
+        ins.append(t)
+        outs.append([torch.empty_like(x) for x in t])
+    return plan, (ins, outs)
+
+
+def measure(family, dtype, nx, ny, nz, n_grids, steps, reps=2):
+    """{schedule: ms per time step} of every valid schedule (hfav_autotune)."""
+    import torch
+    plan, (ax, go) = plan_for(family, dtype, nx, ny, nz, n_grids, device_arrays=True)
+    times = plan.autotune(ax, go, n_steps=steps, reps=reps)
+    torch.cuda.synchronize()
+    out = {k: v / steps for k, v in times.items() if v > 0}
+    plan.free()
+    del ax, go
+    torch.cuda.empty_cache()
+    return out
+
+
+def collect(path=CORPUS, workloads=None, log=print):
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    rows = []
+    for wl in workloads or corpus_workloads():
+        fam, dt, nx, ny, nz, ng, steps = wl
+        t = measure(fam, dt, nx, ny, nz, ng, steps)
+        for sch, ms in t.items():
+            rows.append(dict(zip(FIELDS, [fam, dt, nx, ny, nz, ng, steps, sch, ms])))
+        log(f"{fam} {dt} {nx}x{ny}x{nz} grids={ng}: {len(t)} schedules, best {min(t, key=t.get)} "
+            f"{min(t.values()):.4f} ms/step")
+    with open(path, "w", newline="") as f:
+        wr = csv.DictWriter(f, fieldnames=FIELDS)
+        wr.writeheader()
+        wr.writerows(rows)
+    return rows
+
+
+def load_corpus(path=CORPUS):
+    with open(path) as f:
+        return list(csv.DictReader(f))
+
+
+def features_of(rows):
+    """Feature matrix (n x 16) and log-time targets of corpus rows (host planner only)."""
+    X, y = [], []
+    cache = {}
+    for r in rows:
+        key = (r["family"], r["dtype"], int(r["nx"]), int(r["ny"]), int(r["nz"]), int(r["n_grids"]))
+        if key not in cache:
+            cache[key] = plan_for(*key)[0]
+        X.append(cache[key].features(r["schedule"]))
+        y.append(np.log(float(r["ms"])))
+    return np.array(X, dtype=np.float32), np.array(y, dtype=np.float32)
+
+
+# ---------------------------------------------------------------------------
+# training and choice
+# ---------------------------------------------------------------------------
+class Model:
+    def __init__(self, params, shift, scale, hidden=HIDDEN, losses=None):
+        self.params, self.shift, self.scale, self.hidden = params, shift, scale, hidden
+        self.losses = losses
+
+    def predict(self, X):
+        import torch
+        Xn = torch.from_numpy(((X - self.shift) * self.scale).astype(np.float32)).cuda()
+        y = torch.empty(Xn.shape[0], dtype=torch.float32, device="cuda")
+        H.mlp_forward(self.params, Xn, self.hidden, y)
+        torch.cuda.synchronize()
+        return y.cpu().numpy()
+
+    def choose(self, plan):
+        """Install the predicted-fastest schedule on the plan; returns (schedule, {schedule: prediction})."""
+        return plan.model_choose(self.params, self.hidden, self.shift, self.scale)
+
+    def save(self, path):
+        np.savez(path, params=self.params.cpu().numpy(), shift=self.shift, scale=self.scale, hidden=self.hidden)
+
+    @staticmethod
+    def load(path):
+        import torch
+        z = np.load(path)
+        return Model(torch.from_numpy(z["params"]).cuda(), z["shift"], z["scale"], int(z["hidden"]))
+
+
+def init_params(n_in, hidden, seed=0):
+    """He-initialised parameters in the layout of csrc/mlp.cu (seeded)."""
+    rng = np.random.default_rng(seed)
+    W1 = rng.normal(0, np.sqrt(2.0 / n_in), (hidden, n_in))
+    W2 = rng.normal(0, np.sqrt(2.0 / hidden), (hidden, hidden))
+    w3 = rng.normal(0, np.sqrt(1.0 / hidden), hidden)
+    return np.concatenate([W1.ravel(), np.zeros(hidden), W2.ravel(), np.zeros(hidden), w3, [0.0]]).astype(np.float32)
+
+
+def train(X, y, hidden=HIDDEN, epochs=4000, lr=3e-3, seed=0):
+    """Full-batch Adam on the GPU (hfav_mlp_train).  Returns a Model."""
+    import torch
+    shift = X.mean(axis=0)
+    sd = X.std(axis=0)
+    scale = np.where(sd > 1e-6, 1.0 / np.maximum(sd, 1e-6), 1.0).astype(np.float32)
+    Xn = torch.from_numpy(((X - shift) * scale).astype(np.float32)).cuda()
+    t = torch.from_numpy(y.astype(np.float32)).cuda()
+    p = torch.from_numpy(init_params(X.shape[1], hidden, seed)).cuda()
+    m = torch.zeros_like(p); v = torch.zeros_like(p); g = torch.zeros_like(p)
+    work = torch.empty(H.mlp_work_floats(X.shape[0], hidden), dtype=torch.float32, device="cuda")
+    losses = torch.empty(epochs, dtype=torch.float32, device="cuda")
+    H.mlp_train(p, m, v, Xn, t, hidden, epochs, lr, work, g, losses)
+    torch.cuda.synchronize()
+    return Model(p, shift.astype(np.float32), scale, hidden, losses.cpu().numpy())
+
+
+if __name__ == "__main__":
+    import sys
+    import torch
+    assert torch.cuda.is_available()
+    out = sys.argv[1] if len(sys.argv) > 1 else CORPUS
+    collect(out)

@@ -1,0 +1,104 @@
+"""The learned schedule model's CUDA kernels and its choice on the held-out workload.
+
+- forward, MSE gradient and Adam step of the hand-written FP32 kernels against
+  the FP64 numpy oracle (oracle/mlp.py): gradient normwise relative error
+  <= 1e-4, forward and Adam <= 1e-5;
+- full-batch training on the GPU lowers the loss on a synthetic target;
+- trained on the measured corpus of the 2D chain and Godunov families
+  (paper_1710_08774_gb300/data/corpus_gb300.csv), the model's pick for the
+  held-out 3D four-stage 7-point chain over 512^3 FP32 is within 10% of the
+  exhaustively tuned best (timed live here), and the test reports what it
+  gains over the default schedule without the model.
+"""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+from oracle import mlp as M
+from paper_1710_08774_gb300 import hfav as H
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(n=257, n_in=16, hidden=64, seed=0):
+    import torch
+    rng = np.random.default_rng(seed)
+    p = (rng.normal(0, 0.3, M.n_params(n_in, hidden))).astype(np.float32)
+    X = rng.normal(size=(n, n_in)).astype(np.float32)
+    t = rng.normal(size=n).astype(np.float32)
+    return p, X, t, torch.from_numpy(p).cuda(), torch.from_numpy(X).cuda(), torch.from_numpy(t).cuda()
+
+
+def test_forward_matches_oracle():
+    import torch
+    p, X, t, dp, dX, dt = _setup()
+    y = torch.empty(X.shape[0], dtype=torch.float32, device="cuda")
+    H.mlp_forward(dp, dX, 64, y)
+    ref = M.forward(p.astype(np.float64), X.astype(np.float64), 64)
+    got = y.cpu().numpy()
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) <= 1e-5
+
+
+def test_gradient_matches_oracle():
+    import torch
+    p, X, t, dp, dX, dt = _setup()
+    g = torch.empty_like(dp)
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    work = torch.empty(H.mlp_work_floats(X.shape[0], 64), dtype=torch.float32, device="cuda")
+    H.mlp_loss_grad(dp, dX, dt, 64, g, loss, work)
+    rl, rg = M.loss_grad(p.astype(np.float64), X.astype(np.float64), t.astype(np.float64), 64)
+    gg = g.cpu().numpy()
+    assert abs(loss.item() - rl) <= 1e-5 * rl
+    assert np.max(np.abs(gg - rg)) / np.max(np.abs(rg)) <= 1e-4
+    # bitwise reproducible (fixed summation order, no atomics)
+    g2 = torch.empty_like(dp)
+    H.mlp_loss_grad(dp, dX, dt, 64, g2, loss, work)
+    assert torch.equal(g, g2)
+
+
+def test_adam_matches_oracle():
+    import torch
+    rng = np.random.default_rng(1)
+    p = rng.normal(size=1000); g = rng.normal(size=1000)
+    m = rng.normal(size=1000) * 0.1; v = np.abs(rng.normal(size=1000)) * 0.1
+    dp, dg, dm, dv = (torch.from_numpy(a.astype(np.float32)).cuda() for a in (p, g, m, v))
+    H.mlp_adam(dp, dg, dm, dv, 1e-2, 3)
+    rp, rm, rv = M.adam(p, g, m, v, 3, lr=1e-2)
+    assert np.max(np.abs(dp.cpu().numpy() - rp)) <= 1e-5 * np.max(np.abs(rp)) + 1e-7
+
+
+def test_training_reduces_loss():
+    from paper_1710_08774_gb300 import model
+    rng = np.random.default_rng(2)
+    X = rng.uniform(-1, 1, size=(600, 16)).astype(np.float32)
+    y = (np.sin(2 * X[:, 0]) + X[:, 1] * X[:, 2] + 0.5 * X[:, 3] ** 2).astype(np.float32)
+    mdl = model.train(X, y, epochs=1500, lr=3e-3)
+    assert mdl.losses[-1] < 0.05 * mdl.losses[0]
+    pred = mdl.predict(X)
+    assert np.mean((pred - y) ** 2) < 0.05 * np.var(y)
+
+
+def test_model_choice_on_heldout_3d_chain():
+    import torch
+    from paper_1710_08774_gb300 import model
+    if not os.path.exists(model.CORPUS):
+        pytest.skip("no measured corpus")
+    rows = model.load_corpus()
+    X, y = model.features_of(rows)
+    assert len(rows) >= 1500
+    mdl = model.train(X, y, epochs=4000, lr=3e-3)
+    # held-out: 3D 4-stage 7-point chain, 512^3 FP32, exhaustive tuning as judge
+    plan, (ax, go) = model.plan_for("chain3d", "f32", 512, 512, 512, 1, device_arrays=True)
+    times = plan.autotune(ax, go, n_steps=1, reps=3)
+    times = {k: v for k, v in times.items() if v > 0}
+    best = min(times.values())
+    pick, pred = mdl.choose(plan)
+    default = "full:reg:32x4"
+    ratio = times[pick] / best
+    gain = times[default] / times[pick]
+    print(f"\nheld-out chain3d 512^3 fp32: exhaustive best {min(times, key=times.get)} {best:.4f} ms; "
+          f"model pick {pick} {times[pick]:.4f} ms (x{ratio:.3f} of best); default {default} "
+          f"{times[default]:.4f} ms (model gains x{gain:.3f})")
+    assert ratio <= 1.10
