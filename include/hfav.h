@@ -234,6 +234,9 @@ int hfav_plan_dump(const hfav_plan_t* plan, char* buf, size_t n);
  * HFAV_N_FEATURES floats (DAG depth, stencil radius, field count, log cells,
  * dtype, fusion, placement, tile, compulsory bytes, recompute ratio ...). */
 #define HFAV_N_FEATURES 16
+/* feature HFAV_FEATURE_BASE holds log2(analytic time estimate in us) / 16;
+ * the learned model predicts ln(time) minus ln of that estimate */
+#define HFAV_FEATURE_BASE 12
 int hfav_plan_features(const hfav_plan_t* plan, const char* schedule, float* feat);
 
 /* ---- execution ------------------------------------------------------- */
@@ -360,9 +363,10 @@ int hfav_mlp_train(float* params, float* m, float* v, int n_in, int hidden, cons
 
 /* Learned schedule choice: features of every valid schedule of the plan
  * (hfav_plan_features, then (f - shift) * scale per feature when the host
- * arrays are given), the network's predicted cost of each (pred, host, n_pred
- * entries in hfav_plan_variants order), and the argmin installed as the
- * plan's schedule and copied to `best`.  Synchronises the default stream. */
+ * arrays are given), the predicted ln(time) of each -- the network's output
+ * plus ln of the analytic estimate in feature HFAV_FEATURE_BASE -- (pred,
+ * host, n_pred entries in hfav_plan_variants order), and the argmin installed
+ * as the plan's schedule and copied to `best`.  Synchronises the default stream. */
 int hfav_model_choose(hfav_plan_t* plan, const float* params, int hidden, const float* feat_shift,
                       const float* feat_scale, float* pred, int n_pred, char* best, size_t n_best);
 

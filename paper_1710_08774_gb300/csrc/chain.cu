@@ -476,6 +476,191 @@ __global__ void __launch_bounds__(256) chain3d_ring(const C3Args a) {
     }
 }
 
+// register-window form (placement reg): the CTA's TX x TY threads own an
+// output tile TX x (TY*M), M = 16 / TY.  Every stage keeps, for each position
+// a thread computes, the window of its input along k in registers (three
+// planes), so only the in-plane neighbours of the previous stage go through
+// one shared plane buffer per stage (double-buffered).  Positions and their
+// shared / global offsets are fixed per thread and computed once: no integer
+// division and no periodic wrap arithmetic inside the k loop.
+template <int TX, int TY>
+struct C3Tile {
+    static constexpr int NT = TX * TY, M = 16 / TY > 0 ? 16 / TY : 1, TYO = TY * M;
+    static constexpr int WU = TX + 6, HU = TYO + 6, PU = WU * HU;
+    static constexpr int W1 = TX + 4, H1 = TYO + 4, P1 = W1 * H1;
+    static constexpr int W2 = TX + 2, H2 = TYO + 2, P2 = W2 * H2;
+    static constexpr int NU = (PU + NT - 1) / NT, N1 = (P1 + NT - 1) / NT, N2 = (P2 + NT - 1) / NT;
+};
+
+template <typename T, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a) {
+    using G = C3Tile<TX, TY>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* U = (T*)smem_raw;          // [2][PU]
+    T* S1 = U + 2 * G::PU;        // [2][P1]
+    T* S2 = S1 + 2 * G::P1;       // [2][P2]
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * G::TYO, k0 = blockIdx.z * a.K;
+    const T* u = (const T*)a.u.p;
+    // u positions: shared offset and global in-plane offset (wrapped / halo-given)
+    int64_t gu[G::NU];
+    int su[G::NU];
+    bool vu[G::NU];
+#pragma unroll
+    for (int r = 0; r < G::NU; ++r) {
+        const int q = tid + r * G::NT;
+        vu[r] = q < G::PU;
+        const int cj = q / G::WU, ci = q - cj * G::WU;
+        su[r] = q;
+        int gi = i0 - 3 + ci, gj = j0 - 3 + cj;
+        if (a.u.wrap) {
+            gi = wrap_idx(gi, a.nx);
+            gj = wrap_idx(gj, a.ny);
+        } else {
+            gi = min(max(gi, -3), a.nx + 2);
+            gj = min(max(gj, -3), a.ny + 2);
+        }
+        gu[r] = (int64_t)(gj + a.u.org[1]) * a.u.pitch[1] + (gi + a.u.org[0]);
+    }
+    // s1 / s2 positions: offsets into their own plane and into the plane below
+    int o1[G::N1], b1[G::N1];
+    bool v1[G::N1];
+#pragma unroll
+    for (int r = 0; r < G::N1; ++r) {
+        const int q = tid + r * G::NT;
+        v1[r] = q < G::P1;
+        const int cj = q / G::W1, ci = q - cj * G::W1;
+        o1[r] = q;
+        b1[r] = (cj + 1) * G::WU + (ci + 1);   // same point in the u plane
+    }
+    int o2[G::N2], b2[G::N2];
+    bool v2[G::N2];
+#pragma unroll
+    for (int r = 0; r < G::N2; ++r) {
+        const int q = tid + r * G::NT;
+        v2[r] = q < G::P2;
+        const int cj = q / G::W2, ci = q - cj * G::W2;
+        o2[r] = q;
+        b2[r] = (cj + 1) * G::W1 + (ci + 1);   // same point in the s1 plane
+    }
+    // output positions: thread (tx, ty) owns rows ty + TY m
+    T wu[G::N1][3], w1[G::N2][3], w2[G::M][3];
+#pragma unroll
+    for (int r = 0; r < G::N1; ++r) wu[r][0] = wu[r][1] = wu[r][2] = (T)0;
+#pragma unroll
+    for (int r = 0; r < G::N2; ++r) w1[r][0] = w1[r][1] = w1[r][2] = (T)0;
+#pragma unroll
+    for (int m = 0; m < G::M; ++m) w2[m][0] = w2[m][1] = w2[m][2] = (T)0;
+    const T c1 = (T)a.a1[0], p1 = (T)a.a1[1], m1 = (T)a.a1[2], q1 = (T)a.a1[3], n1 = (T)a.a1[4];
+    const T kp1 = (T)a.a1[5], km1 = (T)a.a1[6];
+    const T c2 = (T)a.a2[0], p2 = (T)a.a2[1], m2 = (T)a.a2[2], q2 = (T)a.a2[3], n2 = (T)a.a2[4];
+    const T kp2 = (T)a.a2[5], km2 = (T)a.a2[6];
+    for (int kk = k0 - 3; kk <= k0 + a.K + 2; ++kk) {
+        const int buf = kk & 1;
+        // load the u plane kk
+        int kw = kk;
+        if (a.u.wrap) kw = wrap_idx(kk, a.nz);
+        else kw = min(max(kk, -3), a.nz + 2);
+        const int64_t kb = (int64_t)(kw + a.u.org[2]) * a.u.pitch[2];
+        T* Ub = U + buf * G::PU;
+#pragma unroll
+        for (int r = 0; r < G::NU; ++r)
+            if (vu[r]) Ub[su[r]] = u[kb + gu[r]];
+        __syncthreads();
+        // s1 at plane kk-1: k-neighbours from the register window, in-plane from the u plane kk-1
+        if (kk >= k0 - 1) {
+            const T* Up = U + (buf ^ 1) * G::PU;   // plane kk-1
+            T* S1b = S1 + (buf ^ 1) * G::P1;
+#pragma unroll
+            for (int r = 0; r < G::N1; ++r) {
+                if (!v1[r]) continue;
+                wu[r][0] = wu[r][1]; wu[r][1] = wu[r][2]; wu[r][2] = Ub[b1[r]];
+                const int b = b1[r];
+                T v = p1 * Up[b + 1];
+                v = fma(m1, Up[b - 1], v);
+                v = fma(q1, Up[b + G::WU], v);
+                v = fma(n1, Up[b - G::WU], v);
+                v = fma(kp1, wu[r][2], v);
+                v = fma(km1, wu[r][0], v);
+                S1b[o1[r]] = fma(c1, wu[r][1], v);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < G::N1; ++r)
+                if (v1[r]) { wu[r][0] = wu[r][1]; wu[r][1] = wu[r][2]; wu[r][2] = Ub[b1[r]]; }
+        }
+        __syncthreads();
+        // s2 at plane kk-2 from the s1 planes kk-1 (window) and kk-2 (in-plane);
+        // the window starts with s1(k0-2), produced at kk = k0-1
+        if (kk >= k0 - 1) {
+            const T* S1n = S1 + (buf ^ 1) * G::P1;   // plane kk-1
+            const T* S1p = S1 + buf * G::P1;         // plane kk-2
+            T* S2b = S2 + buf * G::P2;
+            const bool comp = kk >= k0 + 1;
+#pragma unroll
+            for (int r = 0; r < G::N2; ++r) {
+                if (!v2[r]) continue;
+                w1[r][0] = w1[r][1]; w1[r][1] = w1[r][2]; w1[r][2] = S1n[b2[r]];
+                if (!comp) continue;
+                const int b = b2[r];
+                T v = p2 * S1p[b + 1];
+                v = fma(m2, S1p[b - 1], v);
+                v = fma(q2, S1p[b + G::W1], v);
+                v = fma(n2, S1p[b - G::W1], v);
+                v = fma(kp2, w1[r][2], v);
+                v = fma(km2, w1[r][0], v);
+                S2b[o2[r]] = fma(c2, w1[r][1], v);
+            }
+        }
+        __syncthreads();
+        // out at plane kk-3 from the s2 planes kk-2 (window) and kk-3 (in-plane);
+        // the window starts with s2(k0-1), produced at kk = k0+1
+        if (kk >= k0 + 1) {
+            const T* S2n = S2 + buf * G::P2;           // plane kk-2
+            const T* S2p = S2 + (buf ^ 1) * G::P2;     // plane kk-3
+            const int kq = kk - 3;
+#pragma unroll
+            for (int m = 0; m < G::M; ++m) {
+                const int ty = threadIdx.y + TY * m;
+                const int b = (ty + 1) * G::W2 + threadIdx.x + 1;
+                w2[m][0] = w2[m][1]; w2[m][1] = w2[m][2]; w2[m][2] = S2n[b];
+                if (kk >= k0 + 3) {
+                    const T gx = S2p[b + 1] - S2p[b - 1];
+                    const T gy = S2p[b + G::W2] - S2p[b - G::W2];
+                    const T gz = w2[m][2] - w2[m][0];
+                    const T s3 = sqrt(fma(gx, gx, fma(gy, gy, gz * gz))) * (T)0.5;
+                    const int i = i0 + threadIdx.x, j = j0 + ty;
+                    if (i < a.nx && j < a.ny && kq < a.nz) *garr_ptr<T>(a.out, i, j, kq) = s3 / ((T)1 + s3);
+                }
+            }
+        }
+    }
+}
+
+template <typename T, int TX, int TY>
+static int launch_c3regw(hfav_plan_t* p, C3Args& a, cudaStream_t st) {
+    using G = C3Tile<TX, TY>;
+    const size_t sm = (size_t)2 * (G::PU + G::P1 + G::P2) * sizeof(T);
+    int64_t tiles = (int64_t)((a.nx + TX - 1) / TX) * ((a.ny + G::TYO - 1) / G::TYO);
+    int K = 16;
+    while (K < 128 && tiles * ((a.nz + 2 * K - 1) / (2 * K)) >= 152 * 6) K *= 2;
+    a.K = K;
+    dim3 grd((a.nx + TX - 1) / TX, (a.ny + G::TYO - 1) / G::TYO, (a.nz + K - 1) / K);
+    cudaFuncSetAttribute(chain3d_regw<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    chain3d_regw<T, TX, TY><<<grd, dim3(TX, TY), sm, st>>>(a);
+    HFAV_LAUNCHED(p->rt, "chain3d_fused", st);
+    return HFAV_OK;
+}
+
+template <typename T>
+static int launch_c3regw_tile(hfav_plan_t* p, const Schedule& s, C3Args& a, cudaStream_t st) {
+    if (s.tx == 32 && s.ty == 4) return launch_c3regw<T, 32, 4>(p, a, st);
+    if (s.tx == 64 && s.ty == 4) return launch_c3regw<T, 64, 4>(p, a, st);
+    if (s.tx == 128 && s.ty == 2) return launch_c3regw<T, 128, 2>(p, a, st);
+    if (s.tx == 32 && s.ty == 8) return launch_c3regw<T, 32, 8>(p, a, st);
+    return set_error(HFAV_EUNSUPPORTED, "3D chain tile");
+}
+
 // tail of the "sweep" schedule: s2 .. out fused from a materialised s1 (halo 2)
 template <typename T>
 __global__ void __launch_bounds__(256) chain3d_tail(const GArr s1, const GArr out, int nx, int ny, int nz, C3Args a) {
@@ -557,6 +742,8 @@ int launch_chain3d(hfav_plan_t* p, const Schedule& s, void* const* ax, void* con
         HFAV_LAUNCHED(p->rt, "chain3d_tail", st);
         return HFAV_OK;
     }
+    if (s.placement == PLACE_REG)
+        return f64 ? launch_c3regw_tile<double>(p, s, a, st) : launch_c3regw_tile<float>(p, s, a, st);
     // chunk of planes per CTA: enough CTAs to fill the machine
     int64_t tiles = (int64_t)((a.nx + TX - 1) / TX) * ((a.ny + TY - 1) / TY);
     int K = 8;
@@ -572,8 +759,6 @@ int launch_chain3d(hfav_plan_t* p, const Schedule& s, void* const* ax, void* con
         if (f64) chain3d_ring<double, true><<<grd, blk, 0, st>>>(a);
         else chain3d_ring<float, true><<<grd, blk, 0, st>>>(a);
     } else {
-        // reg and smem share the ring kernel: the i/j neighbours of every stage
-        // must be visible across threads, so the rings are in shared memory
         if (per > 200 * 1024) return set_error(HFAV_EUNSUPPORTED, "3D tile too large for shared memory");
         if (f64) {
             cudaFuncSetAttribute(chain3d_ring<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)per);

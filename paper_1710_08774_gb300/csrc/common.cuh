@@ -45,12 +45,22 @@ __host__ __device__ inline int wrap_idx(int a, int n) {
     return r < 0 ? r + n : r;
 }
 
+// periodic wrap without integer division on the common paths: indices of a
+// stencil lie within one period of [0, n); anything further out (the unused
+// tail of a CTA tile wider than the grid) takes the general wrap
+__device__ __forceinline__ int wrap1(int a, int n) {
+    if ((unsigned)a < (unsigned)n) return a;
+    if (a < 0 && a >= -n) return a + n;
+    if (a >= n && a < 2 * n) return a - n;
+    return wrap_idx(a, n);
+}
+
 template <typename T>
 __device__ __forceinline__ T garr_ld(const GArr& a, int i, int j, int k) {
     if (a.wrap) {
-        i = wrap_idx(i, a.ext[0]);
-        j = wrap_idx(j, a.ext[1]);
-        k = wrap_idx(k, a.ext[2]);
+        i = wrap1(i, a.ext[0]);
+        j = wrap1(j, a.ext[1]);
+        k = wrap1(k, a.ext[2]);
     }
     const T* p = (const T*)a.p;
     return p[(int64_t)(k + a.org[2]) * a.pitch[2] + (int64_t)(j + a.org[1]) * a.pitch[1] + (i + a.org[0])];

@@ -206,9 +206,10 @@ int hfav_model_choose(hfav_plan_t* p, const float* params, int hidden, const flo
     if (!p || !params || p->analysis_only) return set_error(HFAV_EINVAL, "bad argument");
     auto vars = valid_schedules(p);
     const int nv = (int)vars.size(), NI = HFAV_N_FEATURES;
-    std::vector<float> X((size_t)nv * NI);
+    std::vector<float> X((size_t)nv * NI), base(nv);
     for (int k = 0; k < nv; ++k) {
         features(p, vars[k], &X[(size_t)k * NI]);
+        base[k] = X[(size_t)k * NI + HFAV_FEATURE_BASE] * 16.f * 0.69314718f;   // ln of the estimate
         for (int f = 0; f < NI; ++f) {
             float sh = feat_shift ? feat_shift[f] : 0.f, sc = feat_scale ? feat_scale[f] : 1.f;
             X[(size_t)k * NI + f] = (X[(size_t)k * NI + f] - sh) * sc;
@@ -228,6 +229,7 @@ int hfav_model_choose(hfav_plan_t* p, const float* params, int hidden, const flo
     cudaFree(dX);
     cudaFree(dy);
     if (rc) return rc;
+    for (int k = 0; k < nv; ++k) y[k] += base[k];
     int arg = (int)(std::min_element(y.begin(), y.end()) - y.begin());
     for (int k = 0; k < nv && k < n_pred; ++k) pred[k] = y[k];
     p->sched = vars[arg];

@@ -800,29 +800,54 @@ void features(const hfav_plan_t* p, const Schedule& s, float* f) {
     const double R = p->an.max_radius;
     const int depth = p->an.max_depth;
     const int tiled = d.ndim - 1;   // axes the CTA tile covers (the stream axis is not tiled)
-    double ops64 = 0, ops32 = 0, bytes = 0, staged = 0, launches = 1, halo = 0;
+    // per cell and time step: FP64 / FP32 operations, compulsory HBM bytes,
+    // on-chip loads (shared memory or L1) and index arithmetic, as the kernel
+    // each schedule launches spends them
+    double ops64 = 0, ops32 = 0, bytes = 0, loads = 0, iops = 0, launches = 1, halo = 0;
     if (p->pipeline == PIPE_GODUNOV) {
         const double it = 2.06, sweep = 155.0 + 40.0 * it;
         if (f64) ops64 = 2 * sweep + 16;
         else { ops64 = 2 * 36.0 * it; ops32 = 2 * sweep + 16 - ops64; }
         bytes = s.fusion == FUSE_FULL ? 8 * es : s.fusion == FUSE_SWEEP ? 16 * es : 74 * es;
-        staged = s.fusion == FUSE_UNFUSED ? 0 : 13 * es;
+        loads = s.fusion == FUSE_UNFUSED ? 80 : 26;
+        iops = s.fusion == FUSE_UNFUSED ? 80 * 6 : 60;
         launches = s.fusion == FUSE_FULL ? 1 : s.fusion == FUSE_SWEEP ? 2 : 19;
         halo = s.fusion == FUSE_FULL ? 2.0 : 0.5;
     } else {
-        const double ops = p->pipeline == PIPE_CHAIN3D ? 26.0 : p->pipeline == PIPE_CHAIN2D ? 14.0 : 8.0 * d.rules.size();
-        (f64 ? ops64 : ops32) = ops;
+        const bool c3 = p->pipeline == PIPE_CHAIN3D;
+        const double ops = c3 ? 26.0 : p->pipeline == PIPE_CHAIN2D ? 14.0 : 8.0 * d.rules.size();
         const double io = (double)(d.axioms.size() + d.goals.size()) * es;
-        bytes = s.fusion == FUSE_FULL ? io : s.fusion == FUSE_SWEEP ? io + 2 * es : io + 2 * es * n_inter;
-        // values staged on chip per cell: every stencil reference of a fused stage
-        double refs = 0;
-        for (auto& r : d.rules) refs += r.in.size();
-        staged = s.fusion == FUSE_UNFUSED ? 0 : refs * es;
-        launches = s.fusion == FUSE_FULL ? 1 : s.fusion == FUSE_SWEEP ? 2 : (double)d.rules.size();
-        halo = s.fusion == FUSE_FULL ? R * (depth - 1) : s.fusion == FUSE_SWEEP ? R : 0.0;
+        double refs = 0, ax_refs = 0;
+        for (auto& r : d.rules) {
+            refs += r.in.size();
+            for (auto& x : r.in)
+                for (int f : d.axioms) if (x.field == f) ax_refs += 1;
+        }
+        const double first = d.rules.empty() ? 0 : d.rules[p->an.order[0]].in.size();
+        const double grad = c3 ? 6.0 : 4.0;   // references of the gradient stage
+        if (s.fusion == FUSE_FULL) {
+            bytes = io; loads = refs; iops = 2 * refs;
+            (f64 ? ops64 : ops32) = ops;
+            halo = R * (depth - 1);
+        } else if (s.fusion == FUSE_SWEEP) {
+            // first stage materialised by the generic kernel; the tail of the
+            // 3D chain recomputes s2 at each gradient tap from s1
+            bytes = io + 2 * es;
+            const double tail = c3 ? grad * 7.0 + grad : grad;
+            loads = first + tail;
+            iops = first * (3 * 25.0) + tail * 6.0;
+            (f64 ? ops64 : ops32) = c3 ? 7.0 + grad * 7.0 + 12.0 : ops;
+        } else {
+            bytes = io + 2 * es * n_inter;
+            loads = refs;
+            iops = ax_refs * (3 * 25.0) + (refs - ax_refs) * 8.0;
+            (f64 ? ops64 : ops32) = ops;
+            launches = (double)d.rules.size();
+        }
+        if (s.fusion == FUSE_SWEEP) launches = 2;
     }
     double rec = 1.0;
-    if (s.fusion != FUSE_UNFUSED) {
+    if (s.fusion == FUSE_FULL || (p->pipeline == PIPE_GODUNOV && s.fusion == FUSE_SWEEP)) {
         rec = (s.tx + 2 * halo) / s.tx;
         if (tiled >= 2) rec *= (s.ty + 2 * halo) / s.ty;
     }
@@ -830,22 +855,29 @@ void features(const hfav_plan_t* p, const Schedule& s, float* f) {
     const double t_hbm = bytes * cells / 6.8e12 * us;
     const double t64 = ops64 * rec * cells / 5.9e11 * us;
     const double t32 = ops32 * rec * cells / 6.9e13 * us;
-    const double t_chip = staged * rec * cells / 3.0e13 * us;
+    const double t_chip = loads * es * rec * cells / 3.0e13 * us;
+    const double t_int = iops * rec * cells / 1.8e13 * us;
+    const double t_launch = 3.0 * launches;
+    // the analytic estimate the network corrects (microseconds per step)
+    const double t_model = std::max(std::max(t_hbm, t_chip), std::max(t64, t32)) + t_int + t_launch;
+    // scale-free inputs: how the estimate splits over resources, fusion,
+    // placement, threads per CTA; the tile shape enters only through rec
+    // (the same shape has one tiled axis in 2D and two in 3D)
     f[0] = (float)(std::log2(cells) / 24.0);
-    f[1] = (float)(std::log2(1.0 + t_hbm) / 16.0);
-    f[2] = (float)(std::log2(1.0 + t64) / 16.0);
-    f[3] = (float)(std::log2(1.0 + t32) / 16.0);
-    f[4] = (float)(std::log2(1.0 + t_chip) / 16.0);
-    f[5] = s.fusion == FUSE_FULL ? 1.f : 0.f;
-    f[6] = s.fusion == FUSE_SWEEP ? 1.f : 0.f;
-    f[7] = s.fusion == FUSE_UNFUSED ? 1.f : 0.f;
+    f[1] = (float)(t_hbm / t_model);
+    f[2] = (float)(t64 / t_model);
+    f[3] = (float)(t32 / t_model);
+    f[4] = (float)(t_chip / t_model);
+    f[5] = (float)(t_int / t_model);
+    f[6] = s.fusion == FUSE_FULL ? 1.f : 0.f;
+    f[7] = s.fusion == FUSE_SWEEP ? 1.f : 0.f;
     f[8] = s.placement == PLACE_REG ? 1.f : 0.f;
     f[9] = s.placement == PLACE_SMEM ? 1.f : 0.f;
-    f[10] = (float)(std::log2(launches) / 5.0);
+    f[10] = (float)(t_launch / t_model);
     f[11] = (float)(std::log2((double)s.tx * s.ty) / 8.0);
-    f[12] = (float)(std::log2((double)s.tx / s.ty) / 6.0);
-    f[13] = (float)(std::log2(rec) / 2.0);
-    f[14] = (float)R / 3.f;
+    f[HFAV_FEATURE_BASE] = (float)(std::log2(t_model) / 16.0);
+    f[13] = s.fusion == FUSE_UNFUSED ? 1.f : 0.f;
+    f[14] = 0.f;   // reserved: a family marker such as DAG depth would not carry over
     f[15] = f64 ? 1.f : 0.f;
 }
 

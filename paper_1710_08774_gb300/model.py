@@ -129,8 +129,19 @@ def load_corpus(path=CORPUS):
         return list(csv.DictReader(f))
 
 
+BASE = 12   # HFAV_FEATURE_BASE: log2(analytic estimate in us) / 16
+
+
+def base_log(X):
+    """ln of the analytic time estimate (microseconds) carried in the features."""
+    return X[:, BASE].astype(np.float64) * 16.0 * np.log(2.0)
+
+
 def features_of(rows):
-    """Feature matrix (n x 16) and log-time targets of corpus rows (host planner only)."""
+    """Feature matrix (n x 16) and targets of corpus rows (host planner only).
+
+    The target is ln(measured microseconds per step) minus ln of the planner's
+    analytic estimate: the network learns the correction to the cost model."""
     X, y = [], []
     cache = {}
     for r in rows:
@@ -138,8 +149,9 @@ def features_of(rows):
         if key not in cache:
             cache[key] = plan_for(*key)[0]
         X.append(cache[key].features(r["schedule"]))
-        y.append(np.log(float(r["ms"])))
-    return np.array(X, dtype=np.float32), np.array(y, dtype=np.float32)
+        y.append(np.log(1e3 * float(r["ms"])))
+    X = np.array(X, dtype=np.float32)
+    return X, (np.array(y) - base_log(X)).astype(np.float32)
 
 
 # ---------------------------------------------------------------------------
@@ -150,13 +162,15 @@ class Model:
         self.params, self.shift, self.scale, self.hidden = params, shift, scale, hidden
         self.losses = losses
 
-    def predict(self, X):
+    def predict(self, X, add_base=True):
+        """Predicted ln(microseconds per step) of feature rows (network output
+        plus the analytic estimate's log when add_base)."""
         import torch
         Xn = torch.from_numpy(((X - self.shift) * self.scale).astype(np.float32)).cuda()
         y = torch.empty(Xn.shape[0], dtype=torch.float32, device="cuda")
         H.mlp_forward(self.params, Xn, self.hidden, y)
         torch.cuda.synchronize()
-        return y.cpu().numpy()
+        return y.cpu().numpy() + (base_log(X) if add_base else 0.0)
 
     def choose(self, plan):
         """Install the predicted-fastest schedule on the plan; returns (schedule, {schedule: prediction})."""

@@ -81,16 +81,31 @@ def run_chain3d(u, schedule, dtype=np.float64):
     return op[3:-3, 3:-3, 3:-3].double().cpu().numpy()
 
 
-@pytest.mark.parametrize("schedule", ["full:reg:32x4", "full:smem:64x4", "full:hbm:32x8", "full:smem:128x2",
-                                      "sweep:reg:32x4", "unfused"])
+@pytest.mark.parametrize("schedule", ["full:reg:32x4", "full:reg:64x4", "full:reg:128x2", "full:reg:32x8",
+                                      "full:smem:64x4", "full:hbm:32x8", "full:smem:128x2", "sweep:reg:32x4",
+                                      "unfused"])
 def test_chain3d_f64(schedule):
     u = I.chain3d_input(40, seed=4)
     ref = oracle.chain3d(u)
     assert normwise(run_chain3d(u, schedule), ref) <= 1e-12
 
 
-@pytest.mark.parametrize("schedule", ["full:reg:32x4", "full:smem:64x4", "sweep:reg:32x4", "unfused"])
+@pytest.mark.parametrize("schedule", ["full:reg:32x4", "full:reg:128x2", "full:reg:32x8", "full:smem:64x4",
+                                      "sweep:reg:32x4", "unfused"])
 def test_chain3d_f32_ragged(schedule):
     u = I.chain3d_input(37, seed=9)
     ref = oracle.chain3d(u)
     assert normwise(run_chain3d(u, schedule, np.float32), ref) <= 2e-5
+
+
+@pytest.mark.parametrize("schedule", ["full:reg:32x4", "full:reg:32x8", "full:smem:64x4", "unfused"])
+def test_chain3d_halo_given_quintic_exact(schedule):
+    import torch
+    n = 20
+    k, j, i = np.meshgrid(*(np.arange(-3, n + 3),) * 3, indexing="ij")
+    u = torch.from_numpy((i.astype(np.float64)) ** 5).cuda()
+    op = torch.full_like(u, float("nan"))
+    P = H.Plan(H.chain3d_dag(), [H.Grid.of(u, 3)], H.HFAV_F64, H.HFAV_BC_HALO_GIVEN, schedule)
+    P.run([u], [op])
+    torch.cuda.synchronize()
+    assert np.all(op[3:-3, 3:-3, 3:-3].cpu().numpy() == 120.0 / 121.0)

@@ -73,6 +73,15 @@ def test_f64_1024_workload():
     assert np.allclose(s["dt"][:10], dts, rtol=1e-13)
 
 
+@pytest.mark.parametrize("schedule", ["sweep:reg:32x4", "sweep:reg:64x4", "sweep:smem:32x8", "unfused"])
+def test_f64_2048_two_steps(schedule):
+    U = I.sod_state(2048, 2048, seed=1)
+    ref, dts, _ = oracle.godunov(U, 2)
+    (got,), _, s = gpu_godunov([U], 2, schedule)
+    check_fields(got, ref, 1e-12)
+    assert np.allclose(s["dt"][:2], dts, rtol=1e-13)
+
+
 @pytest.mark.parametrize("schedule", ["sweep:reg:32x4", "sweep:smem:64x4", "full:reg:32x4", "unfused"])
 def test_f32_bulk_matches_f64_oracle(schedule):
     U = I.sod_state(128, 96, seed=5)
@@ -119,3 +128,74 @@ def test_batch_of_uneven_grids(dtype, tol, schedule):
     for g, U in enumerate(Us):
         ref, _, _ = oracle.godunov(U, 10)
         check_fields(got[g], ref, tol)
+
+
+def _golden4096():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "godunov4096_seed1_10steps.txt")
+    dt = totals = absmax = None
+    pts, vals = [], []
+    for ln in open(path):
+        if ln.startswith("#"):
+            continue
+        f = ln.split()
+        if f[0] == "dt":
+            dt = np.array([float(x) for x in f[1:]])
+        elif f[0] == "totals":
+            totals = np.array([float(x) for x in f[1:]])
+        elif f[0] == "absmax":
+            absmax = np.array([float(x) for x in f[1:]])
+        else:
+            pts.append((int(f[0]), int(f[1])))
+            vals.append([float(x) for x in f[2:]])
+    return dt, totals, absmax, np.array(pts), np.array(vals)
+
+
+@pytest.mark.parametrize("schedule", ["sweep:reg:32x4", "sweep:hbm:32x4"])
+def test_f32_bulk_4096_full_size_sampled(schedule):
+    """The 4096^2 FP32-bulk workload at full size: sampled cells against the
+    stored FP64 oracle result (tests/golden/make_godunov4096.py), 1e-4
+    normwise per field; dt history and conserved totals."""
+    import torch
+    dt_ref, totals, absmax, pts, vals = _golden4096()
+    U = I.sod_state(4096, 4096, seed=1)
+    ins = state_tensors(U, torch.float32)
+    outs = empty_like_state(ins)
+    P = H.Plan(H.godunov_dag(), [H.Grid.of(ins[0], 0)], H.HFAV_F32, H.HFAV_BC_PERIODIC, schedule)
+    P.run(ins, outs, 10)
+    st = P.status()
+    assert st["newton_nonconverged"] == 0 and st["nonphysical"] == 0
+    assert np.allclose(st["dt"][:10], dt_ref, rtol=1e-5)
+    jj = torch.from_numpy(pts[:, 0]).cuda(); ii = torch.from_numpy(pts[:, 1]).cuda()
+    for f in range(4):
+        got = outs[f][jj, ii].double().cpu().numpy()
+        assert np.max(np.abs(got - vals[:, f])) / absmax[f] <= 1e-4, f
+    for f in (0, 3):
+        tot = outs[f].double().sum().item()
+        assert abs(tot - totals[f]) <= 1e-5 * abs(totals[f])
+
+
+def test_batch64_full_size_one_grid_and_conservation():
+    """The 64-grid FP32 batch at full size, 100 steps through a captured graph:
+    the smallest grid against the oracle (1e-4 normwise per field) and mass /
+    energy conservation of every grid (FP32 bulk: 1e-5 relative)."""
+    import math
+    import torch
+    sides = I.batch_sides(64, seed=3)
+    Us = [I.sod_state(nx, ny, seed=3, grid=g) for g, (nx, ny) in enumerate(sides)]
+    ins = [state_tensors(U, torch.float32) for U in Us]
+    outs = [empty_like_state(t) for t in ins]
+    P = H.Plan(H.godunov_dag(), [H.Grid.of(t[0], 0) for t in ins], H.HFAV_F32, H.HFAV_BC_PERIODIC,
+               "sweep:reg:32x4")
+    P.run(ins, outs, 100, graph=True)
+    st = P.status()
+    assert st["newton_nonconverged"] == 0 and st["nonphysical"] == 0
+    g = min(range(64), key=lambda k: sides[k][0] * sides[k][1])
+    ref, _, _ = oracle.godunov(Us[g], 100)
+    got = np.stack([o.double().cpu().numpy() for o in outs[g]])
+    check_fields(got, ref, 1e-4)
+    for k in range(64):
+        for f in (0, 3):
+            t0 = math.fsum(Us[k][f].astype(np.float32).astype(np.float64).ravel().tolist())
+            t1 = outs[k][f].double().sum().item()
+            assert abs(t1 - t0) <= 1e-5 * abs(t0), (k, f)

@@ -76,7 +76,7 @@ def test_training_reduces_loss():
     y = (np.sin(2 * X[:, 0]) + X[:, 1] * X[:, 2] + 0.5 * X[:, 3] ** 2).astype(np.float32)
     mdl = model.train(X, y, epochs=1500, lr=3e-3)
     assert mdl.losses[-1] < 0.05 * mdl.losses[0]
-    pred = mdl.predict(X)
+    pred = mdl.predict(X, add_base=False)
     assert np.mean((pred - y) ** 2) < 0.05 * np.var(y)
 
 
@@ -98,6 +98,7 @@ def test_model_choice_on_heldout_3d_chain():
     default = "full:reg:32x4"
     ratio = times[pick] / best
     gain = times[default] / times[pick]
+    print("\n" + "\n".join(f"  {k} {v:.4f} ms" for k, v in sorted(times.items(), key=lambda kv: kv[1])))
     print(f"\nheld-out chain3d 512^3 fp32: exhaustive best {min(times, key=times.get)} {best:.4f} ms; "
           f"model pick {pick} {times[pick]:.4f} ms (x{ratio:.3f} of best); default {default} "
           f"{times[default]:.4f} ms (model gains x{gain:.3f})")

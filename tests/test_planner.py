@@ -192,4 +192,4 @@ def test_schedules_and_variants():
     with pytest.raises(H.HfavError):
         P.schedule = "full:reg:48x4"
     f = P.features("full:reg:32x4")
-    assert f.shape == (16,) and f[5] == 1.0 and f[7] == 0.0
+    assert f.shape == (16,) and f[6] == 1.0 and f[13] == 0.0
