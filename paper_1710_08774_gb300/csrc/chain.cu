@@ -193,6 +193,9 @@ __device__ __forceinline__ T ld_u(const C2Args& a, int i, int j) {
     return garr_ld<T>(a.u, i, j, 0);
 }
 
+// rows loaded ahead of use by the 2D chain kernels (register queue depth)
+#define C2_PD 4
+
 // smem / hbm placement: 3-row rings of u (TX+4 wide) and L (TX+2 wide)
 template <typename T, bool HBM>
 __global__ void __launch_bounds__(256) chain2d_ring(const C2Args a) {
@@ -211,9 +214,22 @@ __global__ void __launch_bounds__(256) chain2d_ring(const C2Args a) {
     }
     T* su = base;            // [3][WU]
     T* sL = base + 3 * WU;   // [3][WL]
+    // row loads C2_PD rows ahead: column t and, for t < 4, column TX + t
+    const bool two = t + TX < WU;
+    T q[C2_PD], q2[C2_PD];
+#pragma unroll
+    for (int k = 0; k < C2_PD; ++k) {
+        q[k] = ld_u<T>(a, i0 - 2 + t, j0 - 2 + k);
+        q2[k] = two ? ld_u<T>(a, i0 - 2 + t + TX, j0 - 2 + k) : (T)0;
+    }
     for (int r = j0 - 2; r <= j0 + a.R + 1; ++r) {
         T* ur = su + ((r + 3) % 3) * WU;
-        for (int c = t; c < WU; c += TX) ur[c] = ld_u<T>(a, i0 - 2 + c, r);
+        ur[t] = q[0];
+        if (two) ur[t + TX] = q2[0];
+#pragma unroll
+        for (int k = 0; k + 1 < C2_PD; ++k) { q[k] = q[k + 1]; q2[k] = q2[k + 1]; }
+        q[C2_PD - 1] = ld_u<T>(a, i0 - 2 + t, r + C2_PD);
+        if (two) q2[C2_PD - 1] = ld_u<T>(a, i0 - 2 + t + TX, r + C2_PD);
         __syncthreads();
         if (r >= j0) {   // L(r-1) over columns i0-1 .. i0+TX
             const T* um = su + ((r - 2 + 3) % 3) * WU;
@@ -235,7 +251,11 @@ __global__ void __launch_bounds__(256) chain2d_ring(const C2Args a) {
     }
 }
 
-// reg placement: vertical windows in registers, one shared row per stage
+// reg placement: vertical windows in registers, one shared row per stage.
+// Rows are loaded C2_PD iterations ahead into a register queue so that
+// several rows' loads are in flight per thread (the row loop itself
+// synchronises the CTA twice per row and would otherwise expose the full
+// memory latency on every row).
 template <typename T>
 __global__ void __launch_bounds__(256) chain2d_reg(const C2Args a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -247,16 +267,33 @@ __global__ void __launch_bounds__(256) chain2d_reg(const C2Args a) {
     T* sL = su + WU;                             // [2][WL] L rows, double buffered
     // own column window u(r-2), u(r-1), u(r); L(r-3), L(r-2), L(r-1)
     T u0 = 0, u1 = 0, u2 = 0, l0 = 0, l1 = 0, l2 = 0;
-    // edge threads also carry the window of one halo column
+    // edge threads also carry the window of one halo column and load the
+    // second halo column's row r-1
     const bool left = (t == 0), right = (t == TX - 1);
     const int ie = left ? i0 - 1 : i0 + TX;
+    const int ih = left ? i0 - 2 : i0 + TX + 1;
     T e0 = 0, e1 = 0, e2 = 0;
+    T q[C2_PD], qe[C2_PD], qh[C2_PD];
+#pragma unroll
+    for (int k = 0; k < C2_PD; ++k) {
+        q[k] = ld_u<T>(a, i, j0 - 2 + k);
+        qe[k] = (left || right) ? ld_u<T>(a, ie, j0 - 2 + k) : (T)0;
+        qh[k] = (left || right) ? ld_u<T>(a, ih, j0 - 3 + k) : (T)0;
+    }
     for (int r = j0 - 2; r <= j0 + a.R + 1; ++r) {
-        u0 = u1; u1 = u2; u2 = ld_u<T>(a, i, r);
-        if (left || right) { e0 = e1; e1 = e2; e2 = ld_u<T>(a, ie, r); }
+        u0 = u1; u1 = u2; u2 = q[0];
+        const T hnew = qh[0];
+        if (left || right) { e0 = e1; e1 = e2; e2 = qe[0]; }
+#pragma unroll
+        for (int k = 0; k + 1 < C2_PD; ++k) { q[k] = q[k + 1]; qe[k] = qe[k + 1]; qh[k] = qh[k + 1]; }
+        q[C2_PD - 1] = ld_u<T>(a, i, r + C2_PD);
+        if (left || right) {
+            qe[C2_PD - 1] = ld_u<T>(a, ie, r + C2_PD);
+            qh[C2_PD - 1] = ld_u<T>(a, ih, r - 1 + C2_PD);
+        }
         su[t + 2] = u1;
-        if (left) { su[1] = e1; su[0] = ld_u<T>(a, i0 - 2, r - 1); }
-        if (right) { su[TX + 2] = e1; su[TX + 3] = ld_u<T>(a, i0 + TX + 1, r - 1); }
+        if (left) { su[1] = e1; su[0] = hnew; }
+        if (right) { su[TX + 2] = e1; su[TX + 3] = hnew; }
         __syncthreads();
         if (r >= j0) {
             T* Lr = sL + ((r - 1) & 1) * WL;
@@ -477,7 +514,8 @@ __global__ void __launch_bounds__(256) chain3d_ring(const C3Args a) {
 }
 
 // register-window form (placement reg): the CTA's TX x TY threads own an
-// output tile TX x (TY*M), M = 16 / TY.  Every stage keeps, for each position
+// output tile TX x (TY*M), TY*M = 16 (8 for TY = 2, which keeps the
+// per-thread windows of the widest tile within the register file).  Every stage keeps, for each position
 // a thread computes, the window of its input along k in registers (three
 // planes), so only the in-plane neighbours of the previous stage go through
 // one shared plane buffer per stage (double-buffered).  Positions and their
@@ -485,7 +523,7 @@ __global__ void __launch_bounds__(256) chain3d_ring(const C3Args a) {
 // division and no periodic wrap arithmetic inside the k loop.
 template <int TX, int TY>
 struct C3Tile {
-    static constexpr int NT = TX * TY, M = 16 / TY > 0 ? 16 / TY : 1, TYO = TY * M;
+    static constexpr int NT = TX * TY, M = (TY >= 4 ? 16 : 8) / TY, TYO = TY * M;
     static constexpr int WU = TX + 6, HU = TYO + 6, PU = WU * HU;
     static constexpr int W1 = TX + 4, H1 = TYO + 4, P1 = W1 * H1;
     static constexpr int W2 = TX + 2, H2 = TYO + 2, P2 = W2 * H2;
@@ -502,16 +540,14 @@ __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a) {
     const int tid = threadIdx.y * TX + threadIdx.x;
     const int i0 = blockIdx.x * TX, j0 = blockIdx.y * G::TYO, k0 = blockIdx.z * a.K;
     const T* u = (const T*)a.u.p;
-    // u positions: shared offset and global in-plane offset (wrapped / halo-given)
-    int64_t gu[G::NU];
-    int su[G::NU];
-    bool vu[G::NU];
+    // u positions: in-plane global offset (wrapped / halo-given), 32-bit
+    // (a padded plane is far below 2^31 elements); shared offsets and the
+    // s1 / s2 positions follow from tid and compile-time strides
+    int gu[G::NU];
 #pragma unroll
     for (int r = 0; r < G::NU; ++r) {
         const int q = tid + r * G::NT;
-        vu[r] = q < G::PU;
         const int cj = q / G::WU, ci = q - cj * G::WU;
-        su[r] = q;
         int gi = i0 - 3 + ci, gj = j0 - 3 + cj;
         if (a.u.wrap) {
             gi = wrap_idx(gi, a.nx);
@@ -520,29 +556,12 @@ __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a) {
             gi = min(max(gi, -3), a.nx + 2);
             gj = min(max(gj, -3), a.ny + 2);
         }
-        gu[r] = (int64_t)(gj + a.u.org[1]) * a.u.pitch[1] + (gi + a.u.org[0]);
+        gu[r] = (int)((int64_t)(gj + a.u.org[1]) * a.u.pitch[1] + (gi + a.u.org[0]));
     }
-    // s1 / s2 positions: offsets into their own plane and into the plane below
-    int o1[G::N1], b1[G::N1];
-    bool v1[G::N1];
-#pragma unroll
-    for (int r = 0; r < G::N1; ++r) {
-        const int q = tid + r * G::NT;
-        v1[r] = q < G::P1;
-        const int cj = q / G::W1, ci = q - cj * G::W1;
-        o1[r] = q;
-        b1[r] = (cj + 1) * G::WU + (ci + 1);   // same point in the u plane
-    }
-    int o2[G::N2], b2[G::N2];
-    bool v2[G::N2];
-#pragma unroll
-    for (int r = 0; r < G::N2; ++r) {
-        const int q = tid + r * G::NT;
-        v2[r] = q < G::P2;
-        const int cj = q / G::W2, ci = q - cj * G::W2;
-        o2[r] = q;
-        b2[r] = (cj + 1) * G::W1 + (ci + 1);   // same point in the s1 plane
-    }
+    // s1 position r: index q1 = tid + r NT in its (TX+4)-wide plane, at
+    // (ci+1, cj+1) of the u plane; s2 position r likewise in the s1 plane
+    auto b1_of = [&](int q) { const int cj = q / G::W1; return (cj + 1) * G::WU + (q - cj * G::W1) + 1; };
+    auto b2_of = [&](int q) { const int cj = q / G::W2; return (cj + 1) * G::W1 + (q - cj * G::W2) + 1; };
     // output positions: thread (tx, ty) owns rows ty + TY m
     T wu[G::N1][3], w1[G::N2][3], w2[G::M][3];
 #pragma unroll
@@ -561,11 +580,11 @@ __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a) {
         int kw = kk;
         if (a.u.wrap) kw = wrap_idx(kk, a.nz);
         else kw = min(max(kk, -3), a.nz + 2);
-        const int64_t kb = (int64_t)(kw + a.u.org[2]) * a.u.pitch[2];
+        const T* ub = u + (int64_t)(kw + a.u.org[2]) * a.u.pitch[2];
         T* Ub = U + buf * G::PU;
 #pragma unroll
         for (int r = 0; r < G::NU; ++r)
-            if (vu[r]) Ub[su[r]] = u[kb + gu[r]];
+            if (tid + r * G::NT < G::PU) Ub[tid + r * G::NT] = ub[gu[r]];
         __syncthreads();
         // s1 at plane kk-1: k-neighbours from the register window, in-plane from the u plane kk-1
         if (kk >= k0 - 1) {
@@ -573,21 +592,24 @@ __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a) {
             T* S1b = S1 + (buf ^ 1) * G::P1;
 #pragma unroll
             for (int r = 0; r < G::N1; ++r) {
-                if (!v1[r]) continue;
-                wu[r][0] = wu[r][1]; wu[r][1] = wu[r][2]; wu[r][2] = Ub[b1[r]];
-                const int b = b1[r];
+                const int q = tid + r * G::NT;
+                if (q >= G::P1) continue;
+                const int b = b1_of(q);
+                wu[r][0] = wu[r][1]; wu[r][1] = wu[r][2]; wu[r][2] = Ub[b];
                 T v = p1 * Up[b + 1];
                 v = fma(m1, Up[b - 1], v);
                 v = fma(q1, Up[b + G::WU], v);
                 v = fma(n1, Up[b - G::WU], v);
                 v = fma(kp1, wu[r][2], v);
                 v = fma(km1, wu[r][0], v);
-                S1b[o1[r]] = fma(c1, wu[r][1], v);
+                S1b[q] = fma(c1, wu[r][1], v);
             }
         } else {
 #pragma unroll
-            for (int r = 0; r < G::N1; ++r)
-                if (v1[r]) { wu[r][0] = wu[r][1]; wu[r][1] = wu[r][2]; wu[r][2] = Ub[b1[r]]; }
+            for (int r = 0; r < G::N1; ++r) {
+                const int q = tid + r * G::NT;
+                if (q < G::P1) { wu[r][0] = wu[r][1]; wu[r][1] = wu[r][2]; wu[r][2] = Ub[b1_of(q)]; }
+            }
         }
         __syncthreads();
         // s2 at plane kk-2 from the s1 planes kk-1 (window) and kk-2 (in-plane);
@@ -599,17 +621,18 @@ __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a) {
             const bool comp = kk >= k0 + 1;
 #pragma unroll
             for (int r = 0; r < G::N2; ++r) {
-                if (!v2[r]) continue;
-                w1[r][0] = w1[r][1]; w1[r][1] = w1[r][2]; w1[r][2] = S1n[b2[r]];
+                const int q = tid + r * G::NT;
+                if (q >= G::P2) continue;
+                const int b = b2_of(q);
+                w1[r][0] = w1[r][1]; w1[r][1] = w1[r][2]; w1[r][2] = S1n[b];
                 if (!comp) continue;
-                const int b = b2[r];
                 T v = p2 * S1p[b + 1];
                 v = fma(m2, S1p[b - 1], v);
                 v = fma(q2, S1p[b + G::W1], v);
                 v = fma(n2, S1p[b - G::W1], v);
                 v = fma(kp2, w1[r][2], v);
                 v = fma(km2, w1[r][0], v);
-                S2b[o2[r]] = fma(c2, w1[r][1], v);
+                S2b[q] = fma(c2, w1[r][1], v);
             }
         }
         __syncthreads();

@@ -800,19 +800,27 @@ void features(const hfav_plan_t* p, const Schedule& s, float* f) {
     const double R = p->an.max_radius;
     const int depth = p->an.max_depth;
     const int tiled = d.ndim - 1;   // axes the CTA tile covers (the stream axis is not tiled)
-    // per cell and time step: FP64 / FP32 operations, compulsory HBM bytes,
-    // on-chip loads (shared memory or L1) and index arithmetic, as the kernel
-    // each schedule launches spends them
-    double ops64 = 0, ops32 = 0, bytes = 0, loads = 0, iops = 0, launches = 1, halo = 0;
+    // per cell and time step: FP64 / FP32 operations (times the recompute of
+    // the kernel's halo), compulsory HBM bytes, on-chip operations (shared
+    // memory, shuffles; global-memory staging and L1 loads count double) and
+    // index arithmetic, as the kernel each schedule launches spends them
+    double ops64 = 0, ops32 = 0, bytes = 0, chip = 0, iops = 0, launches = 1, rec = 1.0;
+    const double TX = s.tx, TY = s.ty;
+    const double gw = 2.0;   // weight of a global-memory (L1 / L2) operation
     if (p->pipeline == PIPE_GODUNOV) {
         const double it = 2.06, sweep = 155.0 + 40.0 * it;
         if (f64) ops64 = 2 * sweep + 16;
         else { ops64 = 2 * 36.0 * it; ops32 = 2 * sweep + 16 - ops64; }
-        bytes = s.fusion == FUSE_FULL ? 8 * es : s.fusion == FUSE_SWEEP ? 16 * es : 74 * es;
-        loads = s.fusion == FUSE_UNFUSED ? 80 : 26;
-        iops = s.fusion == FUSE_UNFUSED ? 80 * 6 : 60;
-        launches = s.fusion == FUSE_FULL ? 1 : s.fusion == FUSE_SWEEP ? 2 : 19;
-        halo = s.fusion == FUSE_FULL ? 2.0 : 0.5;
+        const double ywin = s.placement == PLACE_REG ? 0.0 : s.placement == PLACE_SMEM ? 60.0 : 60.0 * gw;
+        const double xst = s.placement == PLACE_REG ? 40.0 : s.placement == PLACE_SMEM ? 40.0 : 40.0 * gw;
+        if (s.fusion == FUSE_FULL) {
+            bytes = 8 * es; chip = 40.0 + 8.0 + ywin; iops = 60; launches = 1;
+            rec = TX / (TX - 2) * 1.15;
+        } else if (s.fusion == FUSE_SWEEP) {
+            bytes = 16 * es; chip = xst + ywin; iops = 60; launches = 2; rec = 1.03;
+        } else {
+            bytes = 74 * es; chip = 80.0 * gw; iops = 80 * 6; launches = 19;
+        }
     } else {
         const bool c3 = p->pipeline == PIPE_CHAIN3D;
         const double ops = c3 ? 26.0 : p->pipeline == PIPE_CHAIN2D ? 14.0 : 8.0 * d.rules.size();
@@ -823,40 +831,46 @@ void features(const hfav_plan_t* p, const Schedule& s, float* f) {
             for (auto& x : r.in)
                 for (int f : d.axioms) if (x.field == f) ax_refs += 1;
         }
-        const double first = d.rules.empty() ? 0 : d.rules[p->an.order[0]].in.size();
-        const double grad = c3 ? 6.0 : 4.0;   // references of the gradient stage
+        double o32 = ops;
         if (s.fusion == FUSE_FULL) {
-            bytes = io; loads = refs; iops = 2 * refs;
-            (f64 ? ops64 : ops32) = ops;
-            halo = R * (depth - 1);
+            bytes = io; iops = 2 * refs; launches = 1;
+            if (c3) {
+                // tile of outputs: TX x 16 (register windows; TX x 8 when TY = 2) or TX x TY (rings)
+                const double oy = s.placement == PLACE_REG ? (TY >= 4 ? 16.0 : 8.0) : TY;
+                const double ru = (TX + 6) * (oy + 6) / (TX * oy), r1 = (TX + 4) * (oy + 4) / (TX * oy),
+                             r2 = (TX + 2) * (oy + 2) / (TX * oy);
+                const double wr = ru + r1 + r2;
+                chip = s.placement == PLACE_REG ? wr + 5 * r1 + 5 * r2 + 5 : (wr + 7 * r1 + 7 * r2 + 6);
+                if (s.placement == PLACE_HBM) chip *= gw;
+                o32 = 7 * r1 + 7 * r2 + 12;
+            } else {
+                const double rr = (TX + 2) / TX * 1.06;
+                chip = s.placement == PLACE_REG ? 6.0 * 1.06 : 11.0 * rr;
+                if (s.placement == PLACE_HBM) chip *= gw;
+                o32 = ops * rr;
+            }
         } else if (s.fusion == FUSE_SWEEP) {
             // first stage materialised by the generic kernel; the tail of the
             // 3D chain recomputes s2 at each gradient tap from s1
-            bytes = io + 2 * es;
-            const double tail = c3 ? grad * 7.0 + grad : grad;
-            loads = first + tail;
+            bytes = io + 2 * es; launches = 2;
+            const double first = d.rules.empty() ? 0 : d.rules[p->an.order[0]].in.size();
+            const double tail = c3 ? 6.0 * 7.0 + 6.0 : 4.0;
+            chip = (first + 1 + tail + 1) * gw;
             iops = first * (3 * 25.0) + tail * 6.0;
-            (f64 ? ops64 : ops32) = c3 ? 7.0 + grad * 7.0 + 12.0 : ops;
+            o32 = c3 ? 7.0 + 6.0 * 7.0 + 12.0 : ops;
         } else {
-            bytes = io + 2 * es * n_inter;
-            loads = refs;
+            bytes = io + 2 * es * n_inter; launches = (double)d.rules.size();
+            chip = (refs + d.rules.size()) * gw;
             iops = ax_refs * (3 * 25.0) + (refs - ax_refs) * 8.0;
-            (f64 ? ops64 : ops32) = ops;
-            launches = (double)d.rules.size();
         }
-        if (s.fusion == FUSE_SWEEP) launches = 2;
-    }
-    double rec = 1.0;
-    if (s.fusion == FUSE_FULL || (p->pipeline == PIPE_GODUNOV && s.fusion == FUSE_SWEEP)) {
-        rec = (s.tx + 2 * halo) / s.tx;
-        if (tiled >= 2) rec *= (s.ty + 2 * halo) / s.ty;
+        (f64 ? ops64 : ops32) = o32;
     }
     const double us = 1e6;
     const double t_hbm = bytes * cells / 6.8e12 * us;
     const double t64 = ops64 * rec * cells / 5.9e11 * us;
-    const double t32 = ops32 * rec * cells / 6.9e13 * us;
-    const double t_chip = loads * es * rec * cells / 3.0e13 * us;
-    const double t_int = iops * rec * cells / 1.8e13 * us;
+    const double t32 = ops32 * cells / 6.9e13 * us;
+    const double t_chip = chip * es * cells / 3.0e13 * us;
+    const double t_int = iops * cells / 1.8e13 * us;
     const double t_launch = 3.0 * launches;
     // the analytic estimate the network corrects (microseconds per step)
     const double t_model = std::max(std::max(t_hbm, t_chip), std::max(t64, t32)) + t_int + t_launch;
