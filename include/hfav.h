@@ -363,11 +363,13 @@ int hfav_mlp_train(float* params, float* m, float* v, int n_in, int hidden, cons
 
 /* Learned schedule choice: features of every valid schedule of the plan
  * (hfav_plan_features, then (f - shift) * scale per feature when the host
- * arrays are given), the predicted ln(time) of each -- the network's output
- * plus ln of the analytic estimate in feature HFAV_FEATURE_BASE -- (pred,
- * host, n_pred entries in hfav_plan_variants order), and the argmin installed
- * as the plan's schedule and copied to `best`.  Synchronises the default stream. */
-int hfav_model_choose(hfav_plan_t* plan, const float* params, int hidden, const float* feat_shift,
+ * arrays are given), the predicted ln(time) of each -- the mean output of the
+ * n_models networks whose parameter vectors lie back to back in `params`
+ * (device), plus ln of the analytic estimate in feature HFAV_FEATURE_BASE --
+ * (pred, host, n_pred entries in hfav_plan_variants order), and the argmin
+ * installed as the plan's schedule and copied to `best`.  Synchronises the
+ * default stream. */
+int hfav_model_choose(hfav_plan_t* plan, const float* params, int n_models, int hidden, const float* feat_shift,
                       const float* feat_scale, float* pred, int n_pred, char* best, size_t n_best);
 
 #ifdef __cplusplus

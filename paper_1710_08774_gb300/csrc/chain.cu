@@ -796,3 +796,53 @@ int launch_chain3d(hfav_plan_t* p, const Schedule& s, void* const* ax, void* con
 }
 
 }  // namespace hfav
+
+// ---------------------------------------------------------------------------
+// resident warps per SM of the chain kernel a schedule launches (its main
+// kernel), for the schedule model's features; -1 without a usable device
+// ---------------------------------------------------------------------------
+namespace hfav {
+namespace {
+template <typename K>
+double warps_of(K kern, int threads, size_t smem) {
+    int occ = 0;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return -1.0;
+    }
+    return (double)occ * threads / 32.0;
+}
+template <typename T>
+double chain_warps_t(const hfav_plan_t* p, const Schedule& s) {
+    const int TX = s.tx, TY = s.ty, NT = TX * TY;
+    const size_t es = sizeof(T);
+    if (s.fusion == FUSE_UNFUSED) return warps_of(generic_rule_kernel<T>, 256, 0);
+    if (p->pipeline == PIPE_CHAIN2D) {
+        if (s.fusion == FUSE_SWEEP) return warps_of(chain2d_tail<T>, NT, 0);
+        if (s.placement == PLACE_REG) return warps_of(chain2d_reg<T>, NT, (size_t)TY * ((TX + 4) + 2 * (TX + 2)) * es);
+        if (s.placement == PLACE_SMEM)
+            return warps_of(chain2d_ring<T, false>, NT, (size_t)TY * (3 * (TX + 4) + 3 * (TX + 2)) * es);
+        return warps_of(chain2d_ring<T, true>, NT, 0);
+    }
+    if (s.fusion == FUSE_SWEEP) return warps_of(chain3d_tail<T>, NT, 0);
+    if (s.placement == PLACE_REG) {
+#define C3W(a, b)                                                                                             \
+    if (TX == a && TY == b) {                                                                                 \
+        using G = C3Tile<a, b>;                                                                               \
+        return warps_of(chain3d_regw<T, a, b>, NT, (size_t)2 * (G::PU + G::P1 + G::P2) * es);                 \
+    }
+        C3W(32, 4) C3W(64, 4) C3W(128, 2) C3W(32, 8)
+#undef C3W
+        return -1.0;
+    }
+    const size_t per = (size_t)3 * ((TX + 6) * (TY + 6) + (TX + 4) * (TY + 4) + (TX + 2) * (TY + 2)) * es;
+    if (s.placement == PLACE_SMEM) return warps_of(chain3d_ring<T, false>, NT, per);
+    return warps_of(chain3d_ring<T, true>, NT, 0);
+}
+}  // namespace
+
+double chain_kernel_warps(const hfav_plan_t* p, const Schedule& s) {
+    return p->dtype == HFAV_F64 ? chain_warps_t<double>(p, s) : chain_warps_t<float>(p, s);
+}
+}  // namespace hfav

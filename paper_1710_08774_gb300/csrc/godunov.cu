@@ -1100,3 +1100,39 @@ extern "C" int hfav_selftest_arith(const double* x, int64_t n, double* rcp_out, 
     if (e != cudaSuccess) return set_error(HFAV_ECUDA, cudaGetErrorString(e));
     return HFAV_OK;
 }
+
+namespace hfav {
+namespace {
+template <typename K>
+double gwarps_of(K kern, int threads, size_t smem) {
+    int occ = 0;
+    if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        return -1.0;
+    }
+    return (double)occ * threads / 32.0;
+}
+template <typename T>
+double godunov_warps_t(const Schedule& s) {
+    const int NT = s.tx * s.ty;
+    const size_t es = sizeof(T);
+    if (s.fusion == FUSE_UNFUSED) return gwarps_of(u_riemann<T>, 256, 0);
+    if (s.fusion == FUSE_SWEEP) {   // the y pass takes the larger share
+        const size_t ysm = s.placement == PLACE_SMEM ? (size_t)NT * YWIN_VALS * es : 0;
+        if (s.placement == PLACE_REG) return gwarps_of(gsweep_y<T, PLACE_REG>, NT, 0);
+        if (s.placement == PLACE_SMEM) return gwarps_of(gsweep_y<T, PLACE_SMEM>, NT, ysm);
+        return gwarps_of(gsweep_y<T, PLACE_HBM>, NT, 0);
+    }
+    const size_t fsm = (size_t)s.ty * fstage_elems<T>(s.tx) * es +
+                       (s.placement == PLACE_SMEM ? (size_t)NT * YWIN_VALS * es : 0);
+    if (s.placement == PLACE_REG) return gwarps_of(gfull<T, PLACE_REG>, NT, fsm);
+    if (s.placement == PLACE_SMEM) return gwarps_of(gfull<T, PLACE_SMEM>, NT, fsm);
+    return gwarps_of(gfull<T, PLACE_HBM>, NT, fsm);
+}
+}  // namespace
+
+double godunov_kernel_warps(const hfav_plan_t* p, const Schedule& s) {
+    return p->dtype == HFAV_F64 ? godunov_warps_t<double>(s) : godunov_warps_t<float>(s);
+}
+}  // namespace hfav

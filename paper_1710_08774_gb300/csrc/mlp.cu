@@ -201,9 +201,9 @@ int hfav_mlp_train(float* params, float* m, float* v, int n_in, int hidden, cons
     return HFAV_OK;
 }
 
-int hfav_model_choose(hfav_plan_t* p, const float* params, int hidden, const float* feat_shift,
+int hfav_model_choose(hfav_plan_t* p, const float* params, int n_models, int hidden, const float* feat_shift,
                       const float* feat_scale, float* pred, int n_pred, char* best, size_t n_best) {
-    if (!p || !params || p->analysis_only) return set_error(HFAV_EINVAL, "bad argument");
+    if (!p || !params || p->analysis_only || n_models < 1) return set_error(HFAV_EINVAL, "bad argument");
     auto vars = valid_schedules(p);
     const int nv = (int)vars.size(), NI = HFAV_N_FEATURES;
     std::vector<float> X((size_t)nv * NI), base(nv);
@@ -219,13 +219,17 @@ int hfav_model_choose(hfav_plan_t* p, const float* params, int hidden, const flo
     HFAV_CUDA(cudaMalloc(&dX, X.size() * sizeof(float)));
     cudaError_t e = cudaMalloc(&dy, nv * sizeof(float));
     if (e != cudaSuccess) { cudaFree(dX); return set_error(HFAV_ENOMEM, "cudaMalloc"); }
-    std::vector<float> y(nv);
+    std::vector<float> y(nv, 0.f), ym(nv);
     int rc = HFAV_OK;
     if (cudaMemcpy(dX, X.data(), X.size() * sizeof(float), cudaMemcpyHostToDevice) != cudaSuccess)
         rc = set_error(HFAV_ECUDA, "upload");
-    if (!rc) rc = hfav_mlp_forward(params, NI, hidden, dX, nv, dy, nullptr);
-    if (!rc && cudaMemcpy(y.data(), dy, nv * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
-        rc = set_error(HFAV_ECUDA, "download");
+    const int64_t np = hfav_mlp_n_params(NI, hidden);
+    for (int m = 0; m < n_models && !rc; ++m) {
+        rc = hfav_mlp_forward(params + m * np, NI, hidden, dX, nv, dy, nullptr);
+        if (!rc && cudaMemcpy(ym.data(), dy, nv * sizeof(float), cudaMemcpyDeviceToHost) != cudaSuccess)
+            rc = set_error(HFAV_ECUDA, "download");
+        for (int k = 0; k < nv && !rc; ++k) y[k] += ym[k] / n_models;
+    }
     cudaFree(dX);
     cudaFree(dy);
     if (rc) return rc;

@@ -109,4 +109,7 @@ void destroy_runtime(hfav_plan_t* p);
 void drop_graph(hfav_plan_t* p);
 int kernel_times(hfav_plan_t* p, std::vector<std::string>* names, std::vector<double>* ms, std::vector<int>* counts);
 int set_timing(hfav_plan_t* p, int on);
+// resident warps per SM of a schedule's main kernel (-1 without a device)
+double chain_kernel_warps(const hfav_plan_t* p, const Schedule& s);
+double godunov_kernel_warps(const hfav_plan_t* p, const Schedule& s);
 }  // namespace hfav

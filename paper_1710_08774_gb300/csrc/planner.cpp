@@ -891,7 +891,12 @@ void features(const hfav_plan_t* p, const Schedule& s, float* f) {
     f[11] = (float)(std::log2((double)s.tx * s.ty) / 8.0);
     f[HFAV_FEATURE_BASE] = (float)(std::log2(t_model) / 16.0);
     f[13] = s.fusion == FUSE_UNFUSED ? 1.f : 0.f;
-    f[14] = 0.f;   // reserved: a family marker such as DAG depth would not carry over
+    // resident warps per SM of the schedule's main kernel (register and
+    // shared-memory limits of the compiled kernel); 24 when no device answers
+    double warps = p->pipeline == PIPE_GODUNOV ? godunov_kernel_warps(p, s)
+                   : (p->pipeline == PIPE_CHAIN2D || p->pipeline == PIPE_CHAIN3D) ? chain_kernel_warps(p, s) : -1.0;
+    if (warps <= 0) warps = 24.0;
+    f[14] = (float)(warps / 64.0);
     f[15] = f64 ? 1.f : 0.f;
 }
 

@@ -142,8 +142,8 @@ def load(path=None):
                            ctypes.c_float, ctypes.c_int, P], ctypes.c_int),
         "hfav_mlp_train": ([P, P, P, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int, ctypes.c_int, ctypes.c_float,
                             P, P, P, P], ctypes.c_int),
-        "hfav_model_choose": ([P, P, ctypes.c_int, fp, fp, fp, ctypes.c_int, ctypes.c_char_p, ctypes.c_size_t],
-                              ctypes.c_int),
+        "hfav_model_choose": ([P, P, ctypes.c_int, ctypes.c_int, fp, fp, fp, ctypes.c_int, ctypes.c_char_p,
+                               ctypes.c_size_t], ctypes.c_int),
         "hfav_plan_timing": ([P, ctypes.c_int], ctypes.c_int),
         "hfav_selftest_arith": ([P, ctypes.c_int64, P, P, P], ctypes.c_int),
         "hfav_chain2d_static": ([P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
@@ -440,14 +440,15 @@ class Plan:
                                    times, len(vs)))
         return dict(zip(vs, [float(t) for t in times]))
 
-    def model_choose(self, params, hidden, shift=None, scale=None):
+    def model_choose(self, params, hidden, shift=None, scale=None, n_models=1):
         vs = self.variants()
         pred = (ctypes.c_float * len(vs))()
         best = ctypes.create_string_buffer(128)
         fp = ctypes.POINTER(ctypes.c_float)
         sh = None if shift is None else (ctypes.c_float * N_FEATURES)(*[float(x) for x in shift])
         sc = None if scale is None else (ctypes.c_float * N_FEATURES)(*[float(x) for x in scale])
-        check(load().hfav_model_choose(self.h, _ptr(params), hidden, sh, sc, pred, len(vs), best, len(best)))
+        check(load().hfav_model_choose(self.h, _ptr(params), n_models, hidden, sh, sc, pred, len(vs), best,
+                                       len(best)))
         return best.value.decode(), dict(zip(vs, [float(x) for x in pred]))
 
 

@@ -158,23 +158,29 @@ def features_of(rows):
 # training and choice
 # ---------------------------------------------------------------------------
 class Model:
-    def __init__(self, params, shift, scale, hidden=HIDDEN, losses=None):
+    """An ensemble of n networks (parameter vectors back to back on the device)."""
+
+    def __init__(self, params, shift, scale, hidden=HIDDEN, losses=None, n_models=1):
         self.params, self.shift, self.scale, self.hidden = params, shift, scale, hidden
-        self.losses = losses
+        self.losses, self.n_models = losses, n_models
 
     def predict(self, X, add_base=True):
         """Predicted ln(microseconds per step) of feature rows (network output
         plus the analytic estimate's log when add_base)."""
         import torch
         Xn = torch.from_numpy(((X - self.shift) * self.scale).astype(np.float32)).cuda()
-        y = torch.empty(Xn.shape[0], dtype=torch.float32, device="cuda")
-        H.mlp_forward(self.params, Xn, self.hidden, y)
-        torch.cuda.synchronize()
-        return y.cpu().numpy() + (base_log(X) if add_base else 0.0)
+        np_ = H.mlp_n_params(X.shape[1], self.hidden)
+        out = np.zeros(X.shape[0])
+        for m in range(self.n_models):
+            y = torch.empty(Xn.shape[0], dtype=torch.float32, device="cuda")
+            H.mlp_forward(self.params[m * np_:(m + 1) * np_], Xn, self.hidden, y)
+            torch.cuda.synchronize()
+            out += y.cpu().numpy() / self.n_models
+        return out + (base_log(X) if add_base else 0.0)
 
     def choose(self, plan):
         """Install the predicted-fastest schedule on the plan; returns (schedule, {schedule: prediction})."""
-        return plan.model_choose(self.params, self.hidden, self.shift, self.scale)
+        return plan.model_choose(self.params, self.hidden, self.shift, self.scale, self.n_models)
 
     def save(self, path):
         np.savez(path, params=self.params.cpu().numpy(), shift=self.shift, scale=self.scale, hidden=self.hidden)
@@ -195,21 +201,27 @@ def init_params(n_in, hidden, seed=0):
     return np.concatenate([W1.ravel(), np.zeros(hidden), W2.ravel(), np.zeros(hidden), w3, [0.0]]).astype(np.float32)
 
 
-def train(X, y, hidden=HIDDEN, epochs=4000, lr=3e-3, seed=0):
-    """Full-batch Adam on the GPU (hfav_mlp_train).  Returns a Model."""
+def train(X, y, hidden=HIDDEN, epochs=800, lr=3e-3, seed=0, n_models=1):
+    """Full-batch Adam on the GPU (hfav_mlp_train), one network per seed
+    seed .. seed + n_models - 1.  Returns a Model (the ensemble)."""
     import torch
     shift = X.mean(axis=0)
     sd = X.std(axis=0)
     scale = np.where(sd > 1e-6, 1.0 / np.maximum(sd, 1e-6), 1.0).astype(np.float32)
     Xn = torch.from_numpy(((X - shift) * scale).astype(np.float32)).cuda()
     t = torch.from_numpy(y.astype(np.float32)).cuda()
-    p = torch.from_numpy(init_params(X.shape[1], hidden, seed)).cuda()
-    m = torch.zeros_like(p); v = torch.zeros_like(p); g = torch.zeros_like(p)
     work = torch.empty(H.mlp_work_floats(X.shape[0], hidden), dtype=torch.float32, device="cuda")
-    losses = torch.empty(epochs, dtype=torch.float32, device="cuda")
-    H.mlp_train(p, m, v, Xn, t, hidden, epochs, lr, work, g, losses)
+    params, losses = [], []
+    for k in range(n_models):
+        p = torch.from_numpy(init_params(X.shape[1], hidden, seed + k)).cuda()
+        m = torch.zeros_like(p); v = torch.zeros_like(p); g = torch.zeros_like(p)
+        lh = torch.empty(epochs, dtype=torch.float32, device="cuda")
+        H.mlp_train(p, m, v, Xn, t, hidden, epochs, lr, work, g, lh)
+        params.append(p)
+        losses.append(lh)
     torch.cuda.synchronize()
-    return Model(p, shift.astype(np.float32), scale, hidden, losses.cpu().numpy())
+    return Model(torch.cat(params), shift.astype(np.float32), scale, hidden,
+                 torch.stack(losses).mean(0).cpu().numpy(), n_models)
 
 
 if __name__ == "__main__":
