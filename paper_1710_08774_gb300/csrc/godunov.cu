@@ -996,13 +996,26 @@ static int run_godunov_t(hfav_plan_t* p, const Schedule& s, void* const* ax, voi
             return p->grids[a.x].extent[0] > p->grids[b.x].extent[0];
         });
         void* dxrows = nullptr;
-        // arcs per row: enough row-arc warps for ~6 per SM sub-partition
+        // arcs per row: the most arcs (warps per row) for which every row is
+        // resident at once -- a row is the unit of work, so a second partial
+        // wave leaves SMs idle -- and at least two warps per SM sub-partition
         int xarcs = 1;
         {
-            int64_t rows = (int64_t)xrows.size();
+            const int64_t rows = (int64_t)xrows.size();
             int minnx = 1 << 30;
             for (auto& q : p->grids) minnx = std::min<int>(minnx, (int)q.extent[0]);
-            while (xarcs < 8 && rows * xarcs < (int64_t)kSMs * 4 * 6 && minnx >= 32 * 2 * xarcs * 2) xarcs *= 2;
+            cudaFuncAttributes fa;
+            int regs = 128;
+            if (cudaFuncGetAttributes(&fa, gsweep_xw<T>) == cudaSuccess) regs = std::max(fa.numRegs, 1);
+            else cudaGetLastError();
+            for (int A = 8; A >= 1; A /= 2) {
+                if (minnx < 32 * 2 * A) continue;   // at least two chunks per arc
+                const int64_t per_sm = std::min<int64_t>(65536 / (32 * A * regs), 2048 / (32 * A));
+                if (rows <= per_sm * kSMs && rows * A >= (int64_t)kSMs * 4 * 2) { xarcs = A; break; }
+            }
+            if (xarcs == 1) {   // rows exceed one wave: enough arcs for ~6 warps per sub-partition
+                while (xarcs < 8 && rows * xarcs < (int64_t)kSMs * 4 * 6 && minnx >= 32 * 2 * xarcs * 2) xarcs *= 2;
+            }
         }
         if (s.placement == PLACE_REG) {
             if ((rc = scratch(p, "gxrows", xrows.size() * sizeof(int2), &dxrows))) return rc;
