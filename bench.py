@@ -47,6 +47,31 @@ CHAIN2D_FLOPS = 14.0     # L 5, G 7 (2 sub, 2 mul, add, sqrt, halve), out 2
 CHAIN3D_FLOPS = 26.0     # s1 7, s2 7, s3 10, out 2
 
 
+# DRAM bytes (read + write) per launch of a workload's dominant kernel from one
+# ncu capture of the bench's profiling case (summaries under profiles/), with
+# the hash of the kernel sources at capture time: a changed source voids it.
+TRAFFIC = {
+    ("godunov2d_fp64_1024x1024_10steps", "gsweep_y"): (34.42e6, "a6a59d5e63d25fb1"),
+    ("chain3d_fp32_512x512x512", "chain3d_fused"): (1082.6e6, "932fd0a39ec35402"),
+}
+
+
+def src_hash(files):
+    import hashlib
+    h = hashlib.sha1()
+    for f in files:
+        h.update(open(os.path.join(ROOT, "paper_1710_08774_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(workload, kernel):
+    t = TRAFFIC.get((workload, kernel))
+    if not t:
+        return None
+    files = ["godunov.cu", "godunov_phys.cuh", "common.cuh"] if kernel.startswith("g") else ["chain.cu", "common.cuh"]
+    return t[0] if src_hash(files) == t[1] else None
+
+
 def peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -454,8 +479,8 @@ def bench(args, name, torch, H, I, dev, ws, rank, local):
         bound, work, unit, peak, src = w.kernel_work(dom, it_avg)
         achieved = work / (dom_ms * 1e-3) / 1e9
         roof = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": None, "peak_source": src, "launch_ms": dom_ms,
-                "work_per_launch": work}
+                "frac": achieved / peak, "traffic": traffic_for(w.name, dom), "peak_source": src,
+                "launch_ms": dom_ms, "work_per_launch": work}
     hbm = peaks().get("hbm_gbs", 6787.6)
     cb = w.compulsory_bytes(best)
     line = {
