@@ -22,12 +22,22 @@ namespace hfav {
 // ---------------------------------------------------------------------------
 // generic one-kernel-per-rule executor (the unfused GPU form)
 // ---------------------------------------------------------------------------
+// Weights reach the kernels in both precisions, rounded on the host: an FP32
+// kernel never converts an FP64 parameter on the device (the conversion runs
+// on the FP64 pipe, and the compiler may re-derive a weight inside a loop).
+template <typename T>
+__device__ __forceinline__ T wsel(double d, float f) {
+    if constexpr (sizeof(T) == 8) return (T)d;
+    else return (T)f;
+}
+
 struct GenericArgs {
     int op;
     int nref;
     int ref_arr[27];
     int ref_off[27][3];
     double w[27];
+    float wf[27];
     GArr arr[8];
     GArr out;
     int lo[3], n[3];   // iteration region: lo .. lo + n - 1 per axis
@@ -48,7 +58,7 @@ __global__ void __launch_bounds__(256) generic_rule_kernel(const GenericArgs a) 
             v = (T)0;
             for (int r = 0; r < a.nref; ++r) {
                 T x = garr_ld<T>(a.arr[a.ref_arr[r]], i + a.ref_off[r][0], j + a.ref_off[r][1], k + a.ref_off[r][2]);
-                v = r == 0 ? (T)a.w[r] * x : fma((T)a.w[r], x, v);
+                v = r == 0 ? wsel<T>(a.w[r], a.wf[r]) * x : fma(wsel<T>(a.w[r], a.wf[r]), x, v);
             }
         } else if (a.op == HFAV_OP_GRADMAG_HALF) {
             T s = (T)0;
@@ -151,6 +161,7 @@ int launch_generic(hfav_plan_t* p, void* const* ax, void* const* go, cudaStream_
         }
         int64_t total = (int64_t)a.n[0] * a.n[1] * a.n[2];
         int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+        for (int k = 0; k < 27; ++k) a.wf[k] = (float)a.w[k];
         if (p->dtype == HFAV_F64) generic_rule_kernel<double><<<blocks, 256, 0, st>>>(a);
         else generic_rule_kernel<float><<<blocks, 256, 0, st>>>(a);
         HFAV_LAUNCHED(p->rt, "generic_rule_kernel", st);
@@ -165,17 +176,18 @@ struct C2Args {
     GArr u, out;
     int nx, ny, R;
     double wc, wip, wim, wjp, wjm;   // 5-point star weights
+    float fc, fip, fim, fjp, fjm;    // the same, rounded to FP32
     void* slab;                      // hbm placement: per-CTA rings
 };
 
 // L at one point from its five star neighbours, summed in the rule's order
 template <typename T>
 __device__ __forceinline__ T lap5(const C2Args& a, T ip, T im, T jp, T jm, T c) {
-    T v = (T)a.wip * ip;
-    v = fma((T)a.wim, im, v);
-    v = fma((T)a.wjp, jp, v);
-    v = fma((T)a.wjm, jm, v);
-    return fma((T)a.wc, c, v);
+    T v = wsel<T>(a.wip, a.fip) * ip;
+    v = fma(wsel<T>(a.wim, a.fim), im, v);
+    v = fma(wsel<T>(a.wjp, a.fjp), jp, v);
+    v = fma(wsel<T>(a.wjm, a.fjm), jm, v);
+    return fma(wsel<T>(a.wc, a.fc), c, v);
 }
 
 template <typename T>
@@ -347,6 +359,7 @@ int launch_chain2d(hfav_plan_t* p, const Schedule& s, void* const* ax, void* con
     a.out.wrap = 0;
     a.nx = nx; a.ny = ny;
     a.wc = m.w1[13]; a.wip = m.w1[14]; a.wim = m.w1[12]; a.wjp = m.w1[16]; a.wjm = m.w1[10];
+    a.fc = (float)a.wc; a.fip = (float)a.wip; a.fim = (float)a.wim; a.fjp = (float)a.wjp; a.fjm = (float)a.wjm;
     for (int k = 0; k < 27; ++k)
         if (k != 13 && k != 14 && k != 12 && k != 16 && k != 10 && m.w1[k] != 0.0)
             return set_error(HFAV_EUNSUPPORTED, "fused 2D chain takes a 5-point star stencil");
@@ -380,6 +393,7 @@ int launch_chain2d(hfav_plan_t* p, const Schedule& s, void* const* ax, void* con
         ga.lo[0] = -fi.halo_lo[0]; ga.lo[1] = -fi.halo_lo[1]; ga.lo[2] = 0;
         ga.n[0] = (int)ex; ga.n[1] = (int)ey; ga.n[2] = 1;
         int blocks = (int)std::min<int64_t>((ex * ey + 255) / 256, 152 * 16);
+        for (int k = 0; k < 27; ++k) ga.wf[k] = (float)ga.w[k];
         if (f64) generic_rule_kernel<double><<<blocks, 256, 0, st>>>(ga);
         else generic_rule_kernel<float><<<blocks, 256, 0, st>>>(ga);
         HFAV_LAUNCHED(p->rt, "generic_rule_kernel", st);
@@ -424,6 +438,7 @@ struct C3Args {
     GArr u, out;
     int nx, ny, nz, K;
     double a1[7], a2[7];   // weights: centre, +i, -i, +j, -j, +k, -k
+    float f1[7], f2[7];    // the same, rounded to FP32
     void* slab;
 };
 
@@ -436,14 +451,14 @@ __device__ __forceinline__ T ld_u3(const C3Args& a, int i, int j, int k) {
 }
 
 template <typename T>
-__device__ __forceinline__ T d7(const double* w, T ip, T im, T jp, T jm, T kp, T km, T c) {
-    T v = (T)w[1] * ip;
-    v = fma((T)w[2], im, v);
-    v = fma((T)w[3], jp, v);
-    v = fma((T)w[4], jm, v);
-    v = fma((T)w[5], kp, v);
-    v = fma((T)w[6], km, v);
-    return fma((T)w[0], c, v);
+__device__ __forceinline__ T d7(const double* w, const float* f, T ip, T im, T jp, T jm, T kp, T km, T c) {
+    T v = wsel<T>(w[1], f[1]) * ip;
+    v = fma(wsel<T>(w[2], f[2]), im, v);
+    v = fma(wsel<T>(w[3], f[3]), jp, v);
+    v = fma(wsel<T>(w[4], f[4]), jm, v);
+    v = fma(wsel<T>(w[5], f[5]), kp, v);
+    v = fma(wsel<T>(w[6], f[6]), km, v);
+    return fma(wsel<T>(w[0], f[0]), c, v);
 }
 
 // ring placement (smem or hbm): 3 planes of u, s1, s2 per CTA
@@ -481,7 +496,7 @@ __global__ void __launch_bounds__(256) chain3d_ring(const C3Args a) {
             for (int c = tid; c < P1; c += NT) {
                 int ci = c % (TX + 4) + 1, cj = c / (TX + 4) + 1;   // position in the u tile
                 int q = cj * (TX + 6) + ci;
-                o[c] = d7<T>(a.a1, u0[q + 1], u0[q - 1], u0[q + TX + 6], u0[q - TX - 6], uq[q], um[q], u0[q]);
+                o[c] = d7<T>(a.a1, a.f1, u0[q + 1], u0[q - 1], u0[q + TX + 6], u0[q - TX - 6], uq[q], um[q], u0[q]);
             }
         }
         __syncthreads();
@@ -494,7 +509,7 @@ __global__ void __launch_bounds__(256) chain3d_ring(const C3Args a) {
             for (int c = tid; c < P2; c += NT) {
                 int ci = c % (TX + 2) + 1, cj = c / (TX + 2) + 1;
                 int q = cj * (TX + 4) + ci;
-                o[c] = d7<T>(a.a2, p0[q + 1], p0[q - 1], p0[q + TX + 4], p0[q - TX - 4], pp[q], pm[q], p0[q]);
+                o[c] = d7<T>(a.a2, a.f2, p0[q + 1], p0[q - 1], p0[q + TX + 4], p0[q - TX - 4], pp[q], pm[q], p0[q]);
             }
         }
         __syncthreads();
@@ -528,15 +543,29 @@ struct C3Tile {
     static constexpr int W1 = TX + 4, H1 = TYO + 4, P1 = W1 * H1;
     static constexpr int W2 = TX + 2, H2 = TYO + 2, P2 = W2 * H2;
     static constexpr int NU = (PU + NT - 1) / NT, N1 = (P1 + NT - 1) / NT, N2 = (P2 + NT - 1) / NT;
+    // u planes are fetched ND planes ahead with asynchronous copies into a
+    // ring of ND + 2 plane buffers (the stage reads planes kk-1 and kk)
+    static constexpr int ND = 2, NB = ND + 2;
+    static constexpr size_t smem(size_t es) { return (size_t)(NB * PU + 3 * P1 + 3 * P2) * es; }
 };
+
+// asynchronous global -> shared copy of one element (cp.async, cached in L1)
+template <int BYTES>
+__device__ __forceinline__ void cp_async_el(void* dst, const void* src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 template <typename T, int TX, int TY>
 __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a) {
     using G = C3Tile<TX, TY>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* U = (T*)smem_raw;          // [2][PU]
-    T* S1 = U + 2 * G::PU;        // [2][P1]
-    T* S2 = S1 + 2 * G::P1;       // [2][P2]
+    T* U = (T*)smem_raw;          // [NB][PU] ring of u planes
+    T* S1 = U + G::NB * G::PU;    // [3][P1] ring of s1 planes
+    T* S2 = S1 + 3 * G::P1;       // [3][P2] ring of s2 planes
     const int tid = threadIdx.y * TX + threadIdx.x;
     const int i0 = blockIdx.x * TX, j0 = blockIdx.y * G::TYO, k0 = blockIdx.z * a.K;
     const T* u = (const T*)a.u.p;
@@ -570,55 +599,68 @@ __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a) {
     for (int r = 0; r < G::N2; ++r) w1[r][0] = w1[r][1] = w1[r][2] = (T)0;
 #pragma unroll
     for (int m = 0; m < G::M; ++m) w2[m][0] = w2[m][1] = w2[m][2] = (T)0;
-    const T c1 = (T)a.a1[0], p1 = (T)a.a1[1], m1 = (T)a.a1[2], q1 = (T)a.a1[3], n1 = (T)a.a1[4];
-    const T kp1 = (T)a.a1[5], km1 = (T)a.a1[6];
-    const T c2 = (T)a.a2[0], p2 = (T)a.a2[1], m2 = (T)a.a2[2], q2 = (T)a.a2[3], n2 = (T)a.a2[4];
-    const T kp2 = (T)a.a2[5], km2 = (T)a.a2[6];
-    for (int kk = k0 - 3; kk <= k0 + a.K + 2; ++kk) {
-        const int buf = kk & 1;
-        // load the u plane kk
-        int kw = kk;
-        if (a.u.wrap) kw = wrap_idx(kk, a.nz);
-        else kw = min(max(kk, -3), a.nz + 2);
-        const T* ub = u + (int64_t)(kw + a.u.org[2]) * a.u.pitch[2];
-        T* Ub = U + buf * G::PU;
+    auto w1_ = [&](int x) { return wsel<T>(a.a1[x], a.f1[x]); };
+    auto w2_ = [&](int x) { return wsel<T>(a.a2[x], a.f2[x]); };
+    const T c1w = w1_(0), p1 = w1_(1), m1 = w1_(2), q1 = w1_(3), n1 = w1_(4), kp1 = w1_(5), km1 = w1_(6);
+    const T c2w = w2_(0), p2 = w2_(1), m2 = w2_(2), q2 = w2_(3), n2 = w2_(4), kp2 = w2_(5), km2 = w2_(6);
+    // Skewed pipeline with one barrier per plane: iteration it loads the u
+    // plane kk = k0 - 3 + it and computes s1 at plane kk-1, s2 at kk-3 and
+    // out at kk-5, so every stage reads only planes written in earlier
+    // iterations.  u planes sit in a ring of NB slots (slot it % NB), s1 and
+    // s2 planes in rings of three (the plane made at iteration it in slot
+    // it % 3).
+    const int nu = a.K + 6, nit = a.K + 8;
+    auto fetch = [&](int it) {
+        if (it < nu) {
+            const int kk = k0 - 3 + it;
+            const int kw = a.u.wrap ? wrap_idx(kk, a.nz) : min(max(kk, -3), a.nz + 2);
+            const T* ub = u + (int64_t)(kw + a.u.org[2]) * a.u.pitch[2];
+            T* Ub = U + (it % G::NB) * G::PU;
 #pragma unroll
-        for (int r = 0; r < G::NU; ++r)
-            if (tid + r * G::NT < G::PU) Ub[tid + r * G::NT] = ub[gu[r]];
+            for (int r = 0; r < G::NU; ++r)
+                if (tid + r * G::NT < G::PU) cp_async_el<sizeof(T)>(Ub + tid + r * G::NT, ub + gu[r]);
+        }
+        cp_async_commit();   // one group per plane, empty past the chunk's end
+    };
+#pragma unroll
+    for (int it = 0; it < G::ND; ++it) fetch(it);
+    int c0 = 0, c1 = 1, c2 = 2;   // it % 3, (it + 1) % 3, (it + 2) % 3
+    for (int it = 0; it < nit; ++it) {
+        cp_async_wait<G::ND - 1>();   // this thread's copies of plane it are done
         __syncthreads();
-        // s1 at plane kk-1: k-neighbours from the register window, in-plane from the u plane kk-1
-        if (kk >= k0 - 1) {
-            const T* Up = U + (buf ^ 1) * G::PU;   // plane kk-1
-            T* S1b = S1 + (buf ^ 1) * G::P1;
+        // the slot of plane it + ND held plane it - 2, last read at it - 1
+        fetch(it + G::ND);
+        // s1 at plane kk-1: k-neighbours from the register window (u planes
+        // kk-2 .. kk), in-plane ones from the u plane kk-1
+        if (it < nu) {
+            const T* Ub = U + (it % G::NB) * G::PU;
+            const T* Up = U + ((it + G::NB - 1) % G::NB) * G::PU;
+            T* S1b = S1 + c0 * G::P1;
+            const bool comp = it >= 2;
 #pragma unroll
             for (int r = 0; r < G::N1; ++r) {
                 const int q = tid + r * G::NT;
                 if (q >= G::P1) continue;
                 const int b = b1_of(q);
                 wu[r][0] = wu[r][1]; wu[r][1] = wu[r][2]; wu[r][2] = Ub[b];
+                if (!comp) continue;
                 T v = p1 * Up[b + 1];
                 v = fma(m1, Up[b - 1], v);
                 v = fma(q1, Up[b + G::WU], v);
                 v = fma(n1, Up[b - G::WU], v);
                 v = fma(kp1, wu[r][2], v);
                 v = fma(km1, wu[r][0], v);
-                S1b[q] = fma(c1, wu[r][1], v);
-            }
-        } else {
-#pragma unroll
-            for (int r = 0; r < G::N1; ++r) {
-                const int q = tid + r * G::NT;
-                if (q < G::P1) { wu[r][0] = wu[r][1]; wu[r][1] = wu[r][2]; wu[r][2] = Ub[b1_of(q)]; }
+                S1b[q] = fma(c1w, wu[r][1], v);
             }
         }
-        __syncthreads();
-        // s2 at plane kk-2 from the s1 planes kk-1 (window) and kk-2 (in-plane);
-        // the window starts with s1(k0-2), produced at kk = k0-1
-        if (kk >= k0 - 1) {
-            const T* S1n = S1 + (buf ^ 1) * G::P1;   // plane kk-1
-            const T* S1p = S1 + buf * G::P1;         // plane kk-2
-            T* S2b = S2 + buf * G::P2;
-            const bool comp = kk >= k0 + 1;
+        // s2 at plane kk-3 from the s1 planes kk-2 (window push, made at
+        // it-1) and kk-3 (in-plane, made at it-2); s1 exists from plane
+        // k0-2 (it = 3) to k0+K+1 (it = K+6)
+        if (it >= 3 && it < nu + 1) {
+            const T* S1n = S1 + c2 * G::P1;
+            const T* S1p = S1 + c1 * G::P1;
+            T* S2b = S2 + c0 * G::P2;
+            const bool comp = it >= 5;
 #pragma unroll
             for (int r = 0; r < G::N2; ++r) {
                 const int q = tid + r * G::NT;
@@ -632,22 +674,21 @@ __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a) {
                 v = fma(n2, S1p[b - G::W1], v);
                 v = fma(kp2, w1[r][2], v);
                 v = fma(km2, w1[r][0], v);
-                S2b[q] = fma(c2, w1[r][1], v);
+                S2b[q] = fma(c2w, w1[r][1], v);
             }
         }
-        __syncthreads();
-        // out at plane kk-3 from the s2 planes kk-2 (window) and kk-3 (in-plane);
-        // the window starts with s2(k0-1), produced at kk = k0+1
-        if (kk >= k0 + 1) {
-            const T* S2n = S2 + buf * G::P2;           // plane kk-2
-            const T* S2p = S2 + (buf ^ 1) * G::P2;     // plane kk-3
-            const int kq = kk - 3;
+        // out at plane kk-5 from the s2 planes kk-4 (window push, made at
+        // it-1) and kk-5 (in-plane, made at it-2); s2 exists from plane k0-1 (it = 6)
+        if (it >= 6) {
+            const T* S2n = S2 + c2 * G::P2;
+            const T* S2p = S2 + c1 * G::P2;
+            const int kq = k0 - 8 + it;
 #pragma unroll
             for (int m = 0; m < G::M; ++m) {
                 const int ty = threadIdx.y + TY * m;
                 const int b = (ty + 1) * G::W2 + threadIdx.x + 1;
                 w2[m][0] = w2[m][1]; w2[m][1] = w2[m][2]; w2[m][2] = S2n[b];
-                if (kk >= k0 + 3) {
+                if (it >= 8) {
                     const T gx = S2p[b + 1] - S2p[b - 1];
                     const T gy = S2p[b + G::W2] - S2p[b - G::W2];
                     const T gz = w2[m][2] - w2[m][0];
@@ -657,13 +698,14 @@ __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a) {
                 }
             }
         }
+        const int t = c0; c0 = c1; c1 = c2; c2 = t;
     }
 }
 
 template <typename T, int TX, int TY>
 static int launch_c3regw(hfav_plan_t* p, C3Args& a, cudaStream_t st) {
     using G = C3Tile<TX, TY>;
-    const size_t sm = (size_t)2 * (G::PU + G::P1 + G::P2) * sizeof(T);
+    const size_t sm = G::smem(sizeof(T));
     int64_t tiles = (int64_t)((a.nx + TX - 1) / TX) * ((a.ny + G::TYO - 1) / G::TYO);
     int K = 16;
     while (K < 128 && tiles * ((a.nz + 2 * K - 1) / (2 * K)) >= 152 * 6) K *= 2;
@@ -693,7 +735,7 @@ __global__ void __launch_bounds__(256) chain3d_tail(const GArr s1, const GArr ou
     if (i >= nx || j >= ny || k >= nz) return;
     auto S1 = [&](int x, int y, int z) { return garr_ld<T>(s1, x, y, z); };
     auto S2 = [&](int x, int y, int z) {
-        return d7<T>(a.a2, S1(x + 1, y, z), S1(x - 1, y, z), S1(x, y + 1, z), S1(x, y - 1, z), S1(x, y, z + 1),
+        return d7<T>(a.a2, a.f2, S1(x + 1, y, z), S1(x - 1, y, z), S1(x, y + 1, z), S1(x, y - 1, z), S1(x, y, z + 1),
                      S1(x, y, z - 1), S1(x, y, z));
     };
     T gx = S2(i + 1, j, k) - S2(i - 1, j, k), gy = S2(i, j + 1, k) - S2(i, j - 1, k),
@@ -728,6 +770,7 @@ int launch_chain3d(hfav_plan_t* p, const Schedule& s, void* const* ax, void* con
     a.nx = (int)g.extent[0]; a.ny = (int)g.extent[1]; a.nz = (int)g.extent[2];
     if (!star7(m.w1, a.a1) || !star7(m.w2, a.a2))
         return set_error(HFAV_EUNSUPPORTED, "fused 3D chain takes 7-point star stencils");
+    for (int x = 0; x < 7; ++x) { a.f1[x] = (float)a.a1[x]; a.f2[x] = (float)a.a2[x]; }
     const bool f64 = p->dtype == HFAV_F64;
     const size_t es = esize(p);
     const int TX = s.tx, TY = s.ty;
@@ -756,6 +799,7 @@ int launch_chain3d(hfav_plan_t* p, const Schedule& s, void* const* ax, void* con
         for (int x = 0; x < 3; ++x) { ga.lo[x] = -fi.halo_lo[x]; ga.n[x] = (int)e[x]; }
         int64_t tot = e[0] * e[1] * e[2];
         int blocks = (int)std::min<int64_t>((tot + 255) / 256, 152 * 16);
+        for (int k = 0; k < 27; ++k) ga.wf[k] = (float)ga.w[k];
         if (f64) generic_rule_kernel<double><<<blocks, 256, 0, st>>>(ga);
         else generic_rule_kernel<float><<<blocks, 256, 0, st>>>(ga);
         HFAV_LAUNCHED(p->rt, "generic_rule_kernel", st);
@@ -830,7 +874,7 @@ double chain_warps_t(const hfav_plan_t* p, const Schedule& s) {
 #define C3W(a, b)                                                                                             \
     if (TX == a && TY == b) {                                                                                 \
         using G = C3Tile<a, b>;                                                                               \
-        return warps_of(chain3d_regw<T, a, b>, NT, (size_t)2 * (G::PU + G::P1 + G::P2) * es);                 \
+        return warps_of(chain3d_regw<T, a, b>, NT, G::smem(es));                                              \
     }
         C3W(32, 4) C3W(64, 4) C3W(128, 2) C3W(32, 8)
 #undef C3W

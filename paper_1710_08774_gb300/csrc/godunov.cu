@@ -42,11 +42,20 @@ struct GGrid {
 
 struct GCommon {
     double cfl, gamma;
+    double ig1;            // 1 / (gamma - 1)
+    float gammaf, ig1f;    // gamma and 1 / (gamma - 1) rounded to FP32 on the host, so an
+                           // FP32 kernel converts no FP64 parameter on the device
     int step;
     unsigned long long* counters;   // [0] Newton non-converged faces, [1] non-physical cells
     void* slab;                     // per-CTA-group scratch for placement hbm
     int reduce_cfl;                 // gsweep_y / gfull: fold the next step's CFL reduction in
 };
+
+template <typename T>
+__device__ __forceinline__ T csel(double d, float f) {
+    if constexpr (sizeof(T) == 8) return (T)d;
+    else return (T)f;
+}
 
 template <typename T>
 __device__ __forceinline__ T ldg_src(const GGrid<T>& G, int f, int i, int j) {
@@ -129,7 +138,7 @@ __global__ void __launch_bounds__(256) gsweep_xw(const GGrid<T>* __restrict__ gr
     const int lane = threadIdx.x & 31;
     const int w = threadIdx.x >> 5;
     const int A = blockDim.x >> 5;
-    const T g = (T)C.gamma, ig1 = (T)(1.0 / (C.gamma - 1.0));
+    const T g = csel<T>(C.gamma, C.gammaf), ig1 = csel<T>(C.ig1, C.ig1f);
     int nonconv = 0;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int2 it = items[item];
@@ -245,7 +254,7 @@ __global__ void __launch_bounds__(256) gsweep_x(const GGrid<T>* __restrict__ gri
     T* st;
     if (HBM) st = (T*)C.slab + (size_t)blockIdx.x * per;
     else st = (T*)smem_raw;
-    const T g = (T)C.gamma, ig1 = (T)(1.0 / (C.gamma - 1.0));
+    const T g = csel<T>(C.gamma, C.gammaf), ig1 = csel<T>(C.ig1, C.ig1f);
     int nonconv = 0;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int2 it = items[item];
@@ -389,7 +398,7 @@ __global__ void __launch_bounds__(256) gsweep_y(const GGrid<T>* __restrict__ gri
                                                 int n_items, const GCommon C) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int TX = blockDim.x, t = threadIdx.x, ty = threadIdx.y, TY = blockDim.y;
-    const T g = (T)C.gamma, ig1 = (T)(1.0 / (C.gamma - 1.0));
+    const T g = csel<T>(C.gamma, C.gammaf), ig1 = csel<T>(C.ig1, C.ig1f);
     const int lane_slot = ty * TX + t;
     volatile T* ring = nullptr;
     int stride = 0;
@@ -455,7 +464,7 @@ __global__ void __launch_bounds__(256) gfull(const GGrid<T>* __restrict__ grids,
                                              int n_items, const GCommon C) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int TX = blockDim.x, t = threadIdx.x, ty = threadIdx.y, TY = blockDim.y;
-    const T g = (T)C.gamma, ig1 = (T)(1.0 / (C.gamma - 1.0));
+    const T g = csel<T>(C.gamma, C.gammaf), ig1 = csel<T>(C.ig1, C.ig1f);
     const size_t per = fstage_elems<T>(TX);
     T* st = (T*)smem_raw + ty * per;
     const int WS = TX + 2;
@@ -921,6 +930,9 @@ static int run_godunov_t(hfav_plan_t* p, const Schedule& s, void* const* ax, voi
     GCommon C;
     C.cfl = gm.cfl;
     C.gamma = gm.gamma;
+    C.ig1 = 1.0 / (gm.gamma - 1.0);
+    C.gammaf = (float)C.gamma;
+    C.ig1f = (float)C.ig1;
     C.counters = rt->counters;
     C.slab = nullptr;
     C.reduce_cfl = 1;
