@@ -528,25 +528,47 @@ __global__ void __launch_bounds__(256) chain3d_ring(const C3Args a) {
     }
 }
 
-// register-window form (placement reg): the CTA's TX x TY threads own an
-// output tile TX x (TY*M), TY*M = 16 (8 for TY = 2, which keeps the
-// per-thread windows of the widest tile within the register file).  Every stage keeps, for each position
-// a thread computes, the window of its input along k in registers (three
-// planes), so only the in-plane neighbours of the previous stage go through
-// one shared plane buffer per stage (double-buffered).  Positions and their
-// shared / global offsets are fixed per thread and computed once: no integer
-// division and no periodic wrap arithmetic inside the k loop.
+// register-window form (placement reg).  The CTA's TX x TY threads own an
+// output tile of TX x TYO cells (TYO = 16; 8 for TY = 2, which keeps the
+// per-thread windows of the widest tile within the register file) and
+// stream k.  Every stage plane (u, s1, s2) is a W x R array in shared memory
+// with one width W = TX + 8 and one column numbering (column c <-> i = i0 -
+// 3 + c, stored at row * W + c + 1), so a stage evaluates its whole plane as
+// dense pairs of adjacent cells: pair q is stored at 2q, 2q + 1 and reads its
+// input plane around 2q + W (the input row below).  No index arithmetic per
+// position, 8-byte (FP32) or 16-byte (FP64) shared accesses, and no bank
+// conflicts from rows of different widths.  Columns outside the loaded u
+// columns produce meaningless s1 / s2 values that no valid cell reads: s1 is
+// valid on columns 1 .. TX+4, s2 on 2 .. TX+3, and out takes 3 .. TX+2.
+// Each stage keeps the k window (three planes) of its input at its own
+// pairs in registers; the window's middle plane is also the centre of the
+// in-plane stencil, so only the four in-plane neighbours go through shared
+// memory.
 template <int TX, int TY>
 struct C3Tile {
     static constexpr int NT = TX * TY, M = (TY >= 4 ? 16 : 8) / TY, TYO = TY * M;
-    static constexpr int WU = TX + 6, HU = TYO + 6, PU = WU * HU;
-    static constexpr int W1 = TX + 4, H1 = TYO + 4, P1 = W1 * H1;
-    static constexpr int W2 = TX + 2, H2 = TYO + 2, P2 = W2 * H2;
-    static constexpr int NU = (PU + NT - 1) / NT, N1 = (P1 + NT - 1) / NT, N2 = (P2 + NT - 1) / NT;
+    static constexpr int W = TX + 8, WL = TX + 6;   // row stride; loaded u columns
+    static constexpr int RU = TYO + 6, R1 = TYO + 4, R2 = TYO + 2;
+    static constexpr int PU = W * RU, P1 = W * R1, P2 = W * R2;
+    static constexpr int LU = WL * RU, NU = (LU + NT - 1) / NT;   // u elements loaded per plane
+    static constexpr int Q1 = P1 / 2, Q2 = P2 / 2, QO = TX * TYO / 2;   // pairs per stage
+    static constexpr int N1 = (Q1 + NT - 1) / NT, N2 = (Q2 + NT - 1) / NT, NO = QO / NT;
+    static_assert(QO % NT == 0 && TX % 2 == 0, "output pairs split evenly over the threads");
     // u planes are fetched ND planes ahead with asynchronous copies into a
-    // ring of ND + 2 plane buffers (the stage reads planes kk-1 and kk)
+    // ring of ND + 2 plane buffers (the s1 stage reads planes kk-1 and kk)
     static constexpr int ND = 2, NB = ND + 2;
     static constexpr size_t smem(size_t es) { return (size_t)(NB * PU + 3 * P1 + 3 * P2) * es; }
+};
+
+template <typename T>
+struct Pair;
+template <>
+struct Pair<float> {
+    using type = float2;
+};
+template <>
+struct Pair<double> {
+    using type = double2;
 };
 
 // asynchronous global -> shared copy of one element (cp.async, cached in L1)
@@ -559,9 +581,37 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// one 7-point star in the rule's summation order (+i, -i, +j, -j, +k, -k, centre)
+template <typename T>
+__device__ __forceinline__ T pt7(const T* w, T ip, T im, T jp, T jm, T kp, T km, T c) {
+    T v = w[1] * ip;
+    v = fma(w[2], im, v);
+    v = fma(w[3], jp, v);
+    v = fma(w[4], jm, v);
+    v = fma(w[5], kp, v);
+    v = fma(w[6], km, v);
+    return fma(w[0], c, v);
+}
+
+// out = s3 / (1 + s3), s3 = sqrt(g2) / 2.  FP64 evaluates that quotient as
+// written (IEEE square root and division); FP32 takes the equal form
+// 1 / (1 + 2 / sqrt(g2)) through the hardware reciprocal square root and
+// reciprocal (a few ulp; g2 = 0 gives 1 / inf = 0).
+template <typename T>
+__device__ __forceinline__ T chain3_out(T gx, T gy, T gz) {
+    const T g2 = fma(gx, gx, fma(gy, gy, gz * gz));
+    if constexpr (sizeof(T) == 4) {
+        return __fdividef(1.0f, fmaf(2.0f, rsqrtf(g2), 1.0f));
+    } else {
+        const T s3 = sqrt(g2) * (T)0.5;
+        return s3 / ((T)1 + s3);
+    }
+}
+
 template <typename T, int TX, int TY>
 __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a) {
     using G = C3Tile<TX, TY>;
+    using V = typename Pair<T>::type;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* U = (T*)smem_raw;          // [NB][PU] ring of u planes
     T* S1 = U + G::NB * G::PU;    // [3][P1] ring of s1 planes
@@ -569,15 +619,14 @@ __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a) {
     const int tid = threadIdx.y * TX + threadIdx.x;
     const int i0 = blockIdx.x * TX, j0 = blockIdx.y * G::TYO, k0 = blockIdx.z * a.K;
     const T* u = (const T*)a.u.p;
-    // u positions: in-plane global offset (wrapped / halo-given), 32-bit
-    // (a padded plane is far below 2^31 elements); shared offsets and the
-    // s1 / s2 positions follow from tid and compile-time strides
-    int gu[G::NU];
+    // loaded u elements: in-plane global offset (wrapped / halo-given;
+    // 32-bit, a padded plane is far below 2^31 elements) and shared offset
+    int gu[G::NU], su[G::NU];
 #pragma unroll
     for (int r = 0; r < G::NU; ++r) {
-        const int q = tid + r * G::NT;
-        const int cj = q / G::WU, ci = q - cj * G::WU;
-        int gi = i0 - 3 + ci, gj = j0 - 3 + cj;
+        const int e = min(tid + r * G::NT, G::LU - 1);
+        const int row = e / G::WL, col = e - row * G::WL;
+        int gi = i0 - 3 + col, gj = j0 - 3 + row;
         if (a.u.wrap) {
             gi = wrap_idx(gi, a.nx);
             gj = wrap_idx(gj, a.ny);
@@ -586,23 +635,36 @@ __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a) {
             gj = min(max(gj, -3), a.ny + 2);
         }
         gu[r] = (int)((int64_t)(gj + a.u.org[1]) * a.u.pitch[1] + (gi + a.u.org[0]));
+        su[r] = row * G::W + col + 1;
     }
-    // s1 position r: index q1 = tid + r NT in its (TX+4)-wide plane, at
-    // (ci+1, cj+1) of the u plane; s2 position r likewise in the s1 plane
-    auto b1_of = [&](int q) { const int cj = q / G::W1; return (cj + 1) * G::WU + (q - cj * G::W1) + 1; };
-    auto b2_of = [&](int q) { const int cj = q / G::W2; return (cj + 1) * G::W1 + (q - cj * G::W2) + 1; };
-    // output positions: thread (tx, ty) owns rows ty + TY m
-    T wu[G::N1][3], w1[G::N2][3], w2[G::M][3];
+    // output pairs: pair o = tid + r NT is row o / (TX/2), columns 3 + 2 (o % (TX/2)) and the next
+    T* op[G::NO];
+    int bo[G::NO];
+    bool ok0[G::NO], ok1[G::NO];
 #pragma unroll
-    for (int r = 0; r < G::N1; ++r) wu[r][0] = wu[r][1] = wu[r][2] = (T)0;
+    for (int r = 0; r < G::NO; ++r) {
+        const int o = tid + r * G::NT;
+        const int row = o / (TX / 2), pc = o - row * (TX / 2);
+        const int i = i0 + 2 * pc, j = j0 + row;
+        ok0[r] = i < a.nx && j < a.ny;
+        ok1[r] = i + 1 < a.nx && j < a.ny;
+        op[r] = garr_ptr<T>(a.out, min(i, a.nx - 1), min(j, a.ny - 1), min(k0, a.nz - 1));
+        bo[r] = (row + 1) * G::W + 4 + 2 * pc;
+    }
+    V wu[G::N1][3], w1[G::N2][3], w2[G::NO][3];
+    const V zero = {(T)0, (T)0};
 #pragma unroll
-    for (int r = 0; r < G::N2; ++r) w1[r][0] = w1[r][1] = w1[r][2] = (T)0;
+    for (int r = 0; r < G::N1; ++r) wu[r][0] = wu[r][1] = wu[r][2] = zero;
 #pragma unroll
-    for (int m = 0; m < G::M; ++m) w2[m][0] = w2[m][1] = w2[m][2] = (T)0;
-    auto w1_ = [&](int x) { return wsel<T>(a.a1[x], a.f1[x]); };
-    auto w2_ = [&](int x) { return wsel<T>(a.a2[x], a.f2[x]); };
-    const T c1w = w1_(0), p1 = w1_(1), m1 = w1_(2), q1 = w1_(3), n1 = w1_(4), kp1 = w1_(5), km1 = w1_(6);
-    const T c2w = w2_(0), p2 = w2_(1), m2 = w2_(2), q2 = w2_(3), n2 = w2_(4), kp2 = w2_(5), km2 = w2_(6);
+    for (int r = 0; r < G::N2; ++r) w1[r][0] = w1[r][1] = w1[r][2] = zero;
+#pragma unroll
+    for (int r = 0; r < G::NO; ++r) w2[r][0] = w2[r][1] = w2[r][2] = zero;
+    T wa[7], wb[7];
+#pragma unroll
+    for (int x = 0; x < 7; ++x) {
+        wa[x] = wsel<T>(a.a1[x], a.f1[x]);
+        wb[x] = wsel<T>(a.a2[x], a.f2[x]);
+    }
     // Skewed pipeline with one barrier per plane: iteration it loads the u
     // plane kk = k0 - 3 + it and computes s1 at plane kk-1, s2 at kk-3 and
     // out at kk-5, so every stage reads only planes written in earlier
@@ -610,6 +672,7 @@ __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a) {
     // s2 planes in rings of three (the plane made at iteration it in slot
     // it % 3).
     const int nu = a.K + 6, nit = a.K + 8;
+    const int64_t kstep = a.out.pitch[2];
     auto fetch = [&](int it) {
         if (it < nu) {
             const int kk = k0 - 3 + it;
@@ -618,7 +681,7 @@ __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a) {
             T* Ub = U + (it % G::NB) * G::PU;
 #pragma unroll
             for (int r = 0; r < G::NU; ++r)
-                if (tid + r * G::NT < G::PU) cp_async_el<sizeof(T)>(Ub + tid + r * G::NT, ub + gu[r]);
+                if (r < G::NU - 1 || tid + r * G::NT < G::LU) cp_async_el<sizeof(T)>(Ub + su[r], ub + gu[r]);
         }
         cp_async_commit();   // one group per plane, empty past the chunk's end
     };
@@ -630,8 +693,7 @@ __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a) {
         __syncthreads();
         // the slot of plane it + ND held plane it - 2, last read at it - 1
         fetch(it + G::ND);
-        // s1 at plane kk-1: k-neighbours from the register window (u planes
-        // kk-2 .. kk), in-plane ones from the u plane kk-1
+        // s1 at plane kk-1: window u(kk-2 .. kk), in-plane neighbours from u(kk-1)
         if (it < nu) {
             const T* Ub = U + (it % G::NB) * G::PU;
             const T* Up = U + ((it + G::NB - 1) % G::NB) * G::PU;
@@ -640,17 +702,17 @@ __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a) {
 #pragma unroll
             for (int r = 0; r < G::N1; ++r) {
                 const int q = tid + r * G::NT;
-                if (q >= G::P1) continue;
-                const int b = b1_of(q);
-                wu[r][0] = wu[r][1]; wu[r][1] = wu[r][2]; wu[r][2] = Ub[b];
+                if (r == G::N1 - 1 && q >= G::Q1) continue;
+                const int b = 2 * q + G::W;
+                wu[r][0] = wu[r][1]; wu[r][1] = wu[r][2]; wu[r][2] = *(const V*)(Ub + b);
                 if (!comp) continue;
-                T v = p1 * Up[b + 1];
-                v = fma(m1, Up[b - 1], v);
-                v = fma(q1, Up[b + G::WU], v);
-                v = fma(n1, Up[b - G::WU], v);
-                v = fma(kp1, wu[r][2], v);
-                v = fma(km1, wu[r][0], v);
-                S1b[q] = fma(c1w, wu[r][1], v);
+                const V n = *(const V*)(Up + b + G::W), sth = *(const V*)(Up + b - G::W);
+                const T l = Up[b - 1], rt = Up[b + 2];
+                const V c = wu[r][1];
+                V o;
+                o.x = pt7<T>(wa, c.y, l, n.x, sth.x, wu[r][2].x, wu[r][0].x, c.x);
+                o.y = pt7<T>(wa, rt, c.x, n.y, sth.y, wu[r][2].y, wu[r][0].y, c.y);
+                *(V*)(S1b + 2 * q) = o;
             }
         }
         // s2 at plane kk-3 from the s1 planes kk-2 (window push, made at
@@ -664,17 +726,17 @@ __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a) {
 #pragma unroll
             for (int r = 0; r < G::N2; ++r) {
                 const int q = tid + r * G::NT;
-                if (q >= G::P2) continue;
-                const int b = b2_of(q);
-                w1[r][0] = w1[r][1]; w1[r][1] = w1[r][2]; w1[r][2] = S1n[b];
+                if (r == G::N2 - 1 && q >= G::Q2) continue;
+                const int b = 2 * q + G::W;
+                w1[r][0] = w1[r][1]; w1[r][1] = w1[r][2]; w1[r][2] = *(const V*)(S1n + b);
                 if (!comp) continue;
-                T v = p2 * S1p[b + 1];
-                v = fma(m2, S1p[b - 1], v);
-                v = fma(q2, S1p[b + G::W1], v);
-                v = fma(n2, S1p[b - G::W1], v);
-                v = fma(kp2, w1[r][2], v);
-                v = fma(km2, w1[r][0], v);
-                S2b[q] = fma(c2w, w1[r][1], v);
+                const V n = *(const V*)(S1p + b + G::W), sth = *(const V*)(S1p + b - G::W);
+                const T l = S1p[b - 1], rt = S1p[b + 2];
+                const V c = w1[r][1];
+                V o;
+                o.x = pt7<T>(wb, c.y, l, n.x, sth.x, w1[r][2].x, w1[r][0].x, c.x);
+                o.y = pt7<T>(wb, rt, c.x, n.y, sth.y, w1[r][2].y, w1[r][0].y, c.y);
+                *(V*)(S2b + 2 * q) = o;
             }
         }
         // out at plane kk-5 from the s2 planes kk-4 (window push, made at
@@ -682,19 +744,22 @@ __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a) {
         if (it >= 6) {
             const T* S2n = S2 + c2 * G::P2;
             const T* S2p = S2 + c1 * G::P2;
-            const int kq = k0 - 8 + it;
+            const bool store = it >= 8 && k0 - 8 + it < a.nz;
 #pragma unroll
-            for (int m = 0; m < G::M; ++m) {
-                const int ty = threadIdx.y + TY * m;
-                const int b = (ty + 1) * G::W2 + threadIdx.x + 1;
-                w2[m][0] = w2[m][1]; w2[m][1] = w2[m][2]; w2[m][2] = S2n[b];
+            for (int r = 0; r < G::NO; ++r) {
+                const int b = bo[r];
+                w2[r][0] = w2[r][1]; w2[r][1] = w2[r][2]; w2[r][2] = *(const V*)(S2n + b);
                 if (it >= 8) {
-                    const T gx = S2p[b + 1] - S2p[b - 1];
-                    const T gy = S2p[b + G::W2] - S2p[b - G::W2];
-                    const T gz = w2[m][2] - w2[m][0];
-                    const T s3 = sqrt(fma(gx, gx, fma(gy, gy, gz * gz))) * (T)0.5;
-                    const int i = i0 + threadIdx.x, j = j0 + ty;
-                    if (i < a.nx && j < a.ny && kq < a.nz) *garr_ptr<T>(a.out, i, j, kq) = s3 / ((T)1 + s3);
+                    const V n = *(const V*)(S2p + b + G::W), sth = *(const V*)(S2p + b - G::W);
+                    const T l = S2p[b - 1], rt = S2p[b + 2];
+                    const V c = w2[r][1];
+                    const T x0 = chain3_out<T>(c.y - l, n.x - sth.x, w2[r][2].x - w2[r][0].x);
+                    const T x1 = chain3_out<T>(rt - c.x, n.y - sth.y, w2[r][2].y - w2[r][0].y);
+                    if (store) {
+                        if (ok0[r]) op[r][0] = x0;
+                        if (ok1[r]) op[r][1] = x1;
+                    }
+                    op[r] += kstep;
                 }
             }
         }
@@ -702,16 +767,52 @@ __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a) {
     }
 }
 
+namespace {
+int device_sms() {
+    static int sms[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    if (!sms[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+        sms[dev] = n;
+    }
+    return sms[dev];
+}
+
+// planes per CTA for the streaming 3D kernel: with `cap` CTAs resident at a
+// time, a launch takes (waves) x (K + lead) iterations; take the K that
+// minimises it (ties to the larger K: fewer re-read halo planes)
+int chunk_planes(int64_t tiles, int nz, int64_t cap, int lead) {
+    int bestK = nz;
+    double best = 1e300;
+    cap = std::max<int64_t>(cap, 1);
+    for (int n = 1; n <= std::min(nz, 1024); ++n) {
+        const int K = (nz + n - 1) / n;
+        const int64_t ctas = tiles * ((nz + K - 1) / K);
+        const double cost = (double)((ctas + cap - 1) / cap) * (K + lead);
+        if (cost < best * (1.0 - 1e-9)) { best = cost; bestK = K; }
+    }
+    return bestK;
+}
+}  // namespace
+
 template <typename T, int TX, int TY>
 static int launch_c3regw(hfav_plan_t* p, C3Args& a, cudaStream_t st) {
     using G = C3Tile<TX, TY>;
     const size_t sm = G::smem(sizeof(T));
-    int64_t tiles = (int64_t)((a.nx + TX - 1) / TX) * ((a.ny + G::TYO - 1) / G::TYO);
-    int K = 16;
-    while (K < 128 && tiles * ((a.nz + 2 * K - 1) / (2 * K)) >= 152 * 6) K *= 2;
-    a.K = K;
-    dim3 grd((a.nx + TX - 1) / TX, (a.ny + G::TYO - 1) / G::TYO, (a.nz + K - 1) / K);
     cudaFuncSetAttribute(chain3d_regw<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    static int occ = 0;   // resident CTAs per SM (same on every device of the one target)
+    if (!occ) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, chain3d_regw<T, TX, TY>, G::NT, sm) != cudaSuccess ||
+            occ <= 0) {
+            cudaGetLastError();
+            occ = 1;
+        }
+    }
+    const int64_t tiles = (int64_t)((a.nx + TX - 1) / TX) * ((a.ny + G::TYO - 1) / G::TYO);
+    a.K = chunk_planes(tiles, a.nz, (int64_t)occ * device_sms(), 8);
+    dim3 grd((a.nx + TX - 1) / TX, (a.ny + G::TYO - 1) / G::TYO, (a.nz + a.K - 1) / a.K);
     chain3d_regw<T, TX, TY><<<grd, dim3(TX, TY), sm, st>>>(a);
     HFAV_LAUNCHED(p->rt, "chain3d_fused", st);
     return HFAV_OK;
