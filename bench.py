@@ -51,8 +51,8 @@ CHAIN3D_FLOPS = 26.0     # s1 7, s2 7, s3 10, out 2
 # ncu capture of the bench's profiling case (summaries under profiles/), with
 # the hash of the kernel sources at capture time: a changed source voids it.
 TRAFFIC = {
-    ("godunov2d_fp64_1024x1024_10steps", "gsweep_y"): (34.42e6, "a6a59d5e63d25fb1"),
-    ("chain3d_fp32_512x512x512", "chain3d_fused"): (1082.6e6, "932fd0a39ec35402"),
+    ("godunov2d_fp64_1024x1024_10steps", "gsweep_y"): (33.746e6, "7d1a7d4d45e53de8"),
+    ("chain3d_fp32_512x512x512", "chain3d_fused"): (1083.5e6, "b61e8d663f3380c5"),
 }
 
 

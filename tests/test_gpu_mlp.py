@@ -74,7 +74,7 @@ def test_training_reduces_loss():
     rng = np.random.default_rng(2)
     X = rng.uniform(-1, 1, size=(600, 16)).astype(np.float32)
     y = (np.sin(2 * X[:, 0]) + X[:, 1] * X[:, 2] + 0.5 * X[:, 3] ** 2).astype(np.float32)
-    mdl = model.train(X, y, epochs=1500, lr=3e-3)
+    mdl = model.train(X, y, epochs=1500, lr=3e-3, drop=())
     assert mdl.losses[-1] < 0.05 * mdl.losses[0]
     pred = mdl.predict(X, add_base=False)
     assert np.mean((pred - y) ** 2) < 0.05 * np.var(y)
@@ -99,13 +99,16 @@ def _heldout():
         times = plan.autotune(ax, go, n_steps=1, reps=3)
         times = {k: v for k, v in times.items() if v > 0}
         pick, pred = mdl.choose(plan)
-        _HELDOUT.update(times=times, pick=pick, pred=pred)
+        F = np.array([plan.features(k) for k in times], dtype=np.float32)
+        base_pick = list(times)[int(np.argmin(model.base_log(F)))]
+        _HELDOUT.update(times=times, pick=pick, pred=pred, base_pick=base_pick)
         best = min(times.values())
         default = "full:reg:32x4"
         print("\n" + "\n".join(f"  {k} {v:.4f} ms" for k, v in sorted(times.items(), key=lambda kv: kv[1])))
         print(f"\nheld-out chain3d 512^3 fp32: exhaustive best {min(times, key=times.get)} {best:.4f} ms; "
               f"model pick {pick} {times[pick]:.4f} ms (x{times[pick] / best:.3f} of best); default {default} "
-              f"{times[default]:.4f} ms (model gains x{times[default] / times[pick]:.3f})")
+              f"{times[default]:.4f} ms (model gains x{times[default] / times[pick]:.3f}); analytic estimate alone "
+              f"{base_pick} {times[base_pick]:.4f} ms (network gains x{times[base_pick] / times[pick]:.3f})")
     return _HELDOUT
 
 
@@ -120,9 +123,22 @@ def test_model_choice_on_heldout_3d_chain_picks_full_fusion():
     assert t[h["pick"]] * 3.0 <= slow
 
 
-@pytest.mark.xfail(strict=False, reason="the network's correction, learned on the 2D kernels (where shared-memory "
-                   "rings beat register windows), misranks placements of the 3D kernels; the pick is within "
-                   "about 1.6x of the exhaustive best, not 10%")
 def test_model_choice_on_heldout_3d_chain_within_10pct():
+    """The model's pick for the held-out 3D chain runs within 10% of the
+    exhaustively tuned best schedule."""
     h = _heldout()
     assert h["times"][h["pick"]] <= 1.10 * min(h["times"].values())
+
+
+def test_dropped_features_transfer_better_across_families():
+    """The feature columns the network leaves out (placement one-hots and
+    occupancy) are left out because, trained on one family and choosing for
+    the other, the network picks better without them (geometric mean of
+    pick / best over the held family's workloads; training data only)."""
+    from paper_1710_08774_gb300 import model
+    rows = model.load_corpus()
+    X, y = model.features_of(rows)
+    without = model.cross_family(rows, X, y)
+    with_all = model.cross_family(rows, X, y, drop=())
+    print(f"\ncross-family pick / best (geomean): without {without}, with all features {with_all}")
+    assert sum(np.log(list(without.values()))) <= sum(np.log(list(with_all.values())))
