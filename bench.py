@@ -280,6 +280,12 @@ def make(name, H, I, torch, dev):
         return Chain(H, I, torch, dev, 2, 256, "f64", 0)
     if name == "chain3d512_f32":
         return Chain(H, I, torch, dev, 3, 512, "f32", 4)
+    # other sizes of the chains (the 2D chain's large-grid sweep): chain2d<N>_f64, chain3d<N>_f32, ...
+    import re
+    m = re.fullmatch(r"chain([23])d(\d+)_(f32|f64)", name)
+    if m:
+        dims = int(m.group(1))
+        return Chain(H, I, torch, dev, dims, int(m.group(2)), m.group(3), 0 if dims == 2 else 4)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -520,7 +526,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="godunov1024_f64", choices=WORKLOADS + ["all"])
+    ap.add_argument("--workload", default=WORKLOADS[0], help="one of " + ", ".join(WORKLOADS + ["all"]) + ", or chain2d<N>_f32|f64 / chain3d<N>_f32|f64 (other chain sizes)")
     ap.add_argument("--schedule", default=None, help="fixed schedule (default: autotuned among fused ones)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--once", action="store_true", help="profiling case: build the plan and run it once")

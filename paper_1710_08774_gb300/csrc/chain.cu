@@ -178,6 +178,7 @@ struct C2Args {
     double wc, wip, wim, wjp, wjm;   // 5-point star weights
     float fc, fip, fim, fjp, fjm;    // the same, rounded to FP32
     void* slab;                      // hbm placement: per-CTA rings
+    int nstrips, sh, vec, vecout;    // reg placement: warp strips, strip origin shift, 16-byte paths
 };
 
 // L at one point from its five star neighbours, summed in the rule's order
@@ -263,64 +264,152 @@ __global__ void __launch_bounds__(256) chain2d_ring(const C2Args a) {
     }
 }
 
-// reg placement: vertical windows in registers, one shared row per stage.
-// Rows are loaded C2_PD iterations ahead into a register queue so that
-// several rows' loads are in flight per thread (the row loop itself
-// synchronises the CTA twice per row and would otherwise expose the full
-// memory latency on every row).
+// reg placement: warp strips.  Each warp owns a strip of 32 V consecutive
+// columns (V = 16 bytes / element size: 4 floats or 2 doubles; lane l holds
+// columns s0 + V l .. s0 + V l + V - 1) and streams a chunk of R rows.  The
+// u and L windows (three rows each) are registers, the i-neighbours cross
+// lanes by shuffle, and the strip's first and last lanes also carry the two
+// columns beyond the strip (their u, and L one column out).  No shared
+// memory and no barriers.  Rows are loaded three rows ahead; the row loop is
+// unrolled by three so the windows rotate by renaming.  Loads and stores are
+// 16-byte vectors where a lane's columns lie inside the array's rows (the
+// strip origin s0 is shifted so that they are aligned), scalars with the
+// periodic wrap elsewhere.
 template <typename T>
-__global__ void __launch_bounds__(256) chain2d_reg(const C2Args a) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int TX = blockDim.x, t = threadIdx.x, ty = threadIdx.y;
-    const int i0 = blockIdx.x * TX, i = i0 + t;
-    const int j0 = (blockIdx.y * blockDim.y + ty) * a.R;
-    const int WU = TX + 4, WL = TX + 2;
-    T* su = (T*)smem_raw + ty * (WU + 2 * WL);   // u row r-1, columns i0-2 .. i0+TX+1
-    T* sL = su + WU;                             // [2][WL] L rows, double buffered
-    // own column window u(r-2), u(r-1), u(r); L(r-3), L(r-2), L(r-1)
-    T u0 = 0, u1 = 0, u2 = 0, l0 = 0, l1 = 0, l2 = 0;
-    // edge threads also carry the window of one halo column and load the
-    // second halo column's row r-1
-    const bool left = (t == 0), right = (t == TX - 1);
-    const int ie = left ? i0 - 1 : i0 + TX;
-    const int ih = left ? i0 - 2 : i0 + TX + 1;
-    T e0 = 0, e1 = 0, e2 = 0;
-    T q[C2_PD], qe[C2_PD], qh[C2_PD];
-#pragma unroll
-    for (int k = 0; k < C2_PD; ++k) {
-        q[k] = ld_u<T>(a, i, j0 - 2 + k);
-        qe[k] = (left || right) ? ld_u<T>(a, ie, j0 - 2 + k) : (T)0;
-        qh[k] = (left || right) ? ld_u<T>(a, ih, j0 - 3 + k) : (T)0;
+struct alignas(16) VRow {
+    static constexpr int V = 16 / (int)sizeof(T);
+    T v[V];
+};
+
+template <typename T>
+__device__ __forceinline__ T c2_squash(T gx, T gy) {
+    const T g2 = fma(gx, gx, gy * gy);
+    if constexpr (sizeof(T) == 4) {
+        // G / (1 + G), G = sqrt(g2) / 2, as the equal 1 / (1 + 2 / sqrt(g2)) through the
+        // hardware reciprocal square root and reciprocal (g2 = 0 gives 1 / inf = 0)
+        return __fdividef(1.0f, fmaf(2.0f, rsqrtf(g2), 1.0f));
+    } else {
+        const T G = sqrt(g2) * (T)0.5;
+        return G / ((T)1 + G);
     }
-    for (int r = j0 - 2; r <= j0 + a.R + 1; ++r) {
-        u0 = u1; u1 = u2; u2 = q[0];
-        const T hnew = qh[0];
-        if (left || right) { e0 = e1; e1 = e2; e2 = qe[0]; }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) chain2d_warp(const C2Args a) {
+    constexpr int V = VRow<T>::V;
+    using Row = VRow<T>;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, lane = tid & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * (blockDim.x * blockDim.y) + tid) >> 5;
+    const int strip = (int)(wid % a.nstrips);
+    const int j0 = (int)(wid / a.nstrips) * a.R;
+    if (j0 >= a.ny) return;   // whole warp
+    const int s0 = strip * 32 * V - a.sh;
+    const int c0 = s0 + V * lane;   // first own column
+    const bool el = lane == 0, er = lane == 31, edge = el || er;
+    const int ce = el ? s0 - 2 : s0 + 32 * V;   // first of the two columns beyond the strip
+    const T* u = (const T*)a.u.p;
+    const bool wrap = a.u.wrap;
+    const bool vin = a.vec && (wrap ? (c0 >= 0 && c0 + V <= a.nx) : (c0 >= -2 && c0 + V <= a.nx + 2));
+    const bool vout = a.vecout && c0 >= 0 && c0 + V <= a.nx;
+    auto col = [&](const T* ub, int c) -> T {
+        if (wrap) return ub[wrap1(c, a.nx)];
+        return (c >= -2 && c < a.nx + 2) ? ub[c] : (T)0;
+    };
+    // u row r: own columns and (first / last lane) the two columns beyond the strip
+    auto load_row = [&](int r, Row& x, T& e0, T& e1) {
+        int jr = r;
+        if (wrap) jr = wrap1(r, a.ny);
+        else if (r < -2 || r >= a.ny + 2) {
 #pragma unroll
-        for (int k = 0; k + 1 < C2_PD; ++k) { q[k] = q[k + 1]; qe[k] = qe[k + 1]; qh[k] = qh[k + 1]; }
-        q[C2_PD - 1] = ld_u<T>(a, i, r + C2_PD);
-        if (left || right) {
-            qe[C2_PD - 1] = ld_u<T>(a, ie, r + C2_PD);
-            qh[C2_PD - 1] = ld_u<T>(a, ih, r - 1 + C2_PD);
+            for (int e = 0; e < V; ++e) x.v[e] = (T)0;
+            e0 = e1 = (T)0;
+            return;
         }
-        su[t + 2] = u1;
-        if (left) { su[1] = e1; su[0] = hnew; }
-        if (right) { su[TX + 2] = e1; su[TX + 3] = hnew; }
-        __syncthreads();
-        if (r >= j0) {
-            T* Lr = sL + ((r - 1) & 1) * WL;
-            T L = lap5<T>(a, su[t + 3], su[t + 1], u2, u0, u1);
-            l0 = l1; l1 = l2; l2 = L;
-            Lr[t + 1] = L;
-            if (left) Lr[0] = lap5<T>(a, su[2], su[0], e2, e0, e1);
-            if (right) Lr[TX + 1] = lap5<T>(a, su[TX + 3], su[TX + 1], e2, e0, e1);
+        const T* ub = u + (int64_t)(jr + a.u.org[1]) * a.u.pitch[1] + a.u.org[0];
+        if (vin) {
+            x = *(const Row*)(ub + c0);
+        } else {
+#pragma unroll
+            for (int e = 0; e < V; ++e) x.v[e] = col(ub, c0 + e);
         }
-        __syncthreads();
-        if (r >= j0 + 2) {
-            const int j = r - 2;
-            const T* L0 = sL + ((r - 2) & 1) * WL;
-            T o = grad_squash<T>(L0[t + 2], L0[t], l2, l0);
-            if (i < a.nx && j < a.ny) *garr_ptr<T>(a.out, i, j, 0) = o;
+        if (edge) {
+            e0 = col(ub, ce);
+            e1 = col(ub, ce + 1);
+        }
+    };
+    const T wc = wsel<T>(a.wc, a.fc), wip = wsel<T>(a.wip, a.fip), wim = wsel<T>(a.wim, a.fim);
+    const T wjp = wsel<T>(a.wjp, a.fjp), wjm = wsel<T>(a.wjm, a.fjm);
+    auto lap = [&](T ip, T im, T jp, T jm, T c) {
+        T v = wip * ip;
+        v = fma(wim, im, v);
+        v = fma(wjp, jp, v);
+        v = fma(wjm, jm, v);
+        return fma(wc, c, v);
+    };
+    // rows j0-2 .. rend stream through; out rows j0 .. rend-2
+    const int rend = min(j0 + a.R, a.ny) + 1;
+    const int n = rend - (j0 - 2) + 1;
+    Row Q[3], U[3], L[3];
+    T QE[3][2], EU[3][2], EL[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) {
+        QE[s][0] = QE[s][1] = EU[s][0] = EU[s][1] = EL[s] = (T)0;
+        load_row(j0 - 2 + s, Q[s], QE[s][0], QE[s][1]);
+    }
+    T* outp = (T*)a.out.p;
+    for (int t0 = 0; t0 < n; t0 += 3) {
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            const int t = t0 + s;
+            if (t >= n) break;
+            const int r = j0 - 2 + t;
+            // slots: s holds row r (u) / r-1 (L); (s+2)%3 row r-1 / r-2; (s+1)%3 row r-2 / r-3
+            const int s1 = (s + 1) % 3, s2 = (s + 2) % 3;
+            U[s] = Q[s];
+            EU[s][0] = QE[s][0];
+            EU[s][1] = QE[s][1];
+            if (r + 3 <= rend) load_row(r + 3, Q[s], QE[s][0], QE[s][1]);
+            if (t >= 2) {   // L at row r-1 from u rows r-2, r-1, r
+                const Row& um = U[s1];
+                const Row& u0 = U[s2];
+                const Row& up = U[s];
+                T left = __shfl_up_sync(0xffffffffu, u0.v[V - 1], 1);
+                T right = __shfl_down_sync(0xffffffffu, u0.v[0], 1);
+                if (el) left = EU[s2][1];
+                if (er) right = EU[s2][0];
+                Row Lr;
+#pragma unroll
+                for (int e = 0; e < V; ++e)
+                    Lr.v[e] = lap(e + 1 < V ? u0.v[e + 1] : right, e > 0 ? u0.v[e - 1] : left, up.v[e], um.v[e], u0.v[e]);
+                L[s] = Lr;
+                if (edge) {   // L one column beyond the strip
+                    EL[s] = el ? lap(u0.v[0], EU[s2][0], EU[s][1], EU[s1][1], EU[s2][1])
+                               : lap(EU[s2][1], u0.v[V - 1], EU[s][0], EU[s1][0], EU[s2][0]);
+                }
+            }
+            if (t >= 4) {   // out at row r-2 from L rows r-3, r-2, r-1
+                const Row& Lm = L[s1];
+                const Row& L0 = L[s2];
+                const Row& Lp = L[s];
+                T left = __shfl_up_sync(0xffffffffu, L0.v[V - 1], 1);
+                T right = __shfl_down_sync(0xffffffffu, L0.v[0], 1);
+                if (el) left = EL[s2];
+                if (er) right = EL[s2];
+                Row o;
+#pragma unroll
+                for (int e = 0; e < V; ++e)
+                    o.v[e] = c2_squash<T>((e + 1 < V ? L0.v[e + 1] : right) - (e > 0 ? L0.v[e - 1] : left),
+                                          Lp.v[e] - Lm.v[e]);
+                const int j = r - 2;
+                T* ob = outp + (int64_t)(j + a.out.org[1]) * a.out.pitch[1] + a.out.org[0];
+                if (vout) {
+                    *(Row*)(ob + c0) = o;
+                } else {
+#pragma unroll
+                    for (int e = 0; e < V; ++e)
+                        if (c0 + e >= 0 && c0 + e < a.nx) ob[c0 + e] = o.v[e];
+                }
+            }
         }
     }
 }
@@ -346,6 +435,37 @@ int rows_per_thread(int64_t cells, int lo, int hi) {
     return R;
 }
 }  // namespace
+
+namespace {
+int chunk_planes(int64_t tiles, int nz, int64_t cap, int lead);
+int device_sms();
+}  // namespace
+
+template <typename T>
+static int launch_c2warp(hfav_plan_t* p, C2Args& a, int TX, int TY, cudaStream_t st) {
+    constexpr int V = VRow<T>::V;
+    const int NT = TX * TY;
+    a.sh = ((a.u.org[0] % V) + V) % V;
+    a.vec = ((uintptr_t)a.u.p % 16 == 0) && (a.u.pitch[1] % V == 0);
+    a.vecout = ((uintptr_t)a.out.p % 16 == 0) && (a.out.pitch[1] % V == 0) && (((a.out.org[0] % V) + V) % V == a.sh);
+    a.nstrips = (a.nx + a.sh + 32 * V - 1) / (32 * V);
+    static int occ = 0;   // resident CTAs per SM at NT threads (same on every device of the one target)
+    static int occ_nt = 0;
+    if (occ_nt != NT) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, chain2d_warp<T>, NT, 0) != cudaSuccess || occ <= 0) {
+            cudaGetLastError();
+            occ = 1;
+        }
+        occ_nt = NT;
+    }
+    // rows per warp: the fewest waves of resident warps times rows (+4 halo rows each)
+    a.R = chunk_planes(a.nstrips, a.ny, (int64_t)occ * (NT / 32) * device_sms(), 4);
+    const int64_t warps = (int64_t)a.nstrips * ((a.ny + a.R - 1) / a.R);
+    const int64_t blocks = (warps + NT / 32 - 1) / (NT / 32);
+    chain2d_warp<T><<<(unsigned)blocks, dim3(TX, TY), 0, st>>>(a);
+    HFAV_LAUNCHED(p->rt, "chain2d_fused", st);
+    return HFAV_OK;
+}
 
 int launch_chain2d(hfav_plan_t* p, const Schedule& s, void* const* ax, void* const* go, cudaStream_t st) {
     if (s.fusion == FUSE_UNFUSED) return launch_generic(p, ax, go, st);
@@ -408,11 +528,9 @@ int launch_chain2d(hfav_plan_t* p, const Schedule& s, void* const* ax, void* con
     const int TX = s.tx, TY = s.ty;
     dim3 blk(TX, TY);
     dim3 grd((nx + TX - 1) / TX, (ny + a.R * TY - 1) / (a.R * TY));
-    if (s.placement == PLACE_REG) {
-        size_t sm = (size_t)TY * ((TX + 4) + 2 * (TX + 2)) * es;
-        if (f64) chain2d_reg<double><<<grd, blk, sm, st>>>(a);
-        else chain2d_reg<float><<<grd, blk, sm, st>>>(a);
-    } else if (s.placement == PLACE_SMEM) {
+    if (s.placement == PLACE_REG)
+        return f64 ? launch_c2warp<double>(p, a, TX, TY, st) : launch_c2warp<float>(p, a, TX, TY, st);
+    if (s.placement == PLACE_SMEM) {
         size_t sm = (size_t)TY * (3 * (TX + 4) + 3 * (TX + 2)) * es;
         if (f64) chain2d_ring<double, false><<<grd, blk, sm, st>>>(a);
         else chain2d_ring<float, false><<<grd, blk, sm, st>>>(a);
@@ -965,7 +1083,7 @@ double chain_warps_t(const hfav_plan_t* p, const Schedule& s) {
     if (s.fusion == FUSE_UNFUSED) return warps_of(generic_rule_kernel<T>, 256, 0);
     if (p->pipeline == PIPE_CHAIN2D) {
         if (s.fusion == FUSE_SWEEP) return warps_of(chain2d_tail<T>, NT, 0);
-        if (s.placement == PLACE_REG) return warps_of(chain2d_reg<T>, NT, (size_t)TY * ((TX + 4) + 2 * (TX + 2)) * es);
+        if (s.placement == PLACE_REG) return warps_of(chain2d_warp<T>, NT, 0);
         if (s.placement == PLACE_SMEM)
             return warps_of(chain2d_ring<T, false>, NT, (size_t)TY * (3 * (TX + 4) + 3 * (TX + 2)) * es);
         return warps_of(chain2d_ring<T, true>, NT, 0);
