@@ -275,6 +275,17 @@ __global__ void __launch_bounds__(256) chain2d_ring(const C2Args a) {
 // 16-byte vectors where a lane's columns lie inside the array's rows (the
 // strip origin s0 is shifted so that they are aligned), scalars with the
 // periodic wrap elsewhere.
+// s / (1 + s) for s = sqrt(g2) / 2, FP32: the equal 1 / (1 + 2 / sqrt(g2))
+// with the hardware reciprocal square root and reciprocal (PTX rsqrt.approx
+// and rcp.approx, flush-to-zero: relative error a few 2^-23; g2 = 0 or
+// subnormal gives 1 / inf = 0)
+__device__ __forceinline__ float squash_rsqrt_f32(float g2) {
+    float r, o;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(g2));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(o) : "f"(fmaf(2.0f, r, 1.0f)));
+    return o;
+}
+
 template <typename T>
 struct alignas(16) VRow {
     static constexpr int V = 16 / (int)sizeof(T);
@@ -285,46 +296,36 @@ template <typename T>
 __device__ __forceinline__ T c2_squash(T gx, T gy) {
     const T g2 = fma(gx, gx, gy * gy);
     if constexpr (sizeof(T) == 4) {
-        // G / (1 + G), G = sqrt(g2) / 2, as the equal 1 / (1 + 2 / sqrt(g2)) through the
-        // hardware reciprocal square root and reciprocal (g2 = 0 gives 1 / inf = 0)
-        return __fdividef(1.0f, fmaf(2.0f, rsqrtf(g2), 1.0f));
+        return squash_rsqrt_f32(g2);
     } else {
         const T G = sqrt(g2) * (T)0.5;
         return G / ((T)1 + G);
     }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(256) chain2d_warp(const C2Args a) {
+// one warp's strip; INT: the strip and the two columns on each side lie
+// inside the rows and the 16-byte paths are open (no column wrap, no
+// per-element fallbacks: the common case, compiled without those branches)
+template <typename T, bool INT>
+__device__ __forceinline__ void c2w_strip(const C2Args& a, int lane, int s0, int j0) {
     constexpr int V = VRow<T>::V;
     using Row = VRow<T>;
-    const int tid = threadIdx.y * blockDim.x + threadIdx.x, lane = tid & 31;
-    const int64_t wid = ((int64_t)blockIdx.x * (blockDim.x * blockDim.y) + tid) >> 5;
-    const int strip = (int)(wid % a.nstrips);
-    const int j0 = (int)(wid / a.nstrips) * a.R;
-    if (j0 >= a.ny) return;   // whole warp
-    const int s0 = strip * 32 * V - a.sh;
     const int c0 = s0 + V * lane;   // first own column
     const bool el = lane == 0, er = lane == 31, edge = el || er;
     const int ce = el ? s0 - 2 : s0 + 32 * V;   // first of the two columns beyond the strip
     const T* u = (const T*)a.u.p;
     const bool wrap = a.u.wrap;
-    const bool vin = a.vec && (wrap ? (c0 >= 0 && c0 + V <= a.nx) : (c0 >= -2 && c0 + V <= a.nx + 2));
-    const bool vout = a.vecout && c0 >= 0 && c0 + V <= a.nx;
+    const bool vin = INT || (a.vec && (wrap ? (c0 >= 0 && c0 + V <= a.nx) : (c0 >= -2 && c0 + V <= a.nx + 2)));
+    const bool vout = INT || (a.vecout && c0 >= 0 && c0 + V <= a.nx);
     auto col = [&](const T* ub, int c) -> T {
+        if (INT) return ub[c];
         if (wrap) return ub[wrap1(c, a.nx)];
         return (c >= -2 && c < a.nx + 2) ? ub[c] : (T)0;
     };
-    // u row r: own columns and (first / last lane) the two columns beyond the strip
+    // u row r (always within -2 .. ny+1): own columns and (first / last
+    // lane) the two columns beyond the strip
     auto load_row = [&](int r, Row& x, T& e0, T& e1) {
-        int jr = r;
-        if (wrap) jr = wrap1(r, a.ny);
-        else if (r < -2 || r >= a.ny + 2) {
-#pragma unroll
-            for (int e = 0; e < V; ++e) x.v[e] = (T)0;
-            e0 = e1 = (T)0;
-            return;
-        }
+        const int jr = wrap ? wrap1(r, a.ny) : r;
         const T* ub = u + (int64_t)(jr + a.u.org[1]) * a.u.pitch[1] + a.u.org[0];
         if (vin) {
             x = *(const Row*)(ub + c0);
@@ -412,6 +413,25 @@ __global__ void __launch_bounds__(256) chain2d_warp(const C2Args a) {
             }
         }
     }
+}
+
+#ifdef C2W_MINB
+#define C2W_LB __launch_bounds__(256, C2W_MINB)
+#else
+#define C2W_LB __launch_bounds__(256)
+#endif
+template <typename T>
+__global__ void C2W_LB chain2d_warp(const C2Args a) {
+    constexpr int V = VRow<T>::V;
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, lane = tid & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * (blockDim.x * blockDim.y) + tid) >> 5;
+    const int strip = (int)(wid % a.nstrips);
+    const int j0 = (int)(wid / a.nstrips) * a.R;
+    if (j0 >= a.ny) return;   // whole warp
+    const int s0 = strip * 32 * V - a.sh;
+    const bool inside = a.u.wrap ? (s0 >= 2 && s0 + 32 * V + 2 <= a.nx) : (s0 >= 0 && s0 + 32 * V <= a.nx);
+    if (a.vec && a.vecout && inside) c2w_strip<T, true>(a, lane, s0, j0);
+    else c2w_strip<T, false>(a, lane, s0, j0);
 }
 
 // tail of the "sweep" schedule: G and out from a materialised L (halo 1)
@@ -713,13 +733,12 @@ __device__ __forceinline__ T pt7(const T* w, T ip, T im, T jp, T jm, T kp, T km,
 
 // out = s3 / (1 + s3), s3 = sqrt(g2) / 2.  FP64 evaluates that quotient as
 // written (IEEE square root and division); FP32 takes the equal form
-// 1 / (1 + 2 / sqrt(g2)) through the hardware reciprocal square root and
-// reciprocal (a few ulp; g2 = 0 gives 1 / inf = 0).
+// 1 / (1 + 2 / sqrt(g2)) (squash_rsqrt_f32).
 template <typename T>
 __device__ __forceinline__ T chain3_out(T gx, T gy, T gz) {
     const T g2 = fma(gx, gx, fma(gy, gy, gz * gz));
     if constexpr (sizeof(T) == 4) {
-        return __fdividef(1.0f, fmaf(2.0f, rsqrtf(g2), 1.0f));
+        return squash_rsqrt_f32(g2);
     } else {
         const T s3 = sqrt(g2) * (T)0.5;
         return s3 / ((T)1 + s3);
