@@ -14,6 +14,7 @@
 // runs one kernel per rule over full arrays (launch_generic).
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -311,9 +312,10 @@ __device__ __forceinline__ void c2w_strip(const C2Args& a, int lane, int s0, int
     constexpr int V = VRow<T>::V;
     using Row = VRow<T>;
     const int c0 = s0 + V * lane;   // first own column
-    const bool el = lane == 0, er = lane == 31, edge = el || er;
-    const int ce = el ? s0 - 2 : s0 + 32 * V;   // first of the two columns beyond the strip
-    const T* u = (const T*)a.u.p;
+    const bool el = lane == 0, er = lane == 31;
+    // the two columns beyond the strip on this lane's side (first / last
+    // lane): `near` next to the strip, `far` one further
+    const int cn = el ? s0 - 1 : s0 + 32 * V, cf = el ? s0 - 2 : s0 + 32 * V + 1;
     const bool wrap = a.u.wrap;
     const bool vin = INT || (a.vec && (wrap ? (c0 >= 0 && c0 + V <= a.nx) : (c0 >= -2 && c0 + V <= a.nx + 2)));
     const bool vout = INT || (a.vecout && c0 >= 0 && c0 + V <= a.nx);
@@ -322,21 +324,29 @@ __device__ __forceinline__ void c2w_strip(const C2Args& a, int lane, int s0, int
         if (wrap) return ub[wrap1(c, a.nx)];
         return (c >= -2 && c < a.nx + 2) ? ub[c] : (T)0;
     };
-    // u row r (always within -2 .. ny+1): own columns and (first / last
-    // lane) the two columns beyond the strip
-    auto load_row = [&](int r, Row& x, T& e0, T& e1) {
-        const int jr = wrap ? wrap1(r, a.ny) : r;
-        const T* ub = u + (int64_t)(jr + a.u.org[1]) * a.u.pitch[1] + a.u.org[0];
+    // row pointers advance by one pitch per row; under the periodic wrap they
+    // are recomputed for rows outside 0 .. ny-1 (rows run over -2 .. ny+1)
+    const int64_t pu = a.u.pitch[1], po = a.out.pitch[1];
+    const T* row0 = (const T*)a.u.p + (int64_t)a.u.org[1] * pu + a.u.org[0];
+    int rl = j0 - 2;   // next row to load
+    const T* lp = row0 + (int64_t)(wrap ? wrap1(rl, a.ny) : rl) * pu;
+    auto load_next = [&](Row& x, T& en, T& ef) {
         if (vin) {
-            x = *(const Row*)(ub + c0);
+            x = *(const Row*)(lp + c0);
         } else {
 #pragma unroll
-            for (int e = 0; e < V; ++e) x.v[e] = col(ub, c0 + e);
+            for (int e = 0; e < V; ++e) x.v[e] = col(lp, c0 + e);
         }
-        if (edge) {
-            e0 = col(ub, ce);
-            e1 = col(ub, ce + 1);
+        if (INT) {   // every lane reads them (in bounds); only lanes 0 and 31 use them
+            en = lp[cn];
+            ef = lp[cf];
+        } else if (el || er) {
+            en = col(lp, cn);
+            ef = col(lp, cf);
         }
+        ++rl;
+        lp += pu;
+        if (wrap && (rl <= 0 || rl >= a.ny)) lp = row0 + (int64_t)wrap1(rl, a.ny) * pu;
     };
     const T wc = wsel<T>(a.wc, a.fc), wip = wsel<T>(a.wip, a.fip), wim = wsel<T>(a.wim, a.fim);
     const T wjp = wsel<T>(a.wjp, a.fjp), wjm = wsel<T>(a.wjm, a.fjm);
@@ -347,71 +357,87 @@ __device__ __forceinline__ void c2w_strip(const C2Args& a, int lane, int s0, int
         v = fma(wjm, jm, v);
         return fma(wc, c, v);
     };
-    // rows j0-2 .. rend stream through; out rows j0 .. rend-2
+    // rows j0-2 .. rend stream through (step t handles row j0-2+t); out rows j0 .. rend-2
     const int rend = min(j0 + a.R, a.ny) + 1;
     const int n = rend - (j0 - 2) + 1;
     Row Q[3], U[3], L[3];
-    T QE[3][2], EU[3][2], EL[3];
+    T QN[3], QF[3], UN[3], UF[3], EL[3];
 #pragma unroll
     for (int s = 0; s < 3; ++s) {
-        QE[s][0] = QE[s][1] = EU[s][0] = EU[s][1] = EL[s] = (T)0;
-        load_row(j0 - 2 + s, Q[s], QE[s][0], QE[s][1]);
+        QN[s] = QF[s] = UN[s] = UF[s] = EL[s] = (T)0;
+        load_next(Q[s], QN[s], QF[s]);   // n >= 4: rows j0-2 .. j0 exist
     }
-    T* outp = (T*)a.out.p;
-    for (int t0 = 0; t0 < n; t0 += 3) {
+    T* op = (T*)a.out.p + (int64_t)(j0 + a.out.org[1]) * po + a.out.org[0];
+    // one step; S = t % 3 (window slot of row t), the flags say which parts run
+    auto step = [&](auto S, bool pf, bool do_l, bool do_out) {
+        constexpr int s = decltype(S)::value, s1 = (s + 1) % 3, s2 = (s + 2) % 3;
+        // slots: s holds row r (u) / r-1 (L); s2 row r-1 / r-2; s1 row r-2 / r-3
+        U[s] = Q[s];
+        UN[s] = QN[s];
+        UF[s] = QF[s];
+        if (pf) load_next(Q[s], QN[s], QF[s]);
+        if (do_l) {   // L at row r-1 from u rows r-2, r-1, r
+            const Row& um = U[s1];
+            const Row& u0 = U[s2];
+            const Row& up = U[s];
+            T left = __shfl_up_sync(0xffffffffu, u0.v[V - 1], 1);
+            T right = __shfl_down_sync(0xffffffffu, u0.v[0], 1);
+            if (el) left = UN[s2];
+            if (er) right = UN[s2];
+            Row Lr;
 #pragma unroll
-        for (int s = 0; s < 3; ++s) {
-            const int t = t0 + s;
-            if (t >= n) break;
-            const int r = j0 - 2 + t;
-            // slots: s holds row r (u) / r-1 (L); (s+2)%3 row r-1 / r-2; (s+1)%3 row r-2 / r-3
-            const int s1 = (s + 1) % 3, s2 = (s + 2) % 3;
-            U[s] = Q[s];
-            EU[s][0] = QE[s][0];
-            EU[s][1] = QE[s][1];
-            if (r + 3 <= rend) load_row(r + 3, Q[s], QE[s][0], QE[s][1]);
-            if (t >= 2) {   // L at row r-1 from u rows r-2, r-1, r
-                const Row& um = U[s1];
-                const Row& u0 = U[s2];
-                const Row& up = U[s];
-                T left = __shfl_up_sync(0xffffffffu, u0.v[V - 1], 1);
-                T right = __shfl_down_sync(0xffffffffu, u0.v[0], 1);
-                if (el) left = EU[s2][1];
-                if (er) right = EU[s2][0];
-                Row Lr;
-#pragma unroll
-                for (int e = 0; e < V; ++e)
-                    Lr.v[e] = lap(e + 1 < V ? u0.v[e + 1] : right, e > 0 ? u0.v[e - 1] : left, up.v[e], um.v[e], u0.v[e]);
-                L[s] = Lr;
-                if (edge) {   // L one column beyond the strip
-                    EL[s] = el ? lap(u0.v[0], EU[s2][0], EU[s][1], EU[s1][1], EU[s2][1])
-                               : lap(EU[s2][1], u0.v[V - 1], EU[s][0], EU[s1][0], EU[s2][0]);
-                }
-            }
-            if (t >= 4) {   // out at row r-2 from L rows r-3, r-2, r-1
-                const Row& Lm = L[s1];
-                const Row& L0 = L[s2];
-                const Row& Lp = L[s];
-                T left = __shfl_up_sync(0xffffffffu, L0.v[V - 1], 1);
-                T right = __shfl_down_sync(0xffffffffu, L0.v[0], 1);
-                if (el) left = EL[s2];
-                if (er) right = EL[s2];
-                Row o;
-#pragma unroll
-                for (int e = 0; e < V; ++e)
-                    o.v[e] = c2_squash<T>((e + 1 < V ? L0.v[e + 1] : right) - (e > 0 ? L0.v[e - 1] : left),
-                                          Lp.v[e] - Lm.v[e]);
-                const int j = r - 2;
-                T* ob = outp + (int64_t)(j + a.out.org[1]) * a.out.pitch[1] + a.out.org[0];
-                if (vout) {
-                    *(Row*)(ob + c0) = o;
-                } else {
-#pragma unroll
-                    for (int e = 0; e < V; ++e)
-                        if (c0 + e >= 0 && c0 + e < a.nx) ob[c0 + e] = o.v[e];
-                }
-            }
+            for (int e = 0; e < V; ++e)
+                Lr.v[e] = lap(e + 1 < V ? u0.v[e + 1] : right, e > 0 ? u0.v[e - 1] : left, up.v[e], um.v[e], u0.v[e]);
+            L[s] = Lr;
+            // L at the near column beyond the strip (used by lanes 0 and 31)
+            const T own = el ? u0.v[0] : u0.v[V - 1];
+            EL[s] = lap(el ? own : UF[s2], el ? UF[s2] : own, UN[s], UN[s1], UN[s2]);
         }
+        if (do_out) {   // out at row r-2 from L rows r-3, r-2, r-1
+            const Row& Lm = L[s1];
+            const Row& L0 = L[s2];
+            const Row& Lp = L[s];
+            T left = __shfl_up_sync(0xffffffffu, L0.v[V - 1], 1);
+            T right = __shfl_down_sync(0xffffffffu, L0.v[0], 1);
+            if (el) left = EL[s2];
+            if (er) right = EL[s2];
+            Row o;
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+                o.v[e] = c2_squash<T>((e + 1 < V ? L0.v[e + 1] : right) - (e > 0 ? L0.v[e - 1] : left),
+                                      Lp.v[e] - Lm.v[e]);
+            if (vout) {
+                *(Row*)(op + c0) = o;
+            } else {
+#pragma unroll
+                for (int e = 0; e < V; ++e)
+                    if (c0 + e >= 0 && c0 + e < a.nx) op[c0 + e] = o.v[e];
+            }
+            op += po;
+        }
+    };
+    using I0 = std::integral_constant<int, 0>;
+    using I1 = std::integral_constant<int, 1>;
+    using I2 = std::integral_constant<int, 2>;
+    // steps 0 .. 5 (n >= 4 always; the prefetch of row t+3 while t+3 < n)
+    step(I0{}, 3 < n, false, false);
+    step(I1{}, 4 < n, false, false);
+    step(I2{}, 5 < n, true, false);
+    step(I0{}, 6 < n, true, false);
+    if (4 < n) step(I1{}, 7 < n, true, true);
+    if (5 < n) step(I2{}, 8 < n, true, true);
+    int t0 = 6;
+    // steady state: whole groups of three steps that all prefetch
+    for (; t0 + 2 + 3 < n; t0 += 3) {
+        step(I0{}, true, true, true);
+        step(I1{}, true, true, true);
+        step(I2{}, true, true, true);
+    }
+    // the last (up to five) steps
+    for (; t0 < n; t0 += 3) {
+        step(I0{}, t0 + 3 < n, true, true);
+        if (t0 + 1 < n) step(I1{}, t0 + 4 < n, true, true);
+        if (t0 + 2 < n) step(I2{}, t0 + 5 < n, true, true);
     }
 }
 
