@@ -287,10 +287,11 @@ __device__ __forceinline__ float squash_rsqrt_f32(float g2) {
     return o;
 }
 
-template <typename T>
-struct alignas(16) VRow {
-    static constexpr int V = 16 / (int)sizeof(T);
-    T v[V];
+// VW consecutive cells of one lane, loaded and stored as one vector
+template <typename T, int VW>
+struct alignas(sizeof(T) * VW) VRow {
+    static constexpr int V = VW;
+    T v[VW];
 };
 
 template <typename T>
@@ -307,10 +308,9 @@ __device__ __forceinline__ T c2_squash(T gx, T gy) {
 // one warp's strip; INT: the strip and the two columns on each side lie
 // inside the rows and the 16-byte paths are open (no column wrap, no
 // per-element fallbacks: the common case, compiled without those branches)
-template <typename T, bool INT>
+template <typename T, int V, bool INT>
 __device__ __forceinline__ void c2w_strip(const C2Args& a, int lane, int s0, int j0) {
-    constexpr int V = VRow<T>::V;
-    using Row = VRow<T>;
+    using Row = VRow<T, V>;
     const int c0 = s0 + V * lane;   // first own column
     const bool el = lane == 0, er = lane == 31;
     // the two columns beyond the strip on this lane's side (first / last
@@ -446,9 +446,8 @@ __device__ __forceinline__ void c2w_strip(const C2Args& a, int lane, int s0, int
 #else
 #define C2W_LB __launch_bounds__(256)
 #endif
-template <typename T>
+template <typename T, int V>
 __global__ void C2W_LB chain2d_warp(const C2Args a) {
-    constexpr int V = VRow<T>::V;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, lane = tid & 31;
     const int64_t wid = ((int64_t)blockIdx.x * (blockDim.x * blockDim.y) + tid) >> 5;
     const int strip = (int)(wid % a.nstrips);
@@ -456,8 +455,8 @@ __global__ void C2W_LB chain2d_warp(const C2Args a) {
     if (j0 >= a.ny) return;   // whole warp
     const int s0 = strip * 32 * V - a.sh;
     const bool inside = a.u.wrap ? (s0 >= 2 && s0 + 32 * V + 2 <= a.nx) : (s0 >= 0 && s0 + 32 * V <= a.nx);
-    if (a.vec && a.vecout && inside) c2w_strip<T, true>(a, lane, s0, j0);
-    else c2w_strip<T, false>(a, lane, s0, j0);
+    if (a.vec && a.vecout && inside) c2w_strip<T, V, true>(a, lane, s0, j0);
+    else c2w_strip<T, V, false>(a, lane, s0, j0);
 }
 
 // tail of the "sweep" schedule: G and out from a materialised L (halo 1)
@@ -487,18 +486,21 @@ int chunk_planes(int64_t tiles, int nz, int64_t cap, int lead);
 int device_sms();
 }  // namespace
 
-template <typename T>
+// 2D warp-strip kernel: 16-byte lane vectors for the 32x4 and 64x4 tiles
+static inline bool c2w_wide(int TX, int TY) { return TY == 4; }
+
+template <typename T, int V>
 static int launch_c2warp(hfav_plan_t* p, C2Args& a, int TX, int TY, cudaStream_t st) {
-    constexpr int V = VRow<T>::V;
     const int NT = TX * TY;
+    constexpr size_t VB = sizeof(T) * V;   // bytes of one lane's vector
     a.sh = ((a.u.org[0] % V) + V) % V;
-    a.vec = ((uintptr_t)a.u.p % 16 == 0) && (a.u.pitch[1] % V == 0);
-    a.vecout = ((uintptr_t)a.out.p % 16 == 0) && (a.out.pitch[1] % V == 0) && (((a.out.org[0] % V) + V) % V == a.sh);
+    a.vec = ((uintptr_t)a.u.p % VB == 0) && (a.u.pitch[1] % V == 0);
+    a.vecout = ((uintptr_t)a.out.p % VB == 0) && (a.out.pitch[1] % V == 0) && (((a.out.org[0] % V) + V) % V == a.sh);
     a.nstrips = (a.nx + a.sh + 32 * V - 1) / (32 * V);
     static int occ = 0;   // resident CTAs per SM at NT threads (same on every device of the one target)
     static int occ_nt = 0;
     if (occ_nt != NT) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, chain2d_warp<T>, NT, 0) != cudaSuccess || occ <= 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, chain2d_warp<T, V>, NT, 0) != cudaSuccess || occ <= 0) {
             cudaGetLastError();
             occ = 1;
         }
@@ -508,7 +510,7 @@ static int launch_c2warp(hfav_plan_t* p, C2Args& a, int TX, int TY, cudaStream_t
     a.R = chunk_planes(a.nstrips, a.ny, (int64_t)occ * (NT / 32) * device_sms(), 4);
     const int64_t warps = (int64_t)a.nstrips * ((a.ny + a.R - 1) / a.R);
     const int64_t blocks = (warps + NT / 32 - 1) / (NT / 32);
-    chain2d_warp<T><<<(unsigned)blocks, dim3(TX, TY), 0, st>>>(a);
+    chain2d_warp<T, V><<<(unsigned)blocks, dim3(TX, TY), 0, st>>>(a);
     HFAV_LAUNCHED(p->rt, "chain2d_fused", st);
     return HFAV_OK;
 }
@@ -574,8 +576,13 @@ int launch_chain2d(hfav_plan_t* p, const Schedule& s, void* const* ax, void* con
     const int TX = s.tx, TY = s.ty;
     dim3 blk(TX, TY);
     dim3 grd((nx + TX - 1) / TX, (ny + a.R * TY - 1) / (a.R * TY));
-    if (s.placement == PLACE_REG)
-        return f64 ? launch_c2warp<double>(p, a, TX, TY, st) : launch_c2warp<float>(p, a, TX, TY, st);
+    if (s.placement == PLACE_REG) {
+        // cells per lane: 16-byte vectors for the 32x4 / 64x4 tiles, half that
+        // (fewer registers, more resident warps) for 128x2 / 32x8
+        const bool wide = c2w_wide(TX, TY);
+        if (f64) return wide ? launch_c2warp<double, 2>(p, a, TX, TY, st) : launch_c2warp<double, 1>(p, a, TX, TY, st);
+        return wide ? launch_c2warp<float, 4>(p, a, TX, TY, st) : launch_c2warp<float, 2>(p, a, TX, TY, st);
+    }
     if (s.placement == PLACE_SMEM) {
         size_t sm = (size_t)TY * (3 * (TX + 4) + 3 * (TX + 2)) * es;
         if (f64) chain2d_ring<double, false><<<grd, blk, sm, st>>>(a);
@@ -1128,7 +1135,9 @@ double chain_warps_t(const hfav_plan_t* p, const Schedule& s) {
     if (s.fusion == FUSE_UNFUSED) return warps_of(generic_rule_kernel<T>, 256, 0);
     if (p->pipeline == PIPE_CHAIN2D) {
         if (s.fusion == FUSE_SWEEP) return warps_of(chain2d_tail<T>, NT, 0);
-        if (s.placement == PLACE_REG) return warps_of(chain2d_warp<T>, NT, 0);
+        if (s.placement == PLACE_REG)
+            return c2w_wide(TX, TY) ? warps_of(chain2d_warp<T, 16 / sizeof(T)>, NT, 0)
+                                    : warps_of(chain2d_warp<T, 8 / sizeof(T)>, NT, 0);
         if (s.placement == PLACE_SMEM)
             return warps_of(chain2d_ring<T, false>, NT, (size_t)TY * (3 * (TX + 4) + 3 * (TX + 2)) * es);
         return warps_of(chain2d_ring<T, true>, NT, 0);
