@@ -265,17 +265,17 @@ __global__ void __launch_bounds__(256) chain2d_ring(const C2Args a) {
     }
 }
 
-// reg placement: warp strips.  Each warp owns a strip of 32 V consecutive
-// columns (V = 16 bytes / element size: 4 floats or 2 doubles; lane l holds
-// columns s0 + V l .. s0 + V l + V - 1) and streams a chunk of R rows.  The
+// reg placement: warp strips.  Each warp streams a chunk of R rows of a
+// strip of 32 V consecutive columns (lane l holds columns s0 + V l ..
+// s0 + V l + V - 1) and stores the strip's inner 32 V - 4 columns; strips
+// overlap by four columns, so no lane needs data from beyond its strip.  The
 // u and L windows (three rows each) are registers, the i-neighbours cross
-// lanes by shuffle, and the strip's first and last lanes also carry the two
-// columns beyond the strip (their u, and L one column out).  No shared
-// memory and no barriers.  Rows are loaded three rows ahead; the row loop is
-// unrolled by three so the windows rotate by renaming.  Loads and stores are
-// 16-byte vectors where a lane's columns lie inside the array's rows (the
-// strip origin s0 is shifted so that they are aligned), scalars with the
-// periodic wrap elsewhere.
+// lanes by shuffle; no shared memory and no barriers.  Rows are loaded three
+// rows ahead; the row loop is unrolled by three so the windows rotate by
+// renaming.  Loads and stores are vectors of V cells where a lane's columns
+// lie inside the array's rows (the strip origin is shifted so that they are
+// aligned), scalars with the periodic wrap elsewhere.
+
 // s / (1 + s) for s = sqrt(g2) / 2, FP32: the equal 1 / (1 + 2 / sqrt(g2))
 // with the hardware reciprocal square root and reciprocal (PTX rsqrt.approx
 // and rcp.approx, flush-to-zero: relative error a few 2^-23; g2 = 0 or
@@ -312,13 +312,11 @@ template <typename T, int V, bool INT>
 __device__ __forceinline__ void c2w_strip(const C2Args& a, int lane, int s0, int j0) {
     using Row = VRow<T, V>;
     const int c0 = s0 + V * lane;   // first own column
-    const bool el = lane == 0, er = lane == 31;
-    // the two columns beyond the strip on this lane's side (first / last
-    // lane): `near` next to the strip, `far` one further
-    const int cn = el ? s0 - 1 : s0 + 32 * V, cf = el ? s0 - 2 : s0 + 32 * V + 1;
     const bool wrap = a.u.wrap;
     const bool vin = INT || (a.vec && (wrap ? (c0 >= 0 && c0 + V <= a.nx) : (c0 >= -2 && c0 + V <= a.nx + 2)));
-    const bool vout = INT || (a.vecout && c0 >= 0 && c0 + V <= a.nx);
+    // outputs: columns s0+2 .. s0+32V-3 of the strip that lie in 0 .. nx-1
+    const int olo = max(s0 + 2, 0), ohi = min(s0 + 32 * V - 3, a.nx - 1);
+    const bool vout = a.vecout && c0 >= olo && c0 + V - 1 <= ohi;
     auto col = [&](const T* ub, int c) -> T {
         if (INT) return ub[c];
         if (wrap) return ub[wrap1(c, a.nx)];
@@ -330,19 +328,12 @@ __device__ __forceinline__ void c2w_strip(const C2Args& a, int lane, int s0, int
     const T* row0 = (const T*)a.u.p + (int64_t)a.u.org[1] * pu + a.u.org[0];
     int rl = j0 - 2;   // next row to load
     const T* lp = row0 + (int64_t)(wrap ? wrap1(rl, a.ny) : rl) * pu;
-    auto load_next = [&](Row& x, T& en, T& ef) {
+    auto load_next = [&](Row& x) {
         if (vin) {
             x = *(const Row*)(lp + c0);
         } else {
 #pragma unroll
             for (int e = 0; e < V; ++e) x.v[e] = col(lp, c0 + e);
-        }
-        if (INT) {   // every lane reads them (in bounds); only lanes 0 and 31 use them
-            en = lp[cn];
-            ef = lp[cf];
-        } else if (el || er) {
-            en = col(lp, cn);
-            ef = col(lp, cf);
         }
         ++rl;
         lp += pu;
@@ -361,46 +352,35 @@ __device__ __forceinline__ void c2w_strip(const C2Args& a, int lane, int s0, int
     const int rend = min(j0 + a.R, a.ny) + 1;
     const int n = rend - (j0 - 2) + 1;
     Row Q[3], U[3], L[3];
-    T QN[3], QF[3], UN[3], UF[3], EL[3];
 #pragma unroll
-    for (int s = 0; s < 3; ++s) {
-        QN[s] = QF[s] = UN[s] = UF[s] = EL[s] = (T)0;
-        load_next(Q[s], QN[s], QF[s]);   // n >= 4: rows j0-2 .. j0 exist
-    }
+    for (int s = 0; s < 3; ++s) load_next(Q[s]);   // n >= 5: rows j0-2 .. j0 exist
     T* op = (T*)a.out.p + (int64_t)(j0 + a.out.org[1]) * po + a.out.org[0];
-    // one step; S = t % 3 (window slot of row t), the flags say which parts run
+    // one step; S = t % 3 (window slot of row t), the flags say which parts run.
+    // Lane 0's left and lane 31's right neighbours are its own values (the
+    // shuffle's identity): they only reach the columns the strip does not store.
     auto step = [&](auto S, bool pf, bool do_l, bool do_out) {
         constexpr int s = decltype(S)::value, s1 = (s + 1) % 3, s2 = (s + 2) % 3;
         // slots: s holds row r (u) / r-1 (L); s2 row r-1 / r-2; s1 row r-2 / r-3
         U[s] = Q[s];
-        UN[s] = QN[s];
-        UF[s] = QF[s];
-        if (pf) load_next(Q[s], QN[s], QF[s]);
+        if (pf) load_next(Q[s]);
         if (do_l) {   // L at row r-1 from u rows r-2, r-1, r
             const Row& um = U[s1];
             const Row& u0 = U[s2];
             const Row& up = U[s];
-            T left = __shfl_up_sync(0xffffffffu, u0.v[V - 1], 1);
-            T right = __shfl_down_sync(0xffffffffu, u0.v[0], 1);
-            if (el) left = UN[s2];
-            if (er) right = UN[s2];
+            const T left = __shfl_up_sync(0xffffffffu, u0.v[V - 1], 1);
+            const T right = __shfl_down_sync(0xffffffffu, u0.v[0], 1);
             Row Lr;
 #pragma unroll
             for (int e = 0; e < V; ++e)
                 Lr.v[e] = lap(e + 1 < V ? u0.v[e + 1] : right, e > 0 ? u0.v[e - 1] : left, up.v[e], um.v[e], u0.v[e]);
             L[s] = Lr;
-            // L at the near column beyond the strip (used by lanes 0 and 31)
-            const T own = el ? u0.v[0] : u0.v[V - 1];
-            EL[s] = lap(el ? own : UF[s2], el ? UF[s2] : own, UN[s], UN[s1], UN[s2]);
         }
         if (do_out) {   // out at row r-2 from L rows r-3, r-2, r-1
             const Row& Lm = L[s1];
             const Row& L0 = L[s2];
             const Row& Lp = L[s];
-            T left = __shfl_up_sync(0xffffffffu, L0.v[V - 1], 1);
-            T right = __shfl_down_sync(0xffffffffu, L0.v[0], 1);
-            if (el) left = EL[s2];
-            if (er) right = EL[s2];
+            const T left = __shfl_up_sync(0xffffffffu, L0.v[V - 1], 1);
+            const T right = __shfl_down_sync(0xffffffffu, L0.v[0], 1);
             Row o;
 #pragma unroll
             for (int e = 0; e < V; ++e)
@@ -411,7 +391,7 @@ __device__ __forceinline__ void c2w_strip(const C2Args& a, int lane, int s0, int
             } else {
 #pragma unroll
                 for (int e = 0; e < V; ++e)
-                    if (c0 + e >= 0 && c0 + e < a.nx) op[c0 + e] = o.v[e];
+                    if (c0 + e >= olo && c0 + e <= ohi) op[c0 + e] = o.v[e];
             }
             op += po;
         }
@@ -419,12 +399,12 @@ __device__ __forceinline__ void c2w_strip(const C2Args& a, int lane, int s0, int
     using I0 = std::integral_constant<int, 0>;
     using I1 = std::integral_constant<int, 1>;
     using I2 = std::integral_constant<int, 2>;
-    // steps 0 .. 5 (n >= 4 always; the prefetch of row t+3 while t+3 < n)
+    // steps 0 .. 5 (n >= 5 always; the prefetch of row t+3 while t+3 < n)
     step(I0{}, 3 < n, false, false);
     step(I1{}, 4 < n, false, false);
     step(I2{}, 5 < n, true, false);
     step(I0{}, 6 < n, true, false);
-    if (4 < n) step(I1{}, 7 < n, true, true);
+    step(I1{}, 7 < n, true, true);
     if (5 < n) step(I2{}, 8 < n, true, true);
     int t0 = 6;
     // steady state: whole groups of three steps that all prefetch
@@ -453,8 +433,10 @@ __global__ void C2W_LB chain2d_warp(const C2Args a) {
     const int strip = (int)(wid % a.nstrips);
     const int j0 = (int)(wid / a.nstrips) * a.R;
     if (j0 >= a.ny) return;   // whole warp
-    const int s0 = strip * 32 * V - a.sh;
-    const bool inside = a.u.wrap ? (s0 >= 2 && s0 + 32 * V + 2 <= a.nx) : (s0 >= 0 && s0 + 32 * V <= a.nx);
+    // strips overlap by 4 columns: strip k loads 32V columns from s0 and
+    // stores the inner 32V - 4
+    const int s0 = strip * (32 * V - 4) - 2 - a.sh;
+    const bool inside = a.u.wrap ? (s0 >= 0 && s0 + 32 * V <= a.nx) : (s0 >= -2 && s0 + 32 * V <= a.nx + 2);
     if (a.vec && a.vecout && inside) c2w_strip<T, V, true>(a, lane, s0, j0);
     else c2w_strip<T, V, false>(a, lane, s0, j0);
 }
@@ -493,10 +475,10 @@ template <typename T, int V>
 static int launch_c2warp(hfav_plan_t* p, C2Args& a, int TX, int TY, cudaStream_t st) {
     const int NT = TX * TY;
     constexpr size_t VB = sizeof(T) * V;   // bytes of one lane's vector
-    a.sh = ((a.u.org[0] % V) + V) % V;
+    a.sh = (((a.u.org[0] - 2) % V) + V) % V;   // (s0 + org) a multiple of V
     a.vec = ((uintptr_t)a.u.p % VB == 0) && (a.u.pitch[1] % V == 0);
-    a.vecout = ((uintptr_t)a.out.p % VB == 0) && (a.out.pitch[1] % V == 0) && (((a.out.org[0] % V) + V) % V == a.sh);
-    a.nstrips = (a.nx + a.sh + 32 * V - 1) / (32 * V);
+    a.vecout = ((uintptr_t)a.out.p % VB == 0) && (a.out.pitch[1] % V == 0) && ((a.out.org[0] - a.u.org[0]) % V == 0);
+    a.nstrips = (a.nx + a.sh + (32 * V - 4) - 1) / (32 * V - 4);
     static int occ = 0;   // resident CTAs per SM at NT threads (same on every device of the one target)
     static int occ_nt = 0;
     if (occ_nt != NT) {
