@@ -52,7 +52,8 @@ CHAIN3D_FLOPS = 26.0     # s1 7, s2 7, s3 10, out 2
 # the hash of the kernel sources at capture time: a changed source voids it.
 TRAFFIC = {
     ("godunov2d_fp64_1024x1024_10steps", "gsweep_y"): (33.746e6, "7d1a7d4d45e53de8"),
-    ("chain3d_fp32_512x512x512", "chain3d_fused"): (1083.5e6, "b61e8d663f3380c5"),
+    ("chain3d_fp32_512x512x512", "chain3d_fused"): (1083.0e6, "c5057c810eeda563"),
+    ("chain2d_fp32_16384x16384", "chain2d_fused"): (2128.2e6, "c5057c810eeda563"),
 }
 
 
@@ -266,7 +267,7 @@ class Chain(Workload):
         return None, None, None
 
 
-WORKLOADS = ["godunov1024_f64", "godunov4096_f32", "batch64_f32", "chain2d256_f64", "chain3d512_f32"]
+WORKLOADS = ["godunov1024_f64", "godunov4096_f32", "batch64_f32", "chain2d256_f64", "chain2d16384_f32", "chain3d512_f32"]
 
 
 def make(name, H, I, torch, dev):

@@ -31,10 +31,11 @@ HIDDEN = 64
 # device-side choice ignores them too): the placement one-hots (8, 9) and
 # the main kernel's occupancy (14).  Leave-one-family-out validation on the
 # measured corpus (train on the Godunov family, choose for the 2D chain, and
-# the reverse; cross_family below) ranks this input set first: geometric-mean
-# pick / best x1.29 (2D chain) / x1.26 (Godunov) without them against x1.40 /
-# x1.41 with them -- those columns describe how one family's kernels were
-# written, not a cost that carries over to another family.
+# the reverse; cross_family below) ranks this input set first: pick / best
+# x1.76 (2D chain) and x1.16 (Godunov) without them against x1.56 and x1.34
+# with them, geometric means; over both families x1.43 against x1.45.  Those
+# columns describe how one family's kernels were written, not a cost that
+# carries over to another family.
 DROP = (8, 9, 14)
 FIELDS = ["family", "dtype", "nx", "ny", "nz", "n_grids", "steps", "schedule", "ms"]
 
