@@ -300,8 +300,10 @@ __device__ __forceinline__ T c2_squash(T gx, T gy) {
     if constexpr (sizeof(T) == 4) {
         return squash_rsqrt_f32(g2);
     } else {
-        const T G = sqrt(g2) * (T)0.5;
-        return G / ((T)1 + G);
+        // the same form in FP64: rsqrt (correctly rounded to an ulp) and the
+        // refined reciprocal; g2 = 0 gives exactly 0 (tested through the bits)
+        const double s = rsqrt(g2);
+        return __double_as_longlong(g2) > 0 ? rcp_nr(fma(2.0, s, 1.0)) : 0.0;
     }
 }
 

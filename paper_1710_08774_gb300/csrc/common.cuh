@@ -72,6 +72,28 @@ __device__ __forceinline__ T* garr_ptr(const GArr& a, int i, int j, int k) {
     return p + (int64_t)(k + a.org[2]) * a.pitch[2] + (int64_t)(j + a.org[1]) * a.pitch[1] + (i + a.org[0]);
 }
 
+// FP64 reciprocal from the hardware estimate (rcp.approx.ftz.f64) refined
+// by Newton-Raphson (a published method)
+__device__ __forceinline__ double rcp_est(double b) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(b));
+    return r;
+}
+// reciprocal to within an ulp or two (two Newton-Raphson steps)
+__device__ __forceinline__ double rcp_nr(double b) {
+    double r = rcp_est(b);
+    r = fma(r, fma(-b, r, 1.0), r);
+    return fma(r, fma(-b, r, 1.0), r);
+}
+__device__ __forceinline__ float rcp_nr(float b) { return 1.0f / b; }
+// quotient a / b: a * (1/b) with one residual correction
+__device__ __forceinline__ double div_nr(double a, double b) {
+    const double r = rcp_nr(b);
+    const double q = a * r;
+    return fma(r, fma(-b, q, a), q);
+}
+__device__ __forceinline__ float div_nr(float a, float b) { return a / b; }
+
 // atomic max of non-negative doubles through their bit patterns (IEEE order
 // of non-negative doubles equals the order of their bits as unsigned ints)
 __device__ __forceinline__ void atomic_max_pos(unsigned long long* slot, double v) {

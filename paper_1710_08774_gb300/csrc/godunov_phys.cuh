@@ -51,25 +51,6 @@ __device__ __forceinline__ bool dneg(double x) { return __double_as_longlong(x) 
 __device__ __forceinline__ bool dpos(float x) { return x > 0.f; }
 __device__ __forceinline__ bool dneg(float x) { return x < 0.f; }
 
-__device__ __forceinline__ double rcp_est(double b) {
-    double r;
-    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(b));
-    return r;
-}
-// reciprocal to within an ulp or two (two Newton-Raphson steps)
-__device__ __forceinline__ double rcp_nr(double b) {
-    double r = rcp_est(b);
-    r = fma(r, fma(-b, r, 1.0), r);
-    return fma(r, fma(-b, r, 1.0), r);
-}
-__device__ __forceinline__ float rcp_nr(float b) { return 1.0f / b; }
-// quotient a / b: a * (1/b) with one residual correction
-__device__ __forceinline__ double div_nr(double a, double b) {
-    const double r = rcp_nr(b);
-    const double q = a * r;
-    return fma(r, fma(-b, q, a), q);
-}
-__device__ __forceinline__ float div_nr(float a, float b) { return a / b; }
 
 // Primitive state of a cell in the frame of a sweep: rho, u_normal,
 // u_transverse, p, sound speed c, 1/c and c/rho.
