@@ -51,9 +51,9 @@ CHAIN3D_FLOPS = 26.0     # s1 7, s2 7, s3 10, out 2
 # ncu capture of the bench's profiling case (summaries under profiles/), with
 # the hash of the kernel sources at capture time: a changed source voids it.
 TRAFFIC = {
-    ("godunov2d_fp64_1024x1024_10steps", "gsweep_y"): (33.746e6, "7d1a7d4d45e53de8"),
-    ("chain3d_fp32_512x512x512", "chain3d_fused"): (1083.0e6, "c5057c810eeda563"),
-    ("chain2d_fp32_16384x16384", "chain2d_fused"): (2128.2e6, "c5057c810eeda563"),
+    ("godunov2d_fp64_1024x1024_10steps", "gsweep_y"): (33.683e6, "ae80a26943d6af8c"),
+    ("chain3d_fp32_512x512x512", "chain3d_fused"): (1084.0e6, "10d5e04765f5c5a8"),
+    ("chain2d_fp32_16384x16384", "chain2d_fused"): (2128.5e6, "10d5e04765f5c5a8"),
 }
 
 
