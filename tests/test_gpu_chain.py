@@ -109,3 +109,67 @@ def test_chain3d_halo_given_quintic_exact(schedule):
     P.run([u], [op])
     torch.cuda.synchronize()
     assert np.all(op[3:-3, 3:-3, 3:-3].cpu().numpy() == 120.0 / 121.0)
+
+
+def _block_wrap(interior, centre, r):
+    """The (2r+1)^d block of a periodic interior array around `centre`."""
+    idx = [np.arange(c - r, c + r + 1) % n for c, n in zip(centre, interior.shape)]
+    return interior[np.ix_(*idx)]
+
+
+def _sample_points(n, dims, count, seed):
+    """Random cells plus the domain's corners and cells on tile / chunk borders."""
+    rng = np.random.default_rng(seed)
+    pts = rng.integers(0, n, size=(count, dims))
+    fixed = [[0] * dims, [n - 1] * dims, [n // 2] * dims]
+    for b in (31, 32, 55, 56, 63, 64, 127, 128, 255, 256):
+        if b < n:
+            fixed.append([b] * dims)
+            fixed.append([(b + 7 * d) % n for d in range(dims)])
+    return np.vstack([pts, np.array(fixed)])
+
+
+@pytest.mark.parametrize("schedule", ["full:reg:32x4", "full:reg:32x8"])
+def test_chain3d_512_f32_full_size_sampled(schedule):
+    """The 512^3 FP32 3D chain at full size, in the fused schedules the bench's
+    autotuner picks: sampled cells (tile and chunk borders among them) against
+    the oracle run on each cell's periodic 7^3 neighbourhood, which fixes the
+    cell's value exactly; the FP32 bar of 2e-5 of max |out|."""
+    import torch
+    n = 512
+    u = I.chain3d_input(n, seed=4, dtype=np.float32)
+    ut = to_dev(u)
+    op = torch.full_like(ut, float("nan"))
+    P = H.Plan(H.chain3d_dag(), [H.Grid.of(ut, 3)], H.HFAV_F32, H.HFAV_BC_PERIODIC, schedule)
+    P.run([ut], [op])
+    torch.cuda.synchronize()
+    pts = _sample_points(n, 3, 300, seed=11)
+    kk, jj, ii = (torch.from_numpy(pts[:, x] + 3).cuda() for x in range(3))
+    got = op[kk, jj, ii].double().cpu().numpy()
+    interior = u[3:-3, 3:-3, 3:-3]
+    ref = np.array([oracle.chain3d(np.pad(_block_wrap(interior, p, 3).astype(np.float64), 3))[3, 3, 3]
+                    for p in pts])
+    assert np.all(np.isfinite(got))
+    assert normwise(got, ref) <= 2e-5
+
+
+@pytest.mark.parametrize("schedule", ["full:reg:32x4", "full:reg:128x2"])
+def test_chain2d_16384_f32_full_size_sampled(schedule):
+    """The 16384^2 FP32 2D chain (the large-grid point of the bench) at full
+    size: sampled cells (strip and chunk borders among them) against the oracle
+    run on each cell's periodic 5 x 5 neighbourhood; 2e-5 of max |out|."""
+    import torch
+    n = 16384
+    u = I.chain2d_input(n, seed=0).astype(np.float32)
+    ut = to_dev(u)
+    op = torch.full_like(ut, float("nan"))
+    P = H.Plan(H.chain2d_dag(), [H.Grid.of(ut, 2)], H.HFAV_F32, H.HFAV_BC_PERIODIC, schedule)
+    P.run([ut], [op])
+    torch.cuda.synchronize()
+    pts = _sample_points(n, 2, 500, seed=12)
+    jj, ii = (torch.from_numpy(pts[:, x] + 2).cuda() for x in range(2))
+    got = op[jj, ii].double().cpu().numpy()
+    interior = u[2:-2, 2:-2]
+    ref = np.array([oracle.chain2d(np.pad(_block_wrap(interior, p, 2).astype(np.float64), 2))[2][2, 2] for p in pts])
+    assert np.all(np.isfinite(got))
+    assert normwise(got, ref) <= 2e-5

@@ -99,3 +99,21 @@ def test_chain3d_bruteforce_roll():
     s3 = np.sqrt(g2) / 2
     out = oracle.chain3d(u, periodic=True)
     assert np.allclose(out, s3 / (1 + s3), rtol=1e-13, atol=1e-14)
+
+
+def test_neighbourhood_block_gives_the_whole_domain_value():
+    """The full-size GPU tests check sampled cells against the oracle run on
+    each cell's periodic neighbourhood (radius 3 in 3D, 2 in 2D).  That block
+    fixes the cell: on small grids it reproduces the whole-domain oracle."""
+    from tests.test_gpu_chain import _block_wrap, _sample_points
+    u = I.chain3d_input(20, seed=4)
+    full = oracle.chain3d(u)
+    interior = u[3:-3, 3:-3, 3:-3]
+    for p in _sample_points(20, 3, 20, 1):
+        b = oracle.chain3d(np.pad(_block_wrap(interior, p, 3), 3))[3, 3, 3]
+        assert abs(b - full[tuple(p)]) <= 1e-14 * max(1.0, abs(full[tuple(p)]))
+    u2 = I.chain2d_input(24, seed=0)
+    _, _, f2 = oracle.chain2d(u2)
+    interior2 = u2[2:-2, 2:-2]
+    for p in _sample_points(24, 2, 30, 2):
+        assert oracle.chain2d(np.pad(_block_wrap(interior2, p, 2), 2))[2][2, 2] == f2[tuple(p)]
