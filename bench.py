@@ -322,6 +322,22 @@ def oracle_sample(workload, n=None):
     return n ** 3 / dt / 1e9, dt, 0.0, f"{n}^3 u~N(0,1), single thread"
 
 
+def workload_name(key):
+    """The workload's descriptive name (config.workload) from its command-line
+    key, without building it (the reference arm runs on the host only)."""
+    import re
+    names = {"godunov1024_f64": "godunov2d_fp64_1024x1024_10steps",
+             "godunov4096_f32": "godunov2d_fp32bulk_4096x4096_10steps",
+             "batch64_f32": "godunov2d_batch64_fp32bulk_100steps_graph"}
+    if key in names:
+        return names[key]
+    m = re.fullmatch(r"chain([23])d(\d+)_(f32|f64)", key)
+    if m:
+        dims, n = int(m.group(1)), m.group(2)
+        return f"chain{dims}d_{'fp64' if m.group(3) == 'f64' else 'fp32'}_{'x'.join([n] * dims)}"
+    raise SystemExit(f"unknown workload {key}")
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -337,7 +353,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(secs) / len(secs),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": name, "sample": sample},
+            "config": {"workload": workload_name(name), "sample": sample},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
