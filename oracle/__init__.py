@@ -45,6 +45,8 @@ def lib():
         dp = ctypes.POINTER(ctypes.c_double)
         L.oracle_chain2d.argtypes = [dp, ctypes.c_long, ctypes.c_long, ctypes.c_long, ctypes.c_int, dp, dp, dp]
         L.oracle_chain3d.argtypes = [dp, ctypes.c_long, ctypes.c_long, ctypes.c_long, ctypes.c_int, dp]
+        L.oracle_cosmo.argtypes = [dp, ctypes.c_long, ctypes.c_long, ctypes.c_long, ctypes.c_long, ctypes.c_long,
+                                   ctypes.c_int, ctypes.c_double, dp, dp, dp, dp]
         L.oracle_riemann.argtypes = [dp, dp, ctypes.c_double, dp, ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_long)]
         L.oracle_godunov.argtypes = [dp, ctypes.c_long, ctypes.c_long, ctypes.c_int, ctypes.c_double,
@@ -83,6 +85,24 @@ def chain3d(u_padded, periodic=True):
     if rc != 0:
         raise RuntimeError(f"oracle_chain3d failed: {rc}")
     return out
+
+
+def cosmo(u_padded, c, periodic=True):
+    """COSMO horizontal diffusion (Sec. 5.3) over an (nz+4, ny+4, nx+4) FP64
+    array, interior at (2, 2, 2); every k plane on its own.
+
+    Returns (lap, flx, fly, out): lap on the halo-1 ring (nz, ny+2, nx+2),
+    flx on faces i = -1 .. nx-1 (nz, ny, nx+1), fly on faces j = -1 .. ny-1
+    (nz, ny+1, nx), out on the interior (nz, ny, nx)."""
+    u = np.ascontiguousarray(u_padded, dtype=np.float64)
+    nz, ny, nx = (s - 4 for s in u.shape)
+    lap = np.empty((nz, ny + 2, nx + 2)); flx = np.empty((nz, ny, nx + 1)); fly = np.empty((nz, ny + 1, nx))
+    out = np.empty((nz, ny, nx))
+    rc = lib().oracle_cosmo(_p(u), nx, ny, nz, u.shape[2], u.shape[1] * u.shape[2], int(bool(periodic)), float(c),
+                            _p(lap), _p(flx), _p(fly), _p(out))
+    if rc != 0:
+        raise RuntimeError(f"oracle_cosmo failed: {rc}")
+    return lap, flx, fly, out
 
 
 def riemann(qL, qR, gamma=1.4):

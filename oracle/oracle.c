@@ -26,6 +26,8 @@
  *     kernels only; the physics written here is the textbook MUSCL-Hancock /
  *     two-shock Godunov scheme, in the reading stated beside each function.
  *   - 3D four-stage 7-point chain (Laplacian, Laplacian, |grad|/2, x/(1+x)).
+ *   - the COSMO horizontal-diffusion micro-kernels (Sec. 5.3: ulapstage,
+ *     flux_x, flux_y, ustage) over 3D data with no dependency in k.
  *
  * Parity status: every function here is pinned by tests/test_oracle_*.py
  * against closed forms, invariants, an exact Riemann solution or brute force.
@@ -511,3 +513,85 @@ double oracle_godunov_cfl_dt(const double* U, long nx, long ny, double cfl, doub
 /* timing helper for the CPU baseline                                         */
 /* ------------------------------------------------------------------------- */
 int oracle_version(void) { return 1; }
+
+/* ------------------------------------------------------------------------- */
+/* COSMO horizontal diffusion (Sec. 5.3)                                      */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * oracle_cosmo
+ *   The paper lists the four kernels and the operands each reads (a cell's u
+ *   and its i / j neighbours for ulapstage; u and ulapstage at two
+ *   neighbouring cells in i (j) for flux_x (flux_y); u and the four
+ *   neighbouring fluxes for ustage) but not their formulas.  Written here:
+ *   the fourth-order horizontal diffusion with a flux limiter of the stencil
+ *   benchmark the paper takes the example from:
+ *     lap(i,j) = u(i+1,j) + u(i-1,j) + u(i,j+1) + u(i,j-1) - 4 u(i,j)
+ *     flx(i,j) = lap(i+1,j) - lap(i,j), or 0 where flx (u(i+1,j) - u(i,j)) > 0
+ *     fly(i,j) = lap(i,j+1) - lap(i,j), or 0 where fly (u(i,j+1) - u(i,j)) > 0
+ *     out(i,j) = u(i,j) - c ((flx(i,j) - flx(i-1,j)) + (fly(i,j) - fly(i,j-1)))
+ *   (the flux at index i is the face i+1/2), every k plane on its own.
+ *   u    : (nz+4) x (ny+4) x (nx+4) array, row pitch pu >= nx+4, plane pitch
+ *          pp >= pu (ny+4), interior at (2,2,2); the k halo is never read.
+ *   periodic != 0 : i and j wrap onto the interior; otherwise the caller's
+ *          halo of width 2 in i and j is used as given.
+ *   lap  : nz x (ny+2) x (nx+2) (halo 1) or NULL;  flx : nz x ny x (nx+1)
+ *          (i = -1 .. nx-1) or NULL;  fly : nz x (ny+1) x nx (j = -1 .. ny-1)
+ *          or NULL;  out : nz x ny x nx.
+ */
+int oracle_cosmo(const double* u, long nx, long ny, long nz, long pu, long pp, int periodic, double c,
+                 double* lap, double* flx, double* fly, double* out) {
+    if (nx < 1 || ny < 1 || nz < 1 || pu < nx + 4 || pp < pu * (ny + 4)) return ORACLE_EINVAL;
+    const long px = nx + 4, py = ny + 4;
+    double* w = (double*)malloc(sizeof(double) * px * py);
+    double* Lw = (double*)malloc(sizeof(double) * (nx + 2) * (ny + 2));
+    double* Fx = (double*)malloc(sizeof(double) * (nx + 1) * ny);
+    double* Fy = (double*)malloc(sizeof(double) * nx * (ny + 1));
+    if (!w || !Lw || !Fx || !Fy) { free(w); free(Lw); free(Fx); free(Fy); return ORACLE_ENOMEM; }
+#define W_(i, j) w[((j) + 2) * px + ((i) + 2)]
+#define L_(i, j) Lw[((j) + 1) * (nx + 2) + ((i) + 1)]
+#define FX_(i, j) Fx[(j) * (nx + 1) + ((i) + 1)]
+#define FY_(i, j) Fy[((j) + 1) * nx + (i)]
+    for (long k = 0; k < nz; ++k) {
+        const double* uk = u + (k + 2) * pp;
+        /* make_boundary: copy (and wrap) the plane into a private padded array */
+        for (long j = -2; j < ny + 2; ++j)
+            for (long i = -2; i < nx + 2; ++i) {
+                long si = periodic ? wrap(i, nx) : i;
+                long sj = periodic ? wrap(j, ny) : j;
+                W_(i, j) = uk[(sj + 2) * pu + (si + 2)];
+            }
+        /* ulapstage over the halo-1 ring */
+        for (long j = -1; j < ny + 1; ++j)
+            for (long i = -1; i < nx + 1; ++i)
+                L_(i, j) = W_(i + 1, j) + W_(i - 1, j) + W_(i, j + 1) + W_(i, j - 1) - 4.0 * W_(i, j);
+        /* flux_x on faces i = -1 .. nx-1 of the interior rows */
+        for (long j = 0; j < ny; ++j)
+            for (long i = -1; i < nx; ++i) {
+                double f = L_(i + 1, j) - L_(i, j);
+                if (f * (W_(i + 1, j) - W_(i, j)) > 0.0) f = 0.0;
+                FX_(i, j) = f;
+            }
+        /* flux_y on faces j = -1 .. ny-1 of the interior columns */
+        for (long j = -1; j < ny; ++j)
+            for (long i = 0; i < nx; ++i) {
+                double f = L_(i, j + 1) - L_(i, j);
+                if (f * (W_(i, j + 1) - W_(i, j)) > 0.0) f = 0.0;
+                FY_(i, j) = f;
+            }
+        /* ustage */
+        for (long j = 0; j < ny; ++j)
+            for (long i = 0; i < nx; ++i)
+                out[(k * ny + j) * nx + i] =
+                    W_(i, j) - c * ((FX_(i, j) - FX_(i - 1, j)) + (FY_(i, j) - FY_(i, j - 1)));
+        if (lap) memcpy(lap + k * (nx + 2) * (ny + 2), Lw, sizeof(double) * (nx + 2) * (ny + 2));
+        if (flx) memcpy(flx + k * (nx + 1) * ny, Fx, sizeof(double) * (nx + 1) * ny);
+        if (fly) memcpy(fly + k * nx * (ny + 1), Fy, sizeof(double) * nx * (ny + 1));
+    }
+#undef W_
+#undef L_
+#undef FX_
+#undef FY_
+    free(w); free(Lw); free(Fx); free(Fy);
+    return ORACLE_OK;
+}

@@ -67,6 +67,15 @@ def chain3d_input(n=64, seed=4, halo=3, dtype=np.float64, fill_halo=np.nan):
     return u
 
 
+def cosmo_input(nx, ny, nz, seed=7, halo=2, dtype=np.float64, fill_halo=np.nan):
+    """u ~ U[0,1) on an nx x ny x nz interior inside an (nz+2h, ny+2h, nx+2h)
+    array (interior at h); the COSMO diffusion reads no k neighbours, the k
+    halo only keeps one halo width for every axis."""
+    u = np.full((nz + 2 * halo, ny + 2 * halo, nx + 2 * halo), fill_halo, dtype=dtype)
+    u[halo:halo + nz, halo:halo + ny, halo:halo + nx] = uniform(seed, 0, nx * ny * nz).reshape(nz, ny, nx)
+    return u
+
+
 def sod_state(nx, ny, seed=1, grid=0, perturb=0.01, gamma=GAMMA):
     """Sod-like conserved state (4, ny, nx) FP64 on [0,1] x [0, ny/nx], dx = 1/nx.
 
