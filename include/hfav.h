@@ -81,6 +81,15 @@ typedef enum {
     HFAV_OP_SQUASH = 3,
     /* generic pointwise ops used by planner-only examples (not run on the GPU)       */
     HFAV_OP_GENERIC = 4,
+    /* COSMO horizontal diffusion (Sec. 5.3 names its kernels flux_x / flux_y and
+     * ustage; the first, ulapstage, is a STENCIL_LINEAR 5-point star):
+     * LIMFLUX, directional along rule.axis, in: u(0) u(+1) lap(0) lap(+1)
+     *   f = lap(+1) - lap(0); out = 0 where f (u(+1) - u(0)) > 0, else f
+     *   (the flux of the face +1/2, stored at index 0)
+     * DIFFUSE, in: u flx(-1,0) flx(0) fly(0,-1) fly(0), params[0] = c
+     *   out = u - c ((flx(0) - flx(-1)) + (fly(0) - fly(-1)))                          */
+    HFAV_OP_LIMFLUX = 5,
+    HFAV_OP_DIFFUSE = 6,
     /* Hydro2D kernels (Sec. 5.4), directional, ideal gas, params[0] = gamma:
      * CONSTOPRIM in: U0 U1 U2 U3 (rho, rho u, rho v, E) -> rho un ut e
      * EOS        in: rho e                              -> p c

@@ -54,8 +54,16 @@ __global__ void __launch_bounds__(256) generic_rule_kernel(const GenericArgs a) 
         int j = (int)(rest % a.n[1]);
         int k = (int)(rest / a.n[1]);
         i += a.lo[0]; j += a.lo[1]; k += a.lo[2];
+        auto ld = [&](int r) {
+            return garr_ld<T>(a.arr[a.ref_arr[r]], i + a.ref_off[r][0], j + a.ref_off[r][1], k + a.ref_off[r][2]);
+        };
         T v;
-        if (a.op == HFAV_OP_STENCIL_LINEAR) {
+        if (a.op == HFAV_OP_LIMFLUX) {   // in: u(0) u(+1) lap(0) lap(+1)
+            const T f = ld(3) - ld(2);
+            v = f * (ld(1) - ld(0)) > (T)0 ? (T)0 : f;
+        } else if (a.op == HFAV_OP_DIFFUSE) {   // in: u flx(-1) flx(0) fly(-1) fly(0)
+            v = ld(0) - wsel<T>(a.w[0], a.wf[0]) * ((ld(2) - ld(1)) + (ld(4) - ld(3)));
+        } else if (a.op == HFAV_OP_STENCIL_LINEAR) {
             v = (T)0;
             for (int r = 0; r < a.nref; ++r) {
                 T x = garr_ld<T>(a.arr[a.ref_arr[r]], i + a.ref_off[r][0], j + a.ref_off[r][1], k + a.ref_off[r][2]);
@@ -180,6 +188,9 @@ struct C2Args {
     float fc, fip, fim, fjp, fjm;    // the same, rounded to FP32
     void* slab;                      // hbm placement: per-CTA rings
     int nstrips, sh, vec, vecout;    // reg placement: warp strips, strip origin shift, 16-byte paths
+    int nz;                          // COSMO: planes (each on its own)
+    double coef;                     // COSMO: c of ustage
+    float coeff;                     // the same, rounded to FP32
 };
 
 // L at one point from its five star neighbours, summed in the rule's order
@@ -497,6 +508,204 @@ static int launch_c2warp(hfav_plan_t* p, C2Args& a, int TX, int TY, cudaStream_t
     chain2d_warp<T, V><<<(unsigned)blocks, dim3(TX, TY), 0, st>>>(a);
     HFAV_LAUNCHED(p->rt, "chain2d_fused", st);
     return HFAV_OK;
+}
+
+// ---------------------------------------------------------------------------
+// COSMO horizontal diffusion (Sec. 5.3), fused: ulapstage, flux_x, flux_y and
+// ustage in one pass with every intermediate in registers.  The same warp
+// strips as the 2D chain (a strip of 32 V columns per warp, stores the inner
+// 32 V - 4, rows streamed three ahead, i-neighbours by shuffle); each warp
+// works in one k plane.  Per arriving u row r: lap at row r-1 (u rows r-2 ..
+// r), then flux_y and flux_x at row r-2 (lap rows r-2, r-1), then ustage at
+// row r-2 (flux_y rows r-3, r-2); windows of three rows of u, two of lap and
+// two of flux_y.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ T limflux(T u0, T u1, T l0, T l1) {
+    const T f = l1 - l0;
+    return f * (u1 - u0) > (T)0 ? (T)0 : f;
+}
+
+template <typename T, int V, bool INT>
+__device__ __forceinline__ void cosmo_strip(const C2Args& a, int lane, int s0, int j0, int kp) {
+    using Row = VRow<T, V>;
+    const int c0 = s0 + V * lane;   // first own column
+    const bool wrap = a.u.wrap;
+    const bool vin = INT || (a.vec && (wrap ? (c0 >= 0 && c0 + V <= a.nx) : (c0 >= -2 && c0 + V <= a.nx + 2)));
+    const int olo = max(s0 + 2, 0), ohi = min(s0 + 32 * V - 3, a.nx - 1);
+    const bool vout = a.vecout && c0 >= olo && c0 + V - 1 <= ohi;
+    auto col = [&](const T* ub, int c) -> T {
+        if (INT) return ub[c];
+        if (wrap) return ub[wrap1(c, a.nx)];
+        return (c >= -2 && c < a.nx + 2) ? ub[c] : (T)0;
+    };
+    const int64_t pu = a.u.pitch[1], po = a.out.pitch[1];
+    const T* row0 = (const T*)a.u.p + (int64_t)(kp + a.u.org[2]) * a.u.pitch[2] + (int64_t)a.u.org[1] * pu + a.u.org[0];
+    int rl = j0 - 2;   // next row to load
+    const T* lp = row0 + (int64_t)(wrap ? wrap1(rl, a.ny) : rl) * pu;
+    auto load_next = [&](Row& x) {
+        if (vin) {
+            x = *(const Row*)(lp + c0);
+        } else {
+#pragma unroll
+            for (int e = 0; e < V; ++e) x.v[e] = col(lp, c0 + e);
+        }
+        ++rl;
+        lp += pu;
+        if (wrap && (rl <= 0 || rl >= a.ny)) lp = row0 + (int64_t)wrap1(rl, a.ny) * pu;
+    };
+    const T wc = wsel<T>(a.wc, a.fc), wip = wsel<T>(a.wip, a.fip), wim = wsel<T>(a.wim, a.fim);
+    const T wjp = wsel<T>(a.wjp, a.fjp), wjm = wsel<T>(a.wjm, a.fjm), cf = wsel<T>(a.coef, a.coeff);
+    auto lap = [&](T ip, T im, T jp, T jm, T c) {
+        T v = wip * ip;
+        v = fma(wim, im, v);
+        v = fma(wjp, jp, v);
+        v = fma(wjm, jm, v);
+        return fma(wc, c, v);
+    };
+    const int rend = min(j0 + a.R, a.ny) + 1;
+    const int n = rend - (j0 - 2) + 1;
+    Row Q[3], U[3], L[3], F[3];
+#pragma unroll
+    for (int s = 0; s < 3; ++s) load_next(Q[s]);   // n >= 5: rows j0-2 .. j0 exist
+    T* op = (T*)a.out.p + (int64_t)(kp + a.out.org[2]) * a.out.pitch[2] + (int64_t)(j0 + a.out.org[1]) * po +
+            a.out.org[0];
+    // one step; S = t % 3: slot S holds u row r / lap row r-1 / flux_y row r-2,
+    // (S+2)%3 the row before each, (S+1)%3 the one before that.  Lane 0's left
+    // and lane 31's right neighbours are its own values (the shuffle's
+    // identity): they only reach columns the strip does not store.
+    auto step = [&](auto Sc, bool pf, bool do_l, bool do_f, bool do_out) {
+        constexpr int s = decltype(Sc)::value, s1 = (s + 1) % 3, s2 = (s + 2) % 3;
+        U[s] = Q[s];
+        if (pf) load_next(Q[s]);
+        if (do_l) {   // lap at row r-1 from u rows r-2, r-1, r
+            const Row& um = U[s1];
+            const Row& u0 = U[s2];
+            const Row& up = U[s];
+            const T left = __shfl_up_sync(0xffffffffu, u0.v[V - 1], 1);
+            const T right = __shfl_down_sync(0xffffffffu, u0.v[0], 1);
+            Row Lr;
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+                Lr.v[e] = lap(e + 1 < V ? u0.v[e + 1] : right, e > 0 ? u0.v[e - 1] : left, up.v[e], um.v[e], u0.v[e]);
+            L[s] = Lr;
+        }
+        if (do_f) {   // flux_y and flux_x at row r-2, then ustage there
+            const Row& u2 = U[s1];   // u row r-2
+            const Row& u1 = U[s2];   // u row r-1
+            const Row& l2 = L[s2];   // lap row r-2
+            const Row& l1 = L[s];    // lap row r-1
+            Row fy, fx;
+#pragma unroll
+            for (int e = 0; e < V; ++e) fy.v[e] = limflux<T>(u2.v[e], u1.v[e], l2.v[e], l1.v[e]);
+            F[s] = fy;
+            const T ur = __shfl_down_sync(0xffffffffu, u2.v[0], 1);
+            const T lr = __shfl_down_sync(0xffffffffu, l2.v[0], 1);
+#pragma unroll
+            for (int e = 0; e < V; ++e)
+                fx.v[e] = limflux<T>(u2.v[e], e + 1 < V ? u2.v[e + 1] : ur, l2.v[e], e + 1 < V ? l2.v[e + 1] : lr);
+            const T fxl = __shfl_up_sync(0xffffffffu, fx.v[V - 1], 1);   // flux_x of the face left of the lane
+            if (do_out) {
+                const Row& fym = F[s2];   // flux_y row r-3
+                Row o;
+#pragma unroll
+                for (int e = 0; e < V; ++e)
+                    o.v[e] = u2.v[e] - cf * ((fx.v[e] - (e > 0 ? fx.v[e - 1] : fxl)) + (fy.v[e] - fym.v[e]));
+                if (vout) {
+                    *(Row*)(op + c0) = o;
+                } else {
+#pragma unroll
+                    for (int e = 0; e < V; ++e)
+                        if (c0 + e >= olo && c0 + e <= ohi) op[c0 + e] = o.v[e];
+                }
+                op += po;
+            }
+        }
+    };
+    using I0 = std::integral_constant<int, 0>;
+    using I1 = std::integral_constant<int, 1>;
+    using I2 = std::integral_constant<int, 2>;
+    // steps 0 .. 5: lap from t = 2, fluxes from t = 3, ustage from t = 4 (n >= 5)
+    step(I0{}, 3 < n, false, false, false);
+    step(I1{}, 4 < n, false, false, false);
+    step(I2{}, 5 < n, true, false, false);
+    step(I0{}, 6 < n, true, true, false);
+    step(I1{}, 7 < n, true, true, true);
+    if (5 < n) step(I2{}, 8 < n, true, true, true);
+    int t0 = 6;
+    for (; t0 + 2 + 3 < n; t0 += 3) {
+        step(I0{}, true, true, true, true);
+        step(I1{}, true, true, true, true);
+        step(I2{}, true, true, true, true);
+    }
+    for (; t0 < n; t0 += 3) {
+        step(I0{}, t0 + 3 < n, true, true, true);
+        if (t0 + 1 < n) step(I1{}, t0 + 4 < n, true, true, true);
+        if (t0 + 2 < n) step(I2{}, t0 + 5 < n, true, true, true);
+    }
+}
+
+template <typename T, int V>
+__global__ void __launch_bounds__(256) cosmo_warp(const C2Args a) {
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, lane = tid & 31;
+    const int64_t wid = ((int64_t)blockIdx.x * (blockDim.x * blockDim.y) + tid) >> 5;
+    const int64_t per_plane = (int64_t)a.nstrips * ((a.ny + a.R - 1) / a.R);
+    const int kp = (int)(wid / per_plane);
+    if (kp >= a.nz) return;   // whole warp
+    const int64_t wq = wid - (int64_t)kp * per_plane;
+    const int strip = (int)(wq % a.nstrips);
+    const int j0 = (int)(wq / a.nstrips) * a.R;
+    const int s0 = strip * (32 * V - 4) - 2 - a.sh;
+    const bool inside = a.u.wrap ? (s0 >= 0 && s0 + 32 * V <= a.nx) : (s0 >= -2 && s0 + 32 * V <= a.nx + 2);
+    if (a.vec && a.vecout && inside) cosmo_strip<T, V, true>(a, lane, s0, j0, kp);
+    else cosmo_strip<T, V, false>(a, lane, s0, j0, kp);
+}
+
+template <typename T, int V>
+static int launch_cosmo_t(hfav_plan_t* p, C2Args& a, int TX, int TY, cudaStream_t st) {
+    const int NT = TX * TY;
+    constexpr size_t VB = sizeof(T) * V;
+    a.sh = (((a.u.org[0] - 2) % V) + V) % V;
+    a.vec = ((uintptr_t)a.u.p % VB == 0) && (a.u.pitch[1] % V == 0) && (a.u.pitch[2] % V == 0);
+    a.vecout = ((uintptr_t)a.out.p % VB == 0) && (a.out.pitch[1] % V == 0) && (a.out.pitch[2] % V == 0) &&
+               ((a.out.org[0] - a.u.org[0]) % V == 0);
+    a.nstrips = (a.nx + a.sh + (32 * V - 4) - 1) / (32 * V - 4);
+    static int occ = 0, occ_nt = 0;   // resident CTAs per SM at NT threads
+    if (occ_nt != NT) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, cosmo_warp<T, V>, NT, 0) != cudaSuccess || occ <= 0) {
+            cudaGetLastError();
+            occ = 1;
+        }
+        occ_nt = NT;
+    }
+    a.R = chunk_planes((int64_t)a.nstrips * a.nz, a.ny, (int64_t)occ * (NT / 32) * device_sms(), 4);
+    const int64_t warps = (int64_t)a.nstrips * ((a.ny + a.R - 1) / a.R) * a.nz;
+    const int64_t blocks = (warps + NT / 32 - 1) / (NT / 32);
+    if (blocks > 0x7fffffffLL) return set_error(HFAV_EUNSUPPORTED, "grid too large");
+    cosmo_warp<T, V><<<(unsigned)blocks, dim3(TX, TY), 0, st>>>(a);
+    HFAV_LAUNCHED(p->rt, "cosmo_fused", st);
+    return HFAV_OK;
+}
+
+int launch_cosmo(hfav_plan_t* p, const Schedule& s, void* const* ax, void* const* go, cudaStream_t st) {
+    if (s.fusion == FUSE_UNFUSED) return launch_generic(p, ax, go, st);
+    if (s.fusion != FUSE_FULL || s.placement != PLACE_REG)
+        return set_error(HFAV_EUNSUPPORTED, "the COSMO pipeline runs full:reg or unfused");
+    const hfav_grid& g = p->grids[0];
+    const ChainMap& m = p->cmap;
+    C2Args a;
+    memset(&a, 0, sizeof a);
+    a.u = caller_view(p, ax[0]);
+    a.out = caller_view(p, go[0]);
+    a.out.wrap = 0;
+    a.nx = (int)g.extent[0]; a.ny = (int)g.extent[1]; a.nz = (int)g.extent[2];
+    a.wc = m.w1[13]; a.wip = m.w1[14]; a.wim = m.w1[12]; a.wjp = m.w1[16]; a.wjm = m.w1[10];
+    a.fc = (float)a.wc; a.fip = (float)a.wip; a.fim = (float)a.wim; a.fjp = (float)a.wjp; a.fjm = (float)a.wjm;
+    a.coef = m.coef;
+    a.coeff = (float)m.coef;
+    const bool f64 = p->dtype == HFAV_F64, wide = c2w_wide(s.tx, s.ty);
+    if (f64) return wide ? launch_cosmo_t<double, 2>(p, a, s.tx, s.ty, st) : launch_cosmo_t<double, 1>(p, a, s.tx, s.ty, st);
+    return wide ? launch_cosmo_t<float, 4>(p, a, s.tx, s.ty, st) : launch_cosmo_t<float, 2>(p, a, s.tx, s.ty, st);
 }
 
 int launch_chain2d(hfav_plan_t* p, const Schedule& s, void* const* ax, void* const* go, cudaStream_t st) {

@@ -143,6 +143,7 @@ int scratch(hfav_plan_t* p, const std::string& name, size_t bytes, void** out);
 
 // launchers (chain.cu / godunov.cu)
 int launch_chain2d(hfav_plan_t* p, const Schedule& s, void* const* ax, void* const* go, cudaStream_t st);
+int launch_cosmo(hfav_plan_t* p, const Schedule& s, void* const* ax, void* const* go, cudaStream_t st);
 int launch_chain3d(hfav_plan_t* p, const Schedule& s, void* const* ax, void* const* go, cudaStream_t st);
 int launch_generic(hfav_plan_t* p, void* const* ax, void* const* go, cudaStream_t st);
 int launch_godunov(hfav_plan_t* p, const Schedule& s, void* const* ax, void* const* go, int n_steps,

@@ -42,7 +42,7 @@ struct Schedule {
 bool parse_schedule(const char* s, Schedule* out, std::string* err);
 
 // Kernel pipelines the planner can map a fusion group onto.
-enum Pipeline { PIPE_GENERIC = 0, PIPE_CHAIN2D = 1, PIPE_CHAIN3D = 2, PIPE_GODUNOV = 3 };
+enum Pipeline { PIPE_GENERIC = 0, PIPE_CHAIN2D = 1, PIPE_CHAIN3D = 2, PIPE_GODUNOV = 3, PIPE_COSMO = 4 };
 
 // Field ids of a recognised Godunov DAG (x sweep then y sweep, optional CFL).
 struct GodunovMap {
@@ -55,6 +55,7 @@ struct GodunovMap {
 struct ChainMap {
     double w1[27] = {};   // first linear stencil, 3x3(x3) box weights, index (dk+1)*9+(dj+1)*3+(di+1)
     double w2[27] = {};   // second linear stencil (3D chain only)
+    double coef = 0.0;    // COSMO: diffusion coefficient c of ustage
     int rules[4] = {-1, -1, -1, -1};
 };
 

@@ -34,7 +34,7 @@ namespace {
 bool op_known(int op) {
     switch (op) {
         case HFAV_OP_STENCIL_LINEAR: case HFAV_OP_GRADMAG_HALF: case HFAV_OP_SQUASH:
-        case HFAV_OP_GENERIC: case HFAV_OP_CONSTOPRIM: case HFAV_OP_EOS: case HFAV_OP_SLOPE:
+        case HFAV_OP_GENERIC: case HFAV_OP_LIMFLUX: case HFAV_OP_DIFFUSE: case HFAV_OP_CONSTOPRIM: case HFAV_OP_EOS: case HFAV_OP_SLOPE:
         case HFAV_OP_TRACE: case HFAV_OP_QLEFTRIGHT: case HFAV_OP_RIEMANN: case HFAV_OP_CMPFLX:
         case HFAV_OP_UPDATE: case HFAV_OP_CFL_DT: case HFAV_OP_REDUCE_SUM: case HFAV_OP_BROADCAST:
             return true;
@@ -624,6 +624,55 @@ bool recognise_chain(hfav_plan_t* p) {
     return false;
 }
 
+// offset of one ref is exactly `want` (i, j, k)
+bool off_is(const hfav_ref& x, int di, int dj, int dk) { return x.off[0] == di && x.off[1] == dj && x.off[2] == dk; }
+
+// COSMO horizontal diffusion (Sec. 5.3): a 5-point star Laplacian of the
+// axiom, LIMFLUX along i and along j of (u, lap), DIFFUSE into the goal, with
+// the refs in the order the op catalogue states; 2D, or 3D with no k offsets.
+bool recognise_cosmo(hfav_plan_t* p) {
+    const Dag& d = p->dag;
+    if (d.axioms.size() != 1 || d.goals.size() != 1 || d.feedback || d.rules.size() != 4) return false;
+    if (d.ndim != 2 && d.ndim != 3) return false;
+    const int u = d.axioms[0];
+    const Rule* lap = nullptr;
+    const Rule* fl[2] = {nullptr, nullptr};
+    const Rule* up = nullptr;
+    int lap_id = -1, fl_id[2] = {-1, -1}, up_id = -1;
+    for (size_t k = 0; k < d.rules.size(); ++k) {
+        const Rule& r = d.rules[k];
+        if (r.op == HFAV_OP_STENCIL_LINEAR) { lap = &r; lap_id = (int)k; }
+        else if (r.op == HFAV_OP_LIMFLUX && (r.axis == 0 || r.axis == 1)) { fl[r.axis] = &r; fl_id[r.axis] = (int)k; }
+        else if (r.op == HFAV_OP_DIFFUSE) { up = &r; up_id = (int)k; }
+    }
+    if (!lap || !fl[0] || !fl[1] || !up) return false;
+    double w[27];
+    if (!take_linear(*lap, u, w)) return false;
+    // a 5-point star in the (i, j) plane: box indices 13 centre, 14 / 12 i+-1, 16 / 10 j+-1
+    for (int k = 0; k < 27; ++k)
+        if (k != 13 && k != 14 && k != 12 && k != 16 && k != 10 && w[k] != 0.0) return false;
+    const int L = lap->out[0];
+    for (int a = 0; a < 2; ++a) {
+        const Rule& r = *fl[a];
+        const int di = a == 0, dj = a == 1;
+        if (r.in.size() != 4 || r.out.size() != 1) return false;
+        if (r.in[0].field != u || !off_is(r.in[0], 0, 0, 0) || r.in[1].field != u || !off_is(r.in[1], di, dj, 0) ||
+            r.in[2].field != L || !off_is(r.in[2], 0, 0, 0) || r.in[3].field != L || !off_is(r.in[3], di, dj, 0))
+            return false;
+    }
+    const int fx = fl[0]->out[0], fy = fl[1]->out[0];
+    if (up->in.size() != 5 || up->out.size() != 1 || up->params.size() != 1 || up->out[0] != d.goals[0]) return false;
+    if (up->in[0].field != u || !off_is(up->in[0], 0, 0, 0) || up->in[1].field != fx || !off_is(up->in[1], -1, 0, 0) ||
+        up->in[2].field != fx || !off_is(up->in[2], 0, 0, 0) || up->in[3].field != fy ||
+        !off_is(up->in[3], 0, -1, 0) || up->in[4].field != fy || !off_is(up->in[4], 0, 0, 0))
+        return false;
+    for (int k = 0; k < 27; ++k) p->cmap.w1[k] = w[k];
+    p->cmap.coef = up->params[0];
+    p->cmap.rules[0] = lap_id; p->cmap.rules[1] = fl_id[0]; p->cmap.rules[2] = fl_id[1]; p->cmap.rules[3] = up_id;
+    p->pipeline = PIPE_COSMO;
+    return true;
+}
+
 // Godunov: one rule of each Hydro2D op per axis (0 then 1), wired as the
 // op catalogue in hfav.h states, plus an optional CFL_DT rule for dt.
 bool recognise_godunov(hfav_plan_t* p) {
@@ -720,9 +769,11 @@ int recognise(hfav_plan_t* p) {
     p->pipeline = PIPE_GENERIC;
     if (recognise_chain(p)) return HFAV_OK;
     if (recognise_godunov(p)) return HFAV_OK;
+    if (recognise_cosmo(p)) return HFAV_OK;
     // generic DAGs of the stencil catalogue run unfused, one kernel per rule
     for (auto& r : p->dag.rules)
-        if (r.op != HFAV_OP_STENCIL_LINEAR && r.op != HFAV_OP_GRADMAG_HALF && r.op != HFAV_OP_SQUASH)
+        if (r.op != HFAV_OP_STENCIL_LINEAR && r.op != HFAV_OP_GRADMAG_HALF && r.op != HFAV_OP_SQUASH &&
+            r.op != HFAV_OP_LIMFLUX && r.op != HFAV_OP_DIFFUSE)
             return HFAV_EUNSUPPORTED;
     return HFAV_OK;
 }
@@ -738,6 +789,10 @@ bool schedule_valid(const hfav_plan_t* p, const Schedule& s, std::string* why) {
     }
     if (s.fusion == FUSE_UNFUSED && s.placement != PLACE_HBM) {
         if (why) *why = "unfused implies hbm intermediates";
+        return false;
+    }
+    if (p->pipeline == PIPE_COSMO && s.fusion != FUSE_UNFUSED && (s.fusion != FUSE_FULL || s.placement != PLACE_REG)) {
+        if (why) *why = "the COSMO pipeline runs fully fused with register windows (full:reg) or unfused";
         return false;
     }
     return true;
@@ -758,7 +813,7 @@ std::vector<Schedule> valid_schedules(const hfav_plan_t* p) {
 
 std::string dump_json(const hfav_plan_t* p) {
     static const char* sto[] = {"axiom", "goal", "hbm", "rolling", "scalar"};
-    static const char* pipes[] = {"generic", "chain2d", "chain3d", "godunov"};
+    static const char* pipes[] = {"generic", "chain2d", "chain3d", "godunov", "cosmo"};
     const Analysis& A = p->an;
     std::ostringstream o;
     o << "{\"pipeline\":\"" << pipes[p->pipeline] << "\",\"schedule\":\"" << p->sched.str()

@@ -22,7 +22,7 @@ ERRORS = {-1: "EINVAL", -2: "ECYCLE", -3: "EPRODUCER", -4: "EMISSING", -5: "EHAL
           -7: "ENOMEM", -8: "ECUDA", -9: "ETIMEOUT", -10: "ENONPHYSICAL", -11: "EUNSUPPORTED"}
 HFAV_F64, HFAV_F32 = 0, 1
 HFAV_BC_PERIODIC, HFAV_BC_HALO_GIVEN = 0, 1
-OP = dict(STENCIL_LINEAR=1, GRADMAG_HALF=2, SQUASH=3, GENERIC=4, CONSTOPRIM=10, EOS=11, SLOPE=12, TRACE=13,
+OP = dict(STENCIL_LINEAR=1, GRADMAG_HALF=2, SQUASH=3, GENERIC=4, LIMFLUX=5, DIFFUSE=6, CONSTOPRIM=10, EOS=11, SLOPE=12, TRACE=13,
           QLEFTRIGHT=14, RIEMANN=15, CMPFLX=16, UPDATE=17, CFL_DT=20, REDUCE_SUM=21, BROADCAST=22)
 STORAGE = ["axiom", "goal", "hbm", "rolling", "scalar"]
 N_FEATURES = 16
@@ -261,6 +261,25 @@ def chain3d_dag():
     D.rule("STENCIL_LINEAR", [("s1", o) for o in star], ["s2"], params=w)
     D.rule("GRADMAG_HALF", [("s2", o) for o in star[:6]], ["s3"])
     D.rule("SQUASH", ["s3"], ["out"])
+    D.axiom("u")
+    D.goal("out")
+    return D
+
+
+def cosmo_dag(c=0.05, ndim=3):
+    """COSMO horizontal diffusion (Sec. 5.3): ulapstage (5-point Laplacian of
+    u), flux_x / flux_y (limited Laplacian differences across the faces i+1/2,
+    j+1/2), ustage (u minus c times the flux divergence); no dependency in k."""
+    D = DagSpec(ndim, stream_axis=ndim - 1)
+    z = (0,) * (ndim - 2)
+    D.rule("STENCIL_LINEAR", [("u", (1, 0) + z), ("u", (-1, 0) + z), ("u", (0, 1) + z), ("u", (0, -1) + z),
+                              ("u", (0, 0) + z)], ["lap"], params=[1, 1, 1, 1, -4])
+    D.rule("LIMFLUX", [("u", (0, 0) + z), ("u", (1, 0) + z), ("lap", (0, 0) + z), ("lap", (1, 0) + z)], ["flx"],
+           axis=0)
+    D.rule("LIMFLUX", [("u", (0, 0) + z), ("u", (0, 1) + z), ("lap", (0, 0) + z), ("lap", (0, 1) + z)], ["fly"],
+           axis=1)
+    D.rule("DIFFUSE", [("u", (0, 0) + z), ("flx", (-1, 0) + z), ("flx", (0, 0) + z), ("fly", (0, -1) + z),
+                       ("fly", (0, 0) + z)], ["out"], params=[c])
     D.axiom("u")
     D.goal("out")
     return D

@@ -82,3 +82,17 @@ def test_planes_are_independent():
     v[2:-2] = u[2:-2][perm]
     _, _, _, out2 = oracle.cosmo(v, 0.05)
     assert np.array_equal(out2, out[perm])
+
+
+def test_neighbourhood_block_gives_the_whole_domain_value():
+    """The full-size GPU test checks sampled cells against the oracle run on
+    each cell's periodic 5 x 5 neighbourhood in its plane: that block fixes the
+    cell (the composed stencil reaches two cells in i and j)."""
+    from tests.test_gpu_chain import _block_wrap, _sample_points
+    u = I.cosmo_input(24, 20, 2, seed=3)
+    full = oracle.cosmo(u, 0.05)[3]
+    for kq in range(2):
+        plane = u[kq + 2, 2:-2, 2:-2]
+        for p in _sample_points(20, 2, 25, 4):
+            blk = _block_wrap(plane, p, 2)[None]
+            assert oracle.cosmo(np.pad(blk, 2), 0.05)[3][0, 2, 2] == full[kq][tuple(p)]

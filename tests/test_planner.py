@@ -193,3 +193,20 @@ def test_schedules_and_variants():
         P.schedule = "full:reg:48x4"
     f = P.features("full:reg:32x4")
     assert f.shape == (16,) and f[6] == 1.0 and f[13] == 0.0
+
+
+def test_cosmo_pipeline_recognised_with_its_schedules():
+    """The COSMO DAG with the catalogue's LIMFLUX / DIFFUSE ops keeps the
+    paper's rolling buffers (5 Ni + 2) and maps onto the fused COSMO pipeline,
+    which runs fully fused with register windows or unfused."""
+    Ni = 128
+    P = H.analyze(H.cosmo_dag(), extent=(Ni, 96, 40))
+    assert P.field("lap")["storage_elems"] + P.field("fly")["storage_elems"] + P.field("flx")["storage_elems"] == \
+        5 * Ni + 2
+    g = H.Grid.make((64, 48, 5), (1, 68, 68 * 52), 2)
+    pl = H.Plan(H.cosmo_dag(), [g], H.HFAV_F64, H.HFAV_BC_PERIODIC, "full:reg:32x4")
+    assert pl.dump()["pipeline"] == "cosmo"
+    assert sorted(pl.variants()) == sorted([f"{f}:{t}" for f in ("full:reg", "unfused:hbm")
+                                            for t in ("32x4", "64x4", "128x2", "32x8")])
+    with pytest.raises(Exception):
+        H.Plan(H.cosmo_dag(), [g], H.HFAV_F64, H.HFAV_BC_PERIODIC, "full:smem:32x4")
