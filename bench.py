@@ -45,6 +45,9 @@ def godunov_flops_sweep(it):
 GODUNOV_CFL_FLOPS = 16.0
 CHAIN2D_FLOPS = 14.0     # L 5, G 7 (2 sub, 2 mul, add, sqrt, halve), out 2
 CHAIN3D_FLOPS = 26.0     # s1 7, s2 7, s3 10, out 2
+COSMO_FLOPS = 16.0       # lap 5, flux_x 3, flux_y 3, ustage 5 (limiter compares not counted)
+COSMO_C = 0.05           # diffusion coefficient of ustage
+COSMO_NZ = 64            # planes of the COSMO workloads
 
 
 # DRAM bytes (read + write) per launch of a workload's dominant kernel from one
@@ -221,6 +224,46 @@ class Batch(Godunov):
         return None, None, None
 
 
+class Cosmo(Workload):
+    """COSMO horizontal diffusion (Sec. 5.3) over an n x n x nz grid, one application per step."""
+    fused_prefix = ("full",)
+
+    def __init__(self, H, I, torch, dev, n, nz, dtype, seed=7):
+        import numpy as np
+        self.n, self.nz, self.dtype = n, nz, dtype
+        self.name = f"cosmo_{'fp64' if dtype == 'f64' else 'fp32'}_{n}x{n}x{nz}"
+        u = I.cosmo_input(n, n, nz, seed=seed, dtype=np.float64 if dtype == "f64" else np.float32)
+        self.u = torch.from_numpy(u).to(dev)
+        self.out = torch.empty_like(self.u)
+        self.dag = H.cosmo_dag(COSMO_C)
+        self.hdt = H.HFAV_F64 if dtype == "f64" else H.HFAV_F32
+        self.grids = [H.Grid.of(self.u, 2)]
+        self.plan = H.Plan(self.dag, self.grids, self.hdt, H.HFAV_BC_PERIODIC, "full:reg:32x4")
+        self.esize = 8 if dtype == "f64" else 4
+
+    def unfused_plan(self, H):
+        return H.Plan(self.dag, self.grids, self.hdt, H.HFAV_BC_PERIODIC, "unfused")
+
+    def run(self, plan):
+        plan.run([self.u], [self.out], 1)
+
+    def cells_per_step(self):
+        return self.n * self.n * self.nz
+
+    def compulsory_bytes(self, sched):
+        return 2 * self.esize * self.cells_per_step()
+
+    def kernel_work(self, kernel, it):
+        cells = self.cells_per_step()
+        if self.dtype == "f32":
+            return "hbm", 2 * self.esize * cells, "GB/s", peaks().get("hbm_gbs", 6787.6), \
+                "measured copy bandwidth (MEASURED_PEAKS.json)"
+        return "alu", COSMO_FLOPS * cells, "GFLOP/s", PEAK_FP64_GFLOPS, "FP64 DFMA rate measured by the repo's probe"
+
+    def io(self):
+        return None, None, None
+
+
 class Chain(Workload):
     fused_prefix = ("full", "sweep")
 
@@ -267,7 +310,8 @@ class Chain(Workload):
         return None, None, None
 
 
-WORKLOADS = ["godunov1024_f64", "godunov4096_f32", "batch64_f32", "chain2d256_f64", "chain2d16384_f32", "chain3d512_f32"]
+WORKLOADS = ["godunov1024_f64", "godunov4096_f32", "batch64_f32", "chain2d256_f64", "chain2d16384_f32", "chain3d512_f32",
+             "cosmo1024_f32"]
 
 
 def make(name, H, I, torch, dev):
@@ -287,6 +331,9 @@ def make(name, H, I, torch, dev):
     if m:
         dims = int(m.group(1))
         return Chain(H, I, torch, dev, dims, int(m.group(2)), m.group(3), 0 if dims == 2 else 4)
+    m = re.fullmatch(r"cosmo(\d+)_(f32|f64)", name)
+    if m:
+        return Cosmo(H, I, torch, dev, int(m.group(1)), COSMO_NZ, m.group(2))
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -314,6 +361,13 @@ def oracle_sample(workload, n=None):
         oracle.chain2d(u)
         dt = time.perf_counter() - t0
         return n * n / dt / 1e9, dt, 0.0, f"{n}x{n} u~U[0,1), single thread"
+    if workload.startswith("cosmo"):
+        n = n or 1024
+        u = I.cosmo_input(n, n, 4, seed=7)
+        t0 = time.perf_counter()
+        oracle.cosmo(u, COSMO_C)
+        dt = time.perf_counter() - t0
+        return n * n * 4 / dt / 1e9, dt, 0.0, f"{n}x{n}x4 u~U[0,1), single thread"
     n = n or 160
     u = I.chain3d_input(n, seed=4)
     t0 = time.perf_counter()
@@ -335,6 +389,9 @@ def workload_name(key):
     if m:
         dims, n = int(m.group(1)), m.group(2)
         return f"chain{dims}d_{'fp64' if m.group(3) == 'f64' else 'fp32'}_{'x'.join([n] * dims)}"
+    m = re.fullmatch(r"cosmo(\d+)_(f32|f64)", key)
+    if m:
+        return f"cosmo_{'fp64' if m.group(2) == 'f64' else 'fp32'}_{m.group(1)}x{m.group(1)}x{COSMO_NZ}"
     raise SystemExit(f"unknown workload {key}")
 
 
@@ -528,13 +585,13 @@ def bench(args, name, torch, H, I, dev, ws, rank, local):
 
 
 def _axg(w):
-    if isinstance(w, Chain):
+    if isinstance(w, (Chain, Cosmo)):
         return [w.u], [w.out]
     return w.ins, w.outs
 
 
 def _nsteps(w):
-    return 1 if isinstance(w, Chain) else w.tsteps
+    return 1 if isinstance(w, (Chain, Cosmo)) else w.tsteps
 
 
 def main():
@@ -543,7 +600,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=WORKLOADS[0], help="one of " + ", ".join(WORKLOADS + ["all"]) + ", or chain2d<N>_f32|f64 / chain3d<N>_f32|f64 (other chain sizes)")
+    ap.add_argument("--workload", default=WORKLOADS[0], help="one of " + ", ".join(WORKLOADS + ["all"]) + ", or chain2d<N>_f32|f64 / chain3d<N>_f32|f64 / cosmo<N>_f32|f64 (other sizes)")
     ap.add_argument("--schedule", default=None, help="fixed schedule (default: autotuned among fused ones)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--once", action="store_true", help="profiling case: build the plan and run it once")
