@@ -334,6 +334,13 @@ int hfav_chain2d_static(const double* u, int64_t nx, int64_t ny, int64_t pitch, 
  * them to within 2 ulp of IEEE division. */
 int hfav_selftest_arith(const double* x, int64_t n, double* rcp_out, double* quot_out, void* stream);
 
+/* Diagnostic: the FP64 reciprocal square root of the Riemann solver's Newton
+ * iteration in the FP32-bulk form (hardware estimate refined by one
+ * Newton-Raphson step).  For n positive doubles x (device): out[k] ~
+ * 1/sqrt(x[k]) (device array).  Tests hold it to within 2^-38 relative of
+ * CUDA's rsqrt. */
+int hfav_selftest_rsqrt(const double* x, int64_t n, double* out, void* stream);
+
 void hfav_free(hfav_plan_t* plan);
 
 const char* hfav_last_error(void);

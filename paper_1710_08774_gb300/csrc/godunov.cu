@@ -43,6 +43,7 @@ struct GGrid {
 struct GCommon {
     double cfl, gamma;
     double ig1;            // 1 / (gamma - 1)
+    double ashk;           // (gamma + 1) / (2 gamma), the shock coefficient of the Riemann solver
     float gammaf, ig1f;    // gamma and 1 / (gamma - 1) rounded to FP32 on the host, so an
                            // FP32 kernel converts no FP64 parameter on the device
     int step;
@@ -139,6 +140,7 @@ __global__ void __launch_bounds__(256) gsweep_xw(const GGrid<T>* __restrict__ gr
     const int w = threadIdx.x >> 5;
     const int A = blockDim.x >> 5;
     const T g = csel<T>(C.gamma, C.gammaf), ig1 = csel<T>(C.ig1, C.ig1f);
+    const double ashk = C.ashk;
     int nonconv = 0;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int2 it = items[item];
@@ -192,7 +194,7 @@ __global__ void __launch_bounds__(256) gsweep_xw(const GGrid<T>* __restrict__ gr
                 Face4<T> q0n = (exact && s == nch + 1) ? qmNext : shfl_face(qmNew, 0);
                 if (lane == 31) qR = q0n;
                 int nc_local = 0;
-                Face4<T> F = flux(riemann(qpOld, qR, g, &nc_local), ig1);
+                Face4<T> F = flux(riemann(qpOld, qR, g, ashk, &nc_local), ig1);
                 if (32 * v - 1 + lane <= nf - 2) nonconv |= nc_local;
                 if (v == 0) {
                     Fsave = shfl_face(F, 0);   // face of cell a0-1
@@ -255,6 +257,7 @@ __global__ void __launch_bounds__(256) gsweep_x(const GGrid<T>* __restrict__ gri
     if (HBM) st = (T*)C.slab + (size_t)blockIdx.x * per;
     else st = (T*)smem_raw;
     const T g = csel<T>(C.gamma, C.gammaf), ig1 = csel<T>(C.ig1, C.ig1f);
+    const double ashk = C.ashk;
     int nonconv = 0;
     for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
         const int2 it = items[item];
@@ -301,7 +304,7 @@ __global__ void __launch_bounds__(256) gsweep_x(const GGrid<T>* __restrict__ gri
                 Face4<T> L, R;
                 L.r = QP[lm + 1]; L.u = QP[QS + lm + 1]; L.v = QP[2 * QS + lm + 1]; L.p = QP[3 * QS + lm + 1];
                 R.r = QM[l + 1]; R.u = QM[QS + l + 1]; R.v = QM[2 * QS + l + 1]; R.p = QM[3 * QS + l + 1];
-                Face4<T> fl = flux(riemann(L, R, g, &nonconv), ig1);
+                Face4<T> fl = flux(riemann(L, R, g, ashk, &nonconv), ig1);
                 F[0 * (S + 1) + l] = fl.r; F[1 * (S + 1) + l] = fl.u; F[2 * (S + 1) + l] = fl.v; F[3 * (S + 1) + l] = fl.p;
             }
         }
@@ -367,7 +370,7 @@ __device__ __forceinline__ void ywin_load(const volatile T* p, int stride, YWin<
 // One row of the y pipeline for a thread: U2 is the conserved state of row r
 // in the y frame (rho, rho v, rho u, E).  Emits the updated cell r-2 into out.
 template <typename T>
-__device__ __forceinline__ bool ystep(YWin<T>& w, const Face4<T>& U2, int r, int j0, T dtdx, T g, T ig1,
+__device__ __forceinline__ bool ystep(YWin<T>& w, const Face4<T>& U2, int r, int j0, T dtdx, T g, double ashk, T ig1,
                                       int* nonconv, Face4<T>* out) {
     Prim<T> W2 = cons_to_prim(U2.r, U2.u, U2.v, U2.p, g);
     bool emit = false;
@@ -375,7 +378,7 @@ __device__ __forceinline__ bool ystep(YWin<T>& w, const Face4<T>& U2, int r, int
         Face4<T> qm, qp;
         slope_trace(w.W0, w.W1, W2, dtdx, qm, qp);   // cell r-1
         if (r >= j0 + 1) {
-            Face4<T> q = riemann(w.qpp, qm, g, nonconv);   // face between r-2 and r-1
+            Face4<T> q = riemann(w.qpp, qm, g, ashk, nonconv);   // face between r-2 and r-1
             Face4<T> F = flux(q, ig1);
             if (r >= j0 + 2) {   // update cell r-2 with its faces below (Fp) and above (F)
                 out->r = fma(-dtdx, F.r - w.Fp.r, w.U0.r);
@@ -399,6 +402,7 @@ __global__ void __launch_bounds__(256) gsweep_y(const GGrid<T>* __restrict__ gri
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int TX = blockDim.x, t = threadIdx.x, ty = threadIdx.y, TY = blockDim.y;
     const T g = csel<T>(C.gamma, C.gammaf), ig1 = csel<T>(C.ig1, C.ig1f);
+    const double ashk = C.ashk;
     const int lane_slot = ty * TX + t;
     volatile T* ring = nullptr;
     int stride = 0;
@@ -430,7 +434,7 @@ __global__ void __launch_bounds__(256) gsweep_y(const GGrid<T>* __restrict__ gri
                     U2.v = ldg_src(G, 1, i, jr); U2.p = ldg_src(G, 3, i, jr);
                     if (PL != PLACE_REG && r > j0 - 2) ywin_load(ring, stride, w);
                     Face4<T> o;
-                    bool emit = ystep(w, U2, r, j0, dtdx, g, ig1, &nonconv, &o);
+                    bool emit = ystep(w, U2, r, j0, dtdx, g, ashk, ig1, &nonconv, &o);
                     if (PL != PLACE_REG) ywin_store(ring, stride, w);
                     const int j = r - 2;
                     if (emit && j < G.ny) {
@@ -465,6 +469,7 @@ __global__ void __launch_bounds__(256) gfull(const GGrid<T>* __restrict__ grids,
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int TX = blockDim.x, t = threadIdx.x, ty = threadIdx.y, TY = blockDim.y;
     const T g = csel<T>(C.gamma, C.gammaf), ig1 = csel<T>(C.ig1, C.ig1f);
+    const double ashk = C.ashk;
     const size_t per = fstage_elems<T>(TX);
     T* st = (T*)smem_raw + ty * per;
     const int WS = TX + 2;
@@ -534,7 +539,7 @@ __global__ void __launch_bounds__(256) gfull(const GGrid<T>* __restrict__ grids,
                 Face4<T> L, Rr;
                 L.r = QP[l]; L.u = QP[TX + l]; L.v = QP[2 * TX + l]; L.p = QP[3 * TX + l];
                 Rr.r = QM[l + 1]; Rr.u = QM[TX + l + 1]; Rr.v = QM[2 * TX + l + 1]; Rr.p = QM[3 * TX + l + 1];
-                Face4<T> fl = flux(riemann(L, Rr, g, &nonconv), ig1);
+                Face4<T> fl = flux(riemann(L, Rr, g, ashk, &nonconv), ig1);
                 F[l] = fl.r; F[TX + l] = fl.u; F[2 * TX + l] = fl.v; F[3 * TX + l] = fl.p;
             }
             __syncthreads();
@@ -553,7 +558,7 @@ __global__ void __launch_bounds__(256) gfull(const GGrid<T>* __restrict__ grids,
                 U2.r = UR[t]; U2.u = UR[2 * TX + t]; U2.v = UR[TX + t]; U2.p = UR[3 * TX + t];
                 if (PL != PLACE_REG && r > j0 - 2) ywin_load(ring, stride, w);
                 Face4<T> o;
-                bool emit = ystep(w, U2, r, j0, dtdx, g, ig1, &nonconv, &o);
+                bool emit = ystep(w, U2, r, j0, dtdx, g, ashk, ig1, &nonconv, &o);
                 if (PL != PLACE_REG) ywin_store(ring, stride, w);
                 const int j = r - 2;
                 if (emit && j < G.ny) {
@@ -692,13 +697,13 @@ __global__ void u_qleftright(UArrays<T> A, int dir) {
 }
 
 template <typename T>
-__global__ void u_riemann(UArrays<T> A, int dir, T g, unsigned long long* counters) {
+__global__ void u_riemann(UArrays<T> A, int dir, T g, double ashk, unsigned long long* counters) {
     int nonconv = 0;
     U_LOOP(-1, na)
         const int64_t x = uidx(A, dir, a, b);
         Face4<T> L{A.qL[0][x], A.qL[1][x], A.qL[2][x], A.qL[3][x]};
         Face4<T> R{A.qR[0][x], A.qR[1][x], A.qR[2][x], A.qR[3][x]};
-        Face4<T> q = riemann(L, R, g, &nonconv);
+        Face4<T> q = riemann(L, R, g, ashk, &nonconv);
         A.gd[0][x] = q.r; A.gd[1][x] = q.u; A.gd[2][x] = q.v; A.gd[3][x] = q.p;
     }
     unsigned m = __ballot_sync(0xffffffffu, nonconv);
@@ -931,6 +936,7 @@ static int run_godunov_t(hfav_plan_t* p, const Schedule& s, void* const* ax, voi
     C.cfl = gm.cfl;
     C.gamma = gm.gamma;
     C.ig1 = 1.0 / (gm.gamma - 1.0);
+    C.ashk = 0.5 * (gm.gamma + 1.0) / gm.gamma;
     C.gammaf = (float)C.gamma;
     C.ig1f = (float)C.ig1;
     C.counters = rt->counters;
@@ -981,7 +987,7 @@ static int run_godunov_t(hfav_plan_t* p, const Schedule& s, void* const* ax, voi
                 u_slope<T><<<blocks, 256, 0, st>>>(A, dir); HFAV_LAUNCHED(rt, "u_slope", st);
                 u_trace<T><<<blocks, 256, 0, st>>>(A, dir, G, step, gm.cfl); HFAV_LAUNCHED(rt, "u_trace", st);
                 u_qleftright<T><<<blocks, 256, 0, st>>>(A, dir); HFAV_LAUNCHED(rt, "u_qleftright", st);
-                u_riemann<T><<<blocks, 256, 0, st>>>(A, dir, g, rt->counters); HFAV_LAUNCHED(rt, "u_riemann", st);
+                u_riemann<T><<<blocks, 256, 0, st>>>(A, dir, g, C.ashk, rt->counters); HFAV_LAUNCHED(rt, "u_riemann", st);
                 u_cmpflx<T><<<blocks, 256, 0, st>>>(A, dir, ig1); HFAV_LAUNCHED(rt, "u_cmpflx", st);
                 u_update<T><<<blocks, 256, 0, st>>>(A, dir, G, step, gm.cfl); HFAV_LAUNCHED(rt, "u_update", st);
             }
@@ -1113,7 +1119,22 @@ __global__ void selftest_arith_k(const double* __restrict__ x, int64_t n, double
         q[k] = div_nr(1.5, x[k]);
     }
 }
+__global__ void selftest_rsqrt_k(const double* __restrict__ x, int64_t n, double* __restrict__ r) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        r[k] = newton_rsqrt<float>(x[k]);
+}
 }  // namespace hfav
+
+extern "C" int hfav_selftest_rsqrt(const double* x, int64_t n, double* out, void* stream) {
+    using namespace hfav;
+    if (!x || !out || n < 0) return set_error(HFAV_EINVAL, "bad argument");
+    if (n == 0) return HFAV_OK;
+    int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    selftest_rsqrt_k<<<blocks, 256, 0, (cudaStream_t)stream>>>(x, n, out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(HFAV_ECUDA, cudaGetErrorString(e));
+    return HFAV_OK;
+}
 
 extern "C" int hfav_selftest_arith(const double* x, int64_t n, double* rcp_out, double* quot_out, void* stream) {
     using namespace hfav;
