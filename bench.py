@@ -45,6 +45,11 @@ def godunov_flops_sweep(it):
 GODUNOV_CFL_FLOPS = 16.0
 CHAIN2D_FLOPS = 14.0     # L 5, G 7 (2 sub, 2 mul, add, sqrt, halve), out 2
 CHAIN3D_FLOPS = 26.0     # s1 7, s2 7, s3 10, out 2
+# element reads + writes per cell of one unfused Godunov step (every kernel
+# reads each input array once and writes each output once), per pass:
+# boundary copy 4 + 4, constoprim 4 + 4, eos 2 + 2, slope 4 + 4, trace 9 + 8,
+# qleftright 8 + 8, riemann 8 + 4, cmpflx 4 + 4, update 8 + 4 = 93; two passes
+GODUNOV_UNFUSED_ARRAYS = 186.0
 COSMO_FLOPS = 16.0       # lap 5, flux_x 3, flux_y 3, ustage 5 (limiter compares not counted)
 COSMO_C = 0.05           # diffusion coefficient of ustage
 COSMO_NZ = 64            # planes of the COSMO workloads
@@ -172,6 +177,9 @@ class Godunov(Workload):
         return self.n * self.n * self.tsteps
 
     def compulsory_bytes(self, sched):
+        if sched.startswith("unfused"):
+            # every Hydro2D kernel of both passes reads its input arrays and writes its outputs
+            return GODUNOV_UNFUSED_ARRAYS * self.esize * self.n * self.n * self.tsteps
         per = 8 * self.esize * (2 if sched.startswith("sweep") else 1)   # 4 fields read + written per pass
         return per * self.n * self.n * self.tsteps
 
@@ -252,7 +260,9 @@ class Cosmo(Workload):
         return self.n * self.n * self.nz
 
     def compulsory_bytes(self, sched):
-        return 2 * self.esize * self.cells_per_step()
+        # unfused: lap reads u, writes lap; each flux reads u and lap, writes itself;
+        # ustage reads u and both fluxes, writes out
+        return (12 if sched.startswith("unfused") else 2) * self.esize * self.cells_per_step()
 
     def kernel_work(self, kernel, it):
         cells = self.cells_per_step()
@@ -297,7 +307,9 @@ class Chain(Workload):
         return self.n ** self.dims
 
     def compulsory_bytes(self, sched):
-        return 2 * self.esize * self.n ** self.dims
+        # unfused: every rule reads its input array and writes its output (3 rules in 2D, 4 in 3D)
+        per = (6 if self.dims == 2 else 8) if sched.startswith("unfused") else 2
+        return per * self.esize * self.n ** self.dims
 
     def kernel_work(self, kernel, it):
         cells = self.n ** self.dims
@@ -495,7 +507,11 @@ def bench(args, name, torch, H, I, dev, ws, rank, local):
             w.run(up)
         ums, _, _ = timed(up, args.steps)
         uvalue = w.cells_per_step() * args.steps / (sum(ums) * 1e-3) / 1e9
-        extra["unfused"] = {"value": uvalue, "ms_per_step": sum(ums) / len(ums)}
+        ub = w.compulsory_bytes("unfused")
+        extra["unfused"] = {"value": uvalue, "ms_per_step": sum(ums) / len(ums),
+                            "hbm_roofline": {"compulsory_bytes_per_step": ub,
+                                             "frac": ub / (sum(ums) / len(ums) * 1e-3) / 1e9 / peaks().get("hbm_gbs", 6787.6),
+                                             "of": "measured"}}
         extra["speedup_vs_unfused"] = value / ws / uvalue
         del up
     if w.graph:
