@@ -434,13 +434,8 @@ __device__ __forceinline__ void c2w_strip(const C2Args& a, int lane, int s0, int
     }
 }
 
-#ifdef C2W_MINB
-#define C2W_LB __launch_bounds__(256, C2W_MINB)
-#else
-#define C2W_LB __launch_bounds__(256)
-#endif
 template <typename T, int V>
-__global__ void C2W_LB chain2d_warp(const C2Args a) {
+__global__ void __launch_bounds__(256) chain2d_warp(const C2Args a) {
     const int tid = threadIdx.y * blockDim.x + threadIdx.x, lane = tid & 31;
     const int64_t wid = ((int64_t)blockIdx.x * (blockDim.x * blockDim.y) + tid) >> 5;
     const int strip = (int)(wid % a.nstrips);
