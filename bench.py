@@ -134,6 +134,18 @@ class Clocks:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def replica_value(total_ms, cells_per_step, steps, ws, device):
+    """Whole-job throughput of ws replicas (Gcell-updates/s): every rank's
+    cells over the slowest rank's time (max over ranks of the timed region).
+    Returns (value, max_ms)."""
+    if ws > 1:
+        import torch
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return ws * cells_per_step * steps / (total_ms * 1e-3) / 1e9, total_ms
+
+
 def dist_env():
     return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -493,12 +505,7 @@ def bench(args, name, torch, H, I, dev, ws, rank, local):
     ms, ktimes, launches = timed(w.plan, args.steps, timing=True)
     clocks = clk.stop()
     st = w.plan.status()
-    total_ms = sum(ms)
-    if ws > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = ws * w.cells_per_step() * args.steps / (total_ms * 1e-3) / 1e9
+    value, total_ms = replica_value(sum(ms), w.cells_per_step(), args.steps, ws, dev)
 
     extra = {}
     up = w.unfused_plan(H)
