@@ -1,0 +1,81 @@
+"""Seeded random DAGs of user rule bodies (HFAV_OP_EXPR) for the tests.
+
+Each rule body is given twice: as the C expression the library compiles and
+as the numpy function the oracle evaluates -- the same user kernel written for
+each side, so neither side's arithmetic comes from the other.  The bodies are
+continuous in their inputs (so an FP32 run and the FP64 oracle take no
+different branch at a near-tie) and keep values O(1) along a chain.
+"""
+import numpy as np
+
+# (C body, numpy body, number of inputs, parameter range or None per parameter)
+BODIES = [
+    ("p0 * in0 + p1 * in1", lambda a, b, p0, p1: p0 * a + p1 * b, 2, [(-0.9, 0.9), (-0.9, 0.9)]),
+    ("fmax(in0, in1) - p0 * in2", lambda a, b, c, p0: np.maximum(a, b) - p0 * c, 3, [(0.1, 0.6)]),
+    ("in0 > in1 ? in0 - in1 : p0 * (in0 - in1)", lambda a, b, p0: np.where(a > b, a - b, p0 * (a - b)), 2,
+     [(0.2, 0.8)]),
+    ("sqrt(in0 * in0 + p0)", lambda a, p0: np.sqrt(a * a + p0), 1, [(0.1, 1.0)]),
+    ("in0 / (1 + fabs(in1))", lambda a, b: a / (1 + np.abs(b)), 2, []),
+    ("exp(-in0 * in0) * in1 + p0 * in2", lambda a, b, c, p0: np.exp(-a * a) * b + p0 * c, 3, [(-0.5, 0.5)]),
+    ("fmin(in0, in1) * p0 + tanh(in2)", lambda a, b, c, p0: np.minimum(a, b) * p0 + np.tanh(c), 3, [(0.3, 0.9)]),
+    ("(in0 + in1 + in2 + in3 - 4 * in4) * p0", lambda a, b, c, d, e, p0: (a + b + c + d - 4 * e) * p0, 5,
+     [(0.1, 0.3)]),
+]
+
+
+def random_dag(ndim, n_rules, seed, radius=1, n_axioms=2):
+    """Rules as dicts {out, refs, c, fn, params}; axioms; goals (the outputs no
+    later rule reads).  Offsets are drawn within `radius` on every axis."""
+    rng = np.random.default_rng(seed)
+    axioms = [f"a{k}" for k in range(n_axioms)]
+    fields = list(axioms)
+    rules, read = [], set()
+    for r in range(n_rules):
+        c, fn, n_in, prange = BODIES[rng.integers(len(BODIES))]
+        refs = []
+        for k in range(n_in):
+            # favour recent fields so chains grow deep
+            f = fields[max(0, len(fields) - 1 - int(rng.integers(0, 3)))] if rng.random() < 0.7 else \
+                fields[int(rng.integers(len(fields)))]
+            off = tuple(int(rng.integers(-radius, radius + 1)) for _ in range(ndim)) + (0,) * (3 - ndim)
+            refs.append((f, off))
+            read.add(f)
+        params = [float(rng.uniform(lo, hi)) for lo, hi in prange]
+        out = f"t{r}"
+        rules.append(dict(out=out, refs=refs, c=c, fn=fn, params=params))
+        fields.append(out)
+    goals = [r["out"] for r in rules if r["out"] not in read]
+    return rules, axioms, goals
+
+
+def to_spec(rules, axioms, goals, ndim, shuffle_seed=None):
+    """The DAG as an hfav DagSpec of EXPR rules (optionally in shuffled order)."""
+    from paper_1710_08774_gb300 import hfav as H
+    D = H.DagSpec(ndim)
+    for a in axioms:
+        D.field(a)
+    order = list(range(len(rules)))
+    if shuffle_seed is not None:
+        np.random.default_rng(shuffle_seed).shuffle(order)
+    for k in order:
+        r = rules[k]
+        D.rule("EXPR", [(f, off[:ndim]) for f, off in r["refs"]], [r["out"]], params=r["params"], expr=r["c"])
+    D.axiom(*axioms)
+    D.goal(*goals)
+    return D
+
+
+def to_oracle(rules):
+    """The DAG in the oracle's form: (out, refs, numpy body, params)."""
+    return [(r["out"], r["refs"], r["fn"], r["params"]) for r in rules]
+
+
+def axiom_values(axioms, shape, seed):
+    """Smooth-plus-noise O(1) axiom fields of the given numpy shape (..., j, i)."""
+    rng = np.random.default_rng(seed)
+    grids = np.meshgrid(*[np.arange(n) for n in shape], indexing="ij")
+    vals = {}
+    for k, a in enumerate(axioms):
+        smooth = sum(np.sin(2 * np.pi * (k + 1 + d) * g / n) for d, (g, n) in enumerate(zip(grids, shape)))
+        vals[a] = 0.5 * smooth / len(shape) + 0.5 * rng.uniform(-1, 1, shape)
+    return vals
