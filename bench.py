@@ -78,7 +78,8 @@ def traffic_for(workload, kernel):
     t = TRAFFIC.get((workload, kernel))
     if not t:
         return None
-    files = ["godunov.cu", "godunov_phys.cuh", "common.cuh"] if kernel.startswith("g") else ["chain.cu", "common.cuh"]
+    files = ["godunov.cu", "godunov_phys.cuh", "common.cuh"] if kernel.startswith("g") else \
+        ["codegen.cu", "common.cuh"] if kernel.startswith("codegen") else ["chain.cu", "common.cuh"]
     return t[0] if src_hash(files) == t[1] else None
 
 
@@ -290,13 +291,15 @@ class Cosmo(Workload):
 class Chain(Workload):
     fused_prefix = ("full", "sweep")
 
-    def __init__(self, H, I, torch, dev, dims, n, dtype, seed):
+    def __init__(self, H, I, torch, dev, dims, n, dtype, seed, expr=False):
         self.dims, self.n, self.dtype = dims, n, dtype
         self.name = f"chain{dims}d_{'fp64' if dtype == 'f64' else 'fp32'}_{'x'.join([str(n)] * dims)}"
+        if expr:   # the same chain as user rule bodies, on generated kernels
+            self.name = "codegen_" + self.name
         td = torch.float64 if dtype == "f64" else torch.float32
         if dims == 2:
             u = I.chain2d_input(n, seed=seed)
-            dag, halo = H.chain2d_dag(), 2
+            dag, halo = (H.chain2d_expr_dag() if expr else H.chain2d_dag()), 2
         else:
             import numpy as np
             u = I.chain3d_input(n, seed=seed, dtype=np.float32 if dtype == "f32" else np.float64)
@@ -306,7 +309,7 @@ class Chain(Workload):
         self.dag = dag
         self.hdt = H.HFAV_F64 if dtype == "f64" else H.HFAV_F32
         self.grids = [H.Grid.of(self.u, halo)]
-        self.plan = H.Plan(dag, self.grids, self.hdt, H.HFAV_BC_PERIODIC, "full:reg:32x4")
+        self.plan = H.Plan(dag, self.grids, self.hdt, H.HFAV_BC_PERIODIC, "full:smem:32x8" if expr else "full:reg:32x4")
         self.esize = 8 if dtype == "f64" else 4
 
     def unfused_plan(self, H):
@@ -336,7 +339,7 @@ class Chain(Workload):
 
 
 WORKLOADS = ["godunov1024_f64", "godunov4096_f32", "batch64_f32", "chain2d256_f64", "chain2d16384_f32", "chain3d512_f32",
-             "cosmo1024_f32"]
+             "cosmo1024_f32", "codegen2d16384_f32"]
 
 
 def make(name, H, I, torch, dev):
@@ -359,6 +362,9 @@ def make(name, H, I, torch, dev):
     m = re.fullmatch(r"cosmo(\d+)_(f32|f64)", name)
     if m:
         return Cosmo(H, I, torch, dev, int(m.group(1)), COSMO_NZ, m.group(2))
+    m = re.fullmatch(r"codegen2d(\d+)_(f32|f64)", name)
+    if m:
+        return Chain(H, I, torch, dev, 2, int(m.group(1)), m.group(2), 0, expr=True)
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -386,6 +392,14 @@ def oracle_sample(workload, n=None):
         oracle.chain2d(u)
         dt = time.perf_counter() - t0
         return n * n / dt / 1e9, dt, 0.0, f"{n}x{n} u~U[0,1), single thread"
+    if workload.startswith("codegen"):
+        from oracle import expr as E
+        n = n or 2048
+        u = I.chain2d_input(n, seed=0)[2:-2, 2:-2]
+        t0 = time.perf_counter()
+        E.evaluate(E.chain2d_rules(), {"u": u})
+        dt = time.perf_counter() - t0
+        return n * n / dt / 1e9, dt, 0.0, f"{n}x{n} u~U[0,1), expression oracle (numpy), single thread"
     if workload.startswith("cosmo"):
         n = n or 1024
         u = I.cosmo_input(n, n, 4, seed=7)
@@ -417,6 +431,9 @@ def workload_name(key):
     m = re.fullmatch(r"cosmo(\d+)_(f32|f64)", key)
     if m:
         return f"cosmo_{'fp64' if m.group(2) == 'f64' else 'fp32'}_{m.group(1)}x{m.group(1)}x{COSMO_NZ}"
+    m = re.fullmatch(r"codegen2d(\d+)_(f32|f64)", key)
+    if m:
+        return f"codegen_chain2d_{'fp64' if m.group(2) == 'f64' else 'fp32'}_{m.group(1)}x{m.group(1)}"
     raise SystemExit(f"unknown workload {key}")
 
 
@@ -624,7 +641,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=WORKLOADS[0], help="one of " + ", ".join(WORKLOADS + ["all"]) + ", or chain2d<N>_f32|f64 / chain3d<N>_f32|f64 / cosmo<N>_f32|f64 (other sizes)")
+    ap.add_argument("--workload", default=WORKLOADS[0], help="one of " + ", ".join(WORKLOADS + ["all"]) + ", or chain2d<N>_f32|f64 / chain3d<N>_f32|f64 / cosmo<N>_f32|f64 / codegen2d<N>_f32|f64 (other sizes)")
     ap.add_argument("--schedule", default=None, help="fixed schedule (default: autotuned among fused ones)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--once", action="store_true", help="profiling case: build the plan and run it once")

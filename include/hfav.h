@@ -7,8 +7,8 @@
  * offsets they read, Sec. 1.1 and the YAML listing of Sec. 4), infers the
  * dataflow DAG (Sec. 3.2), fuses the iteration nests (Sec. 3.3, Listings
  * "fuse_inest_dag" / "fuse_inest"), splits at reduction-to-broadcast dataflow
- * (Sec. 3.3.1 "Splits"), sizes every variable by the Minkowski sum of its
- * offsets and contracts intermediates into rolling buffers (Sec. 3.4), and
+ * (Sec. 3.4 "Splits"), sizes every variable by the Minkowski sum of its
+ * offsets and contracts intermediates into rolling buffers (Sec. 3.5), and
  * emits fused loop nests.  This library does the analysis on the host and
  * runs the fused pipelines as hand-written sm_103a kernels that keep the
  * rolling buffers in registers or shared memory.
@@ -90,6 +90,23 @@ typedef enum {
      *   out = u - c ((flx(0) - flx(-1)) + (fly(0) - fly(-1)))                          */
     HFAV_OP_LIMFLUX = 5,
     HFAV_OP_DIFFUSE = 6,
+    /* A user rule body (the paper's rules name arbitrary kernels, Sec. 1.1 and
+     * the rule listing of Sec. 4): rule.expr is a C expression giving the one
+     * output from in0 .. in{n_in-1} (the inputs at their offsets) and
+     * p0 .. p{n_params-1} (the parameters), evaluated in the plan's precision
+     * (type T: double for HFAV_F64, float for HFAV_F32) with the CUDA math
+     * functions (sqrt, fabs, fmin, fmax, exp, ...) and the ?: operator.  The
+     * plan generates, compiles (NVRTC, at the first run on a device) and
+     * caches the kernels.  Rejected at plan creation (HFAV_EINVAL): characters
+     * outside [A-Za-z0-9_ .+-*<>/%()!=&|?:,^~], a single '&', comments, names
+     * in<k> / p<k> beyond the rule's inputs / parameters, and any other name
+     * but T, double, float, int and the math functions sqrt rsqrt cbrt exp
+     * exp2 expm1 log log2 log10 log1p pow sin cos tan asin acos atan atan2
+     * sinh cosh tanh asinh acosh atanh fabs fmin fmax fma floor ceil trunc
+     * round rint copysign fmod hypot erf erfc tgamma lgamma fdim -- so a body
+     * reads nothing but its inputs.  An expression that does not compile fails
+     * the run with HFAV_EINVAL and the compiler log in hfav_last_error(). */
+    HFAV_OP_EXPR = 7,
     /* Hydro2D kernels (Sec. 5.4), directional, ideal gas, params[0] = gamma:
      * CONSTOPRIM in: U0 U1 U2 U3 (rho, rho u, rho v, E) -> rho un ut e
      * EOS        in: rho e                              -> p c
@@ -133,6 +150,9 @@ typedef struct {
     const int* out;          /* field ids written at offset 0 */
     int n_params;
     const double* params;
+    const char* expr;        /* HFAV_OP_EXPR: the rule body (NUL-terminated, at
+                                most 4096 characters, read during plan creation);
+                                NULL for the other ops */
 } hfav_rule;
 
 /* The rule DAG.  Field ranks: ndim for grid fields, 0 for scalars (the result
@@ -159,7 +179,7 @@ typedef struct {
     int halo;
 } hfav_grid;
 
-/* Storage class the planner assigns to a field (Sec. 3.4). */
+/* Storage class the planner assigns to a field (Sec. 3.5). */
 typedef enum {
     HFAV_STORE_AXIOM = 0,    /* caller array in HBM */
     HFAV_STORE_GOAL = 1,     /* caller array in HBM */
@@ -175,12 +195,12 @@ typedef struct {
     int storage;             /* hfav_storage */
     int halo_lo[3];          /* cells needed below the goal region, per axis */
     int halo_hi[3];          /* cells needed above the goal region, per axis */
-    int window[3];           /* span of the field's composed offsets per axis (Sec. 3.4 "Contraction") */
+    int window[3];           /* span of the field's composed offsets per axis (Sec. 3.5 "Contraction") */
     int stage_window[3];     /* span of the direct consumers' offsets per axis */
     int64_t storage_elems;   /* rolling-buffer elements: window along the outermost
                                 axis with span > 1 times the inner interior extents */
     int n_reuse;             /* number of distinct offsets in the reuse order */
-    int reuse[27][3];        /* offsets in order of first to last use (Sec. 3.4 "Grouping") */
+    int reuse[27][3];        /* offsets in order of first to last use (Sec. 3.5 "Grouping") */
 } hfav_field_info;
 
 /* Statistics of the last hfav_run (hfav_status synchronises the plan's stream). */
@@ -199,9 +219,9 @@ typedef struct hfav_plan_s hfav_plan_t;
 
 /*
  * hfav_plan: validate the DAG, order it topologically (Sec. 3.2), infer every
- * field's footprint and halo (Sec. 3.4, Minkowski sum of offsets), fuse the
- * iteration nests and find splits (Sec. 3.3), contract intermediates
- * (Sec. 3.4), map each fusion group onto a kernel pipeline and pick a schedule.
+ * field's footprint and halo (Sec. 3.5, Minkowski sum of offsets), fuse the
+ * iteration nests and find splits (Sec. 3.3, 3.4), contract intermediates
+ * (Sec. 3.5), map each fusion group onto a kernel pipeline and pick a schedule.
  *   dag       : the rule DAG (copied; may be freed after the call).
  *   grids     : n_grids grid descriptions (copied).  Every axiom/goal array of
  *               grid g uses grids[g]'s extents, pitches and halo.
@@ -239,6 +259,14 @@ int hfav_plan_schedule(const hfav_plan_t* plan, char* buf, size_t n);
 /* JSON dump of the analysis: groups, order, per-field footprint, windows, storage. */
 int hfav_plan_dump(const hfav_plan_t* plan, char* buf, size_t n);
 
+/* The CUDA C++ source of the kernels a plan of generated kernels (a DAG
+ * with HFAV_OP_EXPR rules) compiles under its current schedule: the fused
+ * kernel, or one kernel per EXPR rule for 'unfused' -- the emitted code of
+ * the method (Sec. 3.6).  Copies up to n - 1 characters and a NUL into buf;
+ * HFAV_EINVAL (message: the size needed) when buf is too small,
+ * HFAV_EUNSUPPORTED for plans of the builtin kernels.  Needs no device. */
+int hfav_plan_source(const hfav_plan_t* plan, char* buf, size_t n);
+
 /* Features of the plan under a schedule for the learned cost model: writes
  * HFAV_N_FEATURES floats (DAG depth, stencil radius, field count, log cells,
  * dtype, fusion, placement, tile, compulsory bytes, recompute ratio ...). */
@@ -258,7 +286,7 @@ int hfav_plan_features(const hfav_plan_t* plan, const char* schedule, float* fea
  *               step s+1 (the plan ping-pongs through its own scratch so the
  *               axiom arrays are never written and the last step lands in
  *               the goal arrays); without feedback n_steps must be 1.
- * Goals must not alias axioms (declared aliasing, Sec. 3.4 "In/out chaining",
+ * Goals must not alias axioms (declared aliasing, Sec. 3.5 "In/out chaining",
  * is not supported).  The halo cells of goal arrays are left unspecified.
  * Plan-owned scratch (ping-pong state, HBM intermediates of split or unfused
  * schedules, per-grid time-step slots, counters) is allocated on first use and

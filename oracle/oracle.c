@@ -8,7 +8,7 @@
  * What it computes (HFAV, arXiv 1710.08774):
  *   The fused, contracted loop nests HFAV emits reorder side-effect-free,
  *   order-agnostic kernels (Sec. 3.1 "Fundamentals") and elide intermediate
- *   storage (Sec. 3.4 "Variables and storage").  They therefore reach the same
+ *   storage (Sec. 3.5 "Variables and storage").  They therefore reach the same
  *   values as calling every kernel in its own loop nest over fully
  *   materialised arrays, in topological order of the dataflow DAG (Sec. 3.2).
  *   That plain definition is what this file writes out: one loop nest per

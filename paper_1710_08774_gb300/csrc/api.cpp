@@ -68,7 +68,7 @@ int check_grids(hfav_plan_t* p) {
 
 extern "C" {
 
-int hfav_version(void) { return 10000; }
+int hfav_version(void) { return 10100; }
 
 const char* hfav_last_error(void) { return g_err.c_str(); }
 
@@ -113,6 +113,10 @@ int hfav_plan(const hfav_dag* dag, const hfav_grid* grids, int n_grids, int dtyp
         if (!parse_schedule(schedule, &s, &err)) rc = set_error(HFAV_EINVAL, err);
         else if (p->pipeline == PIPE_GENERIC && (!schedule || !strcmp(schedule, "auto"))) {
             s.fusion = FUSE_UNFUSED; s.placement = PLACE_HBM;
+        } else if (p->pipeline == PIPE_CODEGEN && (!schedule || !strcmp(schedule, "auto"))) {
+            // generated kernels: the fused shared-memory tile in 2D, else one kernel per rule
+            if (p->dag.ndim == 2) { s.fusion = FUSE_FULL; s.placement = PLACE_SMEM; s.tx = 32; s.ty = 8; }
+            else { s.fusion = FUSE_UNFUSED; s.placement = PLACE_HBM; }
         }
         if (rc == HFAV_OK && !schedule_valid(p, s, &err)) rc = set_error(HFAV_EUNSUPPORTED, err);
         if (rc == HFAV_OK) p->sched = s;
@@ -164,6 +168,13 @@ int hfav_plan_schedule(const hfav_plan_t* p, char* buf, size_t n) {
 int hfav_plan_dump(const hfav_plan_t* p, char* buf, size_t n) {
     if (!p) return set_error(HFAV_EINVAL, "null plan");
     return copy_out(dump_json(p), buf, n);
+}
+
+int hfav_plan_source(const hfav_plan_t* p, char* buf, size_t n) {
+    if (!p || p->analysis_only) return set_error(HFAV_EINVAL, "not an executable plan");
+    std::string src;
+    int rc = plan_source(p, &src);
+    return rc ? rc : copy_out(src, buf, n);
 }
 
 int hfav_plan_variants(const hfav_plan_t* p, char* buf, size_t n) {

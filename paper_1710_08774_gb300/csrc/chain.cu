@@ -2,7 +2,7 @@
 // (L = 5-pt Laplacian, G = |grad L| / 2, out = G / (1 + G)), the 3D
 // four-stage 7-point chain, and the generic one-kernel-per-rule executor.
 //
-// Fused kernels follow the paper's contraction (Sec. 3.4): one thread per
+// Fused kernels follow the paper's contraction (Sec. 3.5): one thread per
 // column streams along the outer axis (j in 2D, k in 3D) and every
 // intermediate lives in a rolling window of 3 rows / planes instead of a full
 // array.  The window store is the schedule's placement:
@@ -139,6 +139,18 @@ int launch_generic(hfav_plan_t* p, void* const* ax, void* const* go, cudaStream_
         view[f] = a;
         have[f] = 1;
     }
+    // every read stays inside the array it reads: an input's footprint covers
+    // its consumer's region shifted by the offset (axioms of periodic plans wrap)
+    for (const Rule& R : d.rules)
+        for (const hfav_ref& x : R.in) {
+            if (d.rank[x.field] == 0) continue;
+            const hfav_field_info &fo = p->an.field[R.out[0]], &fi = p->an.field[x.field];
+            const bool wraps = p->bc == HFAV_BC_PERIODIC &&
+                               std::find(d.axioms.begin(), d.axioms.end(), x.field) != d.axioms.end();
+            for (int a = 0; a < d.ndim && !wraps; ++a)
+                if (-fo.halo_lo[a] + x.off[a] < -fi.halo_lo[a] || fo.halo_hi[a] + x.off[a] > fi.halo_hi[a])
+                    return set_error(HFAV_EINVAL, "internal: a rule's region leaves its input's footprint");
+        }
     for (int r : p->an.order) {
         const Rule& R = d.rules[r];
         GenericArgs a;
@@ -167,6 +179,13 @@ int launch_generic(hfav_plan_t* p, void* const* ax, void* const* go, cudaStream_
         for (int x = 0; x < 3; ++x) {
             a.lo[x] = -fo.halo_lo[x];
             a.n[x] = (int)g.extent[x] + fo.halo_lo[x] + fo.halo_hi[x];
+        }
+        if (R.op == HFAV_OP_EXPR) {   // a user rule body: a generated kernel
+            std::vector<int> slot(a.ref_arr, a.ref_arr + a.nref);
+            std::vector<GArr> ins(a.arr, a.arr + fields.size());
+            int rc = launch_cg_rule(p, R, slot, ins, a.out, a.lo, a.n, st);
+            if (rc) return rc;
+            continue;
         }
         int64_t total = (int64_t)a.n[0] * a.n[1] * a.n[2];
         int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);

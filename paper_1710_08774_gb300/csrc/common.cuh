@@ -146,6 +146,12 @@ int launch_chain2d(hfav_plan_t* p, const Schedule& s, void* const* ax, void* con
 int launch_cosmo(hfav_plan_t* p, const Schedule& s, void* const* ax, void* const* go, cudaStream_t st);
 int launch_chain3d(hfav_plan_t* p, const Schedule& s, void* const* ax, void* const* go, cudaStream_t st);
 int launch_generic(hfav_plan_t* p, void* const* ax, void* const* go, cudaStream_t st);
+// codegen.cu: generated kernels of DAGs with user rule bodies (HFAV_OP_EXPR)
+int launch_codegen(hfav_plan_t* p, const Schedule& s, void* const* ax, void* const* go, cudaStream_t st);
+// one generated kernel for one rule of the unfused form: ref_slot[r] is the
+// entry of `ins` that input r reads; out is written over lo .. lo + n - 1
+int launch_cg_rule(hfav_plan_t* p, const Rule& R, const std::vector<int>& ref_slot, const std::vector<GArr>& ins,
+                   const GArr& out, const int* lo, const int* n, cudaStream_t st);
 int launch_godunov(hfav_plan_t* p, const Schedule& s, void* const* ax, void* const* go, int n_steps,
                    cudaStream_t st);
 

@@ -104,7 +104,7 @@ __device__ __forceinline__ void cfl_epilogue(double smax, int bad, int nonconv, 
 // x pass, placement reg: one warp per row streams along i in chunks of 32
 // cells with the rolling buffers in registers and neighbours exchanged by
 // warp shuffles -- the GPU form of the paper's vector-widened rotation of an
-// innermost-dimension buffer (Sec. 3.4 "Vectorization").  Chunk v covers
+// innermost-dimension buffer (Sec. 3.5 "Vectorization").  Chunk v covers
 // cells 32 v - 1 + lane.  Step s computes W of chunk s, the trace of chunk
 // s-1 and the faces (right face of each cell) and updates of chunk s-2.
 // Rows with nx % 32 == 0 are exact-periodic: nx faces, nx traces, and one

@@ -16,6 +16,7 @@ struct Rule {
     std::vector<hfav_ref> in;
     std::vector<int> out;
     std::vector<double> params;
+    std::string expr;   // HFAV_OP_EXPR body
 };
 
 struct Dag {
@@ -42,7 +43,7 @@ struct Schedule {
 bool parse_schedule(const char* s, Schedule* out, std::string* err);
 
 // Kernel pipelines the planner can map a fusion group onto.
-enum Pipeline { PIPE_GENERIC = 0, PIPE_CHAIN2D = 1, PIPE_CHAIN3D = 2, PIPE_GODUNOV = 3, PIPE_COSMO = 4 };
+enum Pipeline { PIPE_GENERIC = 0, PIPE_CHAIN2D = 1, PIPE_CHAIN3D = 2, PIPE_GODUNOV = 3, PIPE_COSMO = 4, PIPE_CODEGEN = 5 };
 
 // Field ids of a recognised Godunov DAG (x sweep then y sweep, optional CFL).
 struct GodunovMap {
@@ -61,7 +62,7 @@ struct ChainMap {
 
 struct Runtime;   // device-side state (runtime.cu)
 
-// Analysis results (Sec. 3.2 - 3.4).
+// Analysis results (Sec. 3.2 - 3.5).
 struct Analysis {
     std::vector<int> order;          // topological rule order
     std::vector<int> rule_group;     // fusion group per rule
@@ -100,6 +101,9 @@ void features(const hfav_plan_t* p, const Schedule& s, float* f);
 
 // errors.cpp-style helpers (api.cpp)
 int set_error(int code, const std::string& msg);
+
+// codegen.cu: the CUDA source a plan of generated kernels compiles
+int plan_source(const hfav_plan_t* p, std::string* out);
 
 // runtime.cu
 int run(hfav_plan_t* p, void* const* ax, void* const* go, int n_steps, void* stream, bool graph);

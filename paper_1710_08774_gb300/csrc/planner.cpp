@@ -11,9 +11,9 @@
 //      rank-ordering and dataflow-ordering rules (Sec. 3.3, Listings
 //      "fuse_inest_dag" and "fuse_inest"); an unfusable pair is a split;
 //   5. variable analysis: footprint by the Minkowski sum of offsets
-//      (Sec. 3.4, footnote), enclosing region (which fields cross nests),
-//      reuse order (Sec. 3.4 "Grouping"), contraction to rolling buffers
-//      (Sec. 3.4 "Contraction");
+//      (Sec. 3.5, footnote), enclosing region (which fields cross nests),
+//      reuse order (Sec. 3.5 "Grouping"), contraction to rolling buffers
+//      (Sec. 3.5 "Contraction");
 //   6. instead of emitting C, the fusion groups are matched against the
 //      hand-written GPU pipelines (recognise()).
 #include <algorithm>
@@ -22,6 +22,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <cctype>
 #include <set>
 #include <sstream>
 
@@ -34,13 +35,71 @@ namespace {
 bool op_known(int op) {
     switch (op) {
         case HFAV_OP_STENCIL_LINEAR: case HFAV_OP_GRADMAG_HALF: case HFAV_OP_SQUASH:
-        case HFAV_OP_GENERIC: case HFAV_OP_LIMFLUX: case HFAV_OP_DIFFUSE: case HFAV_OP_CONSTOPRIM: case HFAV_OP_EOS: case HFAV_OP_SLOPE:
+        case HFAV_OP_GENERIC: case HFAV_OP_LIMFLUX: case HFAV_OP_DIFFUSE: case HFAV_OP_EXPR: case HFAV_OP_CONSTOPRIM: case HFAV_OP_EOS: case HFAV_OP_SLOPE:
         case HFAV_OP_TRACE: case HFAV_OP_QLEFTRIGHT: case HFAV_OP_RIEMANN: case HFAV_OP_CMPFLX:
         case HFAV_OP_UPDATE: case HFAV_OP_CFL_DT: case HFAV_OP_REDUCE_SUM: case HFAV_OP_BROADCAST:
             return true;
         default:
             return false;
     }
+}
+
+// the names a rule body may use besides in<k> / p<k>: the value type, casts
+// and the CUDA math functions
+bool allowed_name(const std::string& id) {
+    static const std::set<std::string> names = {
+        "T", "double", "float", "int", "sqrt", "rsqrt", "cbrt", "exp", "exp2", "expm1", "log", "log2",
+        "log10", "log1p", "pow", "sin", "cos", "tan", "asin", "acos", "atan", "atan2", "sinh", "cosh",
+        "tanh", "asinh", "acosh", "atanh", "fabs", "fmin", "fmax", "fma", "floor", "ceil", "trunc", "round",
+        "rint", "copysign", "fmod", "hypot", "erf", "erfc", "tgamma", "lgamma", "fdim"};
+    return names.count(id) != 0;
+}
+
+// A user rule body may only be an arithmetic expression: no statements,
+// blocks, preprocessor lines, strings, comments, subscripts or addresses (no
+// ';', '{', '#', quotes, '[', single '&'), and every name is one of the
+// rule's inputs in<k> / parameters p<k> or an allowed type or math function
+// -- so a body reads nothing but its inputs.
+std::string check_expr(const char* e, int n_in, int n_params) {
+    if (!e) return "an EXPR rule needs an expression";
+    const size_t n = std::strlen(e);
+    if (n == 0 || n > 4096) return "the expression must have 1 to 4096 characters";
+    static const char ok[] = "_ .+-*<>/%()!=&|?:,^~";
+    for (size_t k = 0; k < n; ++k) {
+        const char c = e[k];
+        if (!std::isalnum((unsigned char)c) && !std::strchr(ok, c) ) return std::string("character '") + c + "' is not allowed";
+    }
+    if (std::strstr(e, "/*") || std::strstr(e, "//")) return "comments are not allowed";
+    for (size_t k = 0; k < n; ++k)   // no address-of (the only way to form a pointer)
+        if (e[k] == '&') {
+            if (k + 1 < n && e[k + 1] == '&') { ++k; continue; }
+            return "'&' is only allowed as '&&'";
+        }
+    for (size_t k = 0; k < n;) {
+        if (std::isalpha((unsigned char)e[k]) || e[k] == '_') {
+            size_t b = k;
+            while (k < n && (std::isalnum((unsigned char)e[k]) || e[k] == '_')) ++k;
+            const std::string id(e + b, k - b);
+            auto index_of = [&](const char* pre) -> long {
+                const size_t m = std::strlen(pre);
+                if (id.size() <= m || id.compare(0, m, pre) != 0) return -1;
+                for (size_t q = m; q < id.size(); ++q)
+                    if (!std::isdigit((unsigned char)id[q])) return -1;
+                return id.size() - m > 6 ? 1000000 : std::stol(id.substr(m));
+            };
+            long a = index_of("in"), b2 = index_of("p");
+            if (a >= n_in) return "'" + id + "' names an input the rule does not have";
+            if (b2 >= n_params) return "'" + id + "' names a parameter the rule does not have";
+            if (a < 0 && b2 < 0 && !allowed_name(id)) return "'" + id + "' is not an input, a parameter or a math function";
+        } else if (std::isdigit((unsigned char)e[k]) || e[k] == '.') {
+            while (k < n && (std::isalnum((unsigned char)e[k]) || e[k] == '.' ||
+                             ((e[k] == '+' || e[k] == '-') && (e[k - 1] == 'e' || e[k - 1] == 'E'))))
+                ++k;
+        } else {
+            ++k;
+        }
+    }
+    return "";
 }
 
 // A rule is a reduction when it writes only rank-0 fields from higher-rank inputs.
@@ -157,6 +216,12 @@ int copy_dag(const hfav_dag* in, Dag* d) {
             r.out.push_back(s.out[k]);
         }
         r.params.assign(s.params, s.params + s.n_params);
+        if (s.op == HFAV_OP_EXPR) {
+            const std::string why = check_expr(s.expr, s.n_in, s.n_params);
+            if (!why.empty()) return set_error(HFAV_EINVAL, "rule " + std::to_string(i) + ": " + why);
+            if (s.n_out != 1) return set_error(HFAV_EINVAL, "rule " + std::to_string(i) + ": an EXPR rule has one output");
+            r.expr = s.expr;
+        }
         d->rules.push_back(r);
     }
     if (in->n_axioms < 0 || in->n_goals < 1 || (in->n_axioms > 0 && !in->axioms) || !in->goals)
@@ -407,6 +472,10 @@ int analyze(hfav_plan_t* p, const int64_t* extent_in) {
                     for (int a = 0; a < 3; ++a) { rlo[a] = std::min(rlo[a], lo[f][a]); rhi[a] = std::max(rhi[a], hi[f][a]); }
                 }
         if (!any) { rlo = {0, 0, 0}; rhi = {0, 0, 0}; }
+        // a rule runs over its outputs' footprint, which always holds the
+        // interior (the reported halos are >= 0): its inputs must cover that
+        // whole region, not only the part the consumers read
+        for (int a = 0; a < d.ndim; ++a) { rlo[a] = std::min(rlo[a], 0); rhi[a] = std::max(rhi[a], 0); }
         for (auto& x : R.in) {
             if (d.rank[x.field] == 0) continue;
             set[x.field] = 1;
@@ -417,7 +486,7 @@ int analyze(hfav_plan_t* p, const int64_t* extent_in) {
         }
     }
 
-    // --- 5b. composed offsets per group (Sec. 3.4 Grouping / Contraction) ---
+    // --- 5b. composed offsets per group (Sec. 3.5 Grouping / Contraction) ---
     // Within a fusion group, a field's references in one steady-state trip are
     // the offsets of its consumers composed back from the group's outputs.
     using Off = std::array<int, 3>;
@@ -770,11 +839,19 @@ int recognise(hfav_plan_t* p) {
     if (recognise_chain(p)) return HFAV_OK;
     if (recognise_godunov(p)) return HFAV_OK;
     if (recognise_cosmo(p)) return HFAV_OK;
-    // generic DAGs of the stencil catalogue run unfused, one kernel per rule
-    for (auto& r : p->dag.rules)
+    // generic DAGs of the stencil catalogue run unfused, one kernel per rule;
+    // DAGs with user rule bodies get generated kernels
+    bool expr = false;
+    for (auto& r : p->dag.rules) {
+        if (r.op == HFAV_OP_EXPR) { expr = true; continue; }
         if (r.op != HFAV_OP_STENCIL_LINEAR && r.op != HFAV_OP_GRADMAG_HALF && r.op != HFAV_OP_SQUASH &&
             r.op != HFAV_OP_LIMFLUX && r.op != HFAV_OP_DIFFUSE)
             return HFAV_EUNSUPPORTED;
+        if (r.out.size() != 1) return HFAV_EUNSUPPORTED;
+    }
+    for (int rk : p->dag.rank)
+        if (rk != p->dag.ndim) return expr ? HFAV_EUNSUPPORTED : HFAV_OK;
+    if (expr) p->pipeline = PIPE_CODEGEN;
     return HFAV_OK;
 }
 
@@ -789,6 +866,11 @@ bool schedule_valid(const hfav_plan_t* p, const Schedule& s, std::string* why) {
     }
     if (s.fusion == FUSE_UNFUSED && s.placement != PLACE_HBM) {
         if (why) *why = "unfused implies hbm intermediates";
+        return false;
+    }
+    if (p->pipeline == PIPE_CODEGEN && s.fusion != FUSE_UNFUSED &&
+        (s.fusion != FUSE_FULL || s.placement != PLACE_SMEM || p->dag.ndim != 2)) {
+        if (why) *why = "generated kernels run fully fused with shared-memory tiles (full:smem, 2D DAGs) or unfused";
         return false;
     }
     if (p->pipeline == PIPE_COSMO && s.fusion != FUSE_UNFUSED && (s.fusion != FUSE_FULL || s.placement != PLACE_REG)) {
@@ -813,7 +895,7 @@ std::vector<Schedule> valid_schedules(const hfav_plan_t* p) {
 
 std::string dump_json(const hfav_plan_t* p) {
     static const char* sto[] = {"axiom", "goal", "hbm", "rolling", "scalar"};
-    static const char* pipes[] = {"generic", "chain2d", "chain3d", "godunov", "cosmo"};
+    static const char* pipes[] = {"generic", "chain2d", "chain3d", "godunov", "cosmo", "codegen"};
     const Analysis& A = p->an;
     std::ostringstream o;
     o << "{\"pipeline\":\"" << pipes[p->pipeline] << "\",\"schedule\":\"" << p->sched.str()

@@ -34,6 +34,7 @@ int launch_once(hfav_plan_t* p, const Schedule& s, void* const* ax, void* const*
         case PIPE_CHAIN3D: return launch_chain3d(p, s, ax, go, st);
         case PIPE_GODUNOV: return launch_godunov(p, s, ax, go, n_steps, st);
         case PIPE_COSMO: return launch_cosmo(p, s, ax, go, st);
+        case PIPE_CODEGEN: return launch_codegen(p, s, ax, go, st);
         default: return launch_generic(p, ax, go, st);
     }
 }

@@ -22,14 +22,14 @@ ERRORS = {-1: "EINVAL", -2: "ECYCLE", -3: "EPRODUCER", -4: "EMISSING", -5: "EHAL
           -7: "ENOMEM", -8: "ECUDA", -9: "ETIMEOUT", -10: "ENONPHYSICAL", -11: "EUNSUPPORTED"}
 HFAV_F64, HFAV_F32 = 0, 1
 HFAV_BC_PERIODIC, HFAV_BC_HALO_GIVEN = 0, 1
-OP = dict(STENCIL_LINEAR=1, GRADMAG_HALF=2, SQUASH=3, GENERIC=4, LIMFLUX=5, DIFFUSE=6, CONSTOPRIM=10, EOS=11, SLOPE=12, TRACE=13,
+OP = dict(STENCIL_LINEAR=1, GRADMAG_HALF=2, SQUASH=3, GENERIC=4, LIMFLUX=5, DIFFUSE=6, EXPR=7, CONSTOPRIM=10, EOS=11, SLOPE=12, TRACE=13,
           QLEFTRIGHT=14, RIEMANN=15, CMPFLX=16, UPDATE=17, CFL_DT=20, REDUCE_SUM=21, BROADCAST=22)
 STORAGE = ["axiom", "goal", "hbm", "rolling", "scalar"]
 N_FEATURES = 16
 
 # every symbol include/hfav.h declares
 SYMBOLS = ["hfav_plan", "hfav_analyze", "hfav_plan_groups", "hfav_plan_field", "hfav_plan_order",
-           "hfav_plan_set_schedule", "hfav_plan_schedule", "hfav_plan_dump", "hfav_plan_features", "hfav_run",
+           "hfav_plan_set_schedule", "hfav_plan_schedule", "hfav_plan_dump", "hfav_plan_source", "hfav_plan_features", "hfav_run",
            "hfav_run_graph", "hfav_status", "hfav_autotune", "hfav_plan_variants", "hfav_free", "hfav_last_error",
            "hfav_version", "hfav_mlp_n_params", "hfav_mlp_forward", "hfav_mlp_work_floats", "hfav_mlp_loss_grad",
            "hfav_mlp_adam", "hfav_mlp_train", "hfav_model_choose", "hfav_plan_timing", "hfav_kernel_times",
@@ -49,7 +49,7 @@ class Ref(ctypes.Structure):
 class Rule(ctypes.Structure):
     _fields_ = [("op", ctypes.c_int), ("axis", ctypes.c_int), ("n_in", ctypes.c_int), ("in_", ctypes.POINTER(Ref)),
                 ("n_out", ctypes.c_int), ("out", ctypes.POINTER(ctypes.c_int)), ("n_params", ctypes.c_int),
-                ("params", ctypes.POINTER(ctypes.c_double))]
+                ("params", ctypes.POINTER(ctypes.c_double)), ("expr", ctypes.c_char_p)]
 
 
 class Dag(ctypes.Structure):
@@ -124,6 +124,7 @@ def load(path=None):
         "hfav_plan_set_schedule": ([P, ctypes.c_char_p], ctypes.c_int),
         "hfav_plan_schedule": ([P, ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
         "hfav_plan_dump": ([P, ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
+        "hfav_plan_source": ([P, ctypes.c_char_p, ctypes.c_size_t], ctypes.c_int),
         "hfav_plan_features": ([P, ctypes.c_char_p, fp], ctypes.c_int),
         "hfav_run": ([P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_int, P], ctypes.c_int),
         "hfav_run_graph": ([P, ctypes.POINTER(P), ctypes.POINTER(P), ctypes.c_int, P], ctypes.c_int),
@@ -186,14 +187,15 @@ class DagSpec:
             self.rank.append(self.ndim if rank is None else rank)
         return self.names.index(name)
 
-    def rule(self, op, ins, outs, params=(), axis=0):
+    def rule(self, op, ins, outs, params=(), axis=0, expr=None):
+        """A rule; `expr` is the C body of an EXPR rule (over in0 .., p0 ..)."""
         refs = []
         for r in ins:
             name, off = (r, (0, 0, 0)) if isinstance(r, str) else r
             off = tuple(off) + (0,) * (3 - len(off))
             refs.append((self.field(name), off))
         out = [self.field(o) for o in outs]
-        self.rules.append((OP[op] if isinstance(op, str) else op, axis, refs, out, list(params)))
+        self.rules.append((OP[op] if isinstance(op, str) else op, axis, refs, out, list(params), expr))
         return len(self.rules) - 1
 
     def axiom(self, *names):
@@ -206,7 +208,7 @@ class DagSpec:
         """The hfav_dag struct (kept alive by this object)."""
         keep = []
         rules = (Rule * len(self.rules))()
-        for k, (op, axis, refs, out, params) in enumerate(self.rules):
+        for k, (op, axis, refs, out, params, expr) in enumerate(self.rules):
             R = rules[k]
             R.op, R.axis = op, axis
             ra = (Ref * max(1, len(refs)))()
@@ -220,6 +222,10 @@ class DagSpec:
             R.n_in, R.in_ = len(refs), ra
             R.n_out, R.out = len(out), oa
             R.n_params, R.params = len(params), pa
+            if expr is not None:
+                eb = ctypes.create_string_buffer(expr.encode())
+                keep.append(eb)
+                R.expr = ctypes.cast(eb, ctypes.c_char_p)
         d = Dag()
         rk = (ctypes.c_int * len(self.rank))(*self.rank)
         ax = (ctypes.c_int * max(1, len(self.axioms)))(*self.axioms)
@@ -248,6 +254,20 @@ def chain2d_dag():
            params=[1, 1, 1, 1, -4])
     D.rule("GRADMAG_HALF", [("L", (1, 0)), ("L", (-1, 0)), ("L", (0, 1)), ("L", (0, -1))], ["G"])
     D.rule("SQUASH", ["G"], ["out"])
+    D.axiom("u")
+    D.goal("out")
+    return D
+
+
+def chain2d_expr_dag():
+    """The 2D chain of chain2d_dag written as user rule bodies (EXPR): runs on
+    kernels generated and compiled at run time instead of the builtin ones."""
+    D = DagSpec(2, stream_axis=1)
+    D.rule("EXPR", [("u", (1, 0)), ("u", (-1, 0)), ("u", (0, 1)), ("u", (0, -1)), ("u", (0, 0))], ["L"],
+           params=[4.0], expr="in0 + in1 + in2 + in3 - p0 * in4")
+    D.rule("EXPR", [("L", (1, 0)), ("L", (-1, 0)), ("L", (0, 1)), ("L", (0, -1))], ["G"],
+           expr="sqrt((in0 - in1) * (in0 - in1) + (in2 - in3) * (in2 - in3)) * (T)0.5")
+    D.rule("EXPR", ["G"], ["out"], expr="in0 / (1 + in0)")
     D.axiom("u")
     D.goal("out")
     return D
@@ -399,6 +419,12 @@ class Plan:
         buf = ctypes.create_string_buffer(1 << 20)
         check(load().hfav_plan_dump(self.h, buf, len(buf)))
         return json.loads(buf.value.decode())
+
+    def source(self):
+        """CUDA source of the plan's generated kernels (DAGs with EXPR rules)."""
+        buf = ctypes.create_string_buffer(1 << 22)
+        check(load().hfav_plan_source(self.h, buf, len(buf)))
+        return buf.value.decode()
 
     # -- schedule -------------------------------------------------------------
     @property

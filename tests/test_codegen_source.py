@@ -1,0 +1,119 @@
+"""Runtime code generation on the host (no GPU): DAGs with user rule bodies
+(HFAV_OP_EXPR) plan onto generated kernels, bad bodies are refused at plan
+creation, and the CUDA source the plan emits compiles with NVRTC for sm_103a
+in both precisions under every schedule."""
+import ctypes
+import os
+
+import numpy as np
+import pytest
+
+from paper_1710_08774_gb300 import hfav as H
+from tests import expr_dags as X
+
+
+def _grid(shape, halo):
+    return H.Grid.of(np.zeros(tuple(n + 2 * halo for n in shape)), halo)
+
+
+def _nvrtc():
+    for name in ("libnvrtc.so.13", "/usr/local/cuda/lib64/libnvrtc.so.13", "libnvrtc.so"):
+        try:
+            return ctypes.CDLL(name)
+        except OSError:
+            pass
+    pytest.skip("libnvrtc not available")
+
+
+def _compile(L, src):
+    prog = ctypes.c_void_p()
+    assert L.nvrtcCreateProgram(ctypes.byref(prog), src.encode(), b"generated.cu", 0, None, None) == 0
+    opts = (ctypes.c_char_p * 2)(b"--gpu-architecture=sm_103a", b"--std=c++17")
+    rc = L.nvrtcCompileProgram(prog, 2, opts)
+    n = ctypes.c_size_t()
+    L.nvrtcGetProgramLogSize(prog, ctypes.byref(n))
+    log = ctypes.create_string_buffer(max(1, n.value))
+    L.nvrtcGetProgramLog(prog, log)
+    L.nvrtcDestroyProgram(ctypes.byref(prog))
+    return rc, log.value.decode(errors="replace")
+
+
+def test_expr_dag_plans_onto_generated_kernels():
+    rules, axioms, goals = X.random_dag(2, 5, 0)
+    P = H.Plan(X.to_spec(rules, axioms, goals, 2), [_grid((40, 30), 6)])
+    assert P.dump()["pipeline"] == "codegen"
+    assert P.schedule == "full:smem:32x8"          # the default in 2D
+    assert set(P.variants()) == {f"{f}:{t}" for f in ("full:smem", "unfused:hbm")
+                                 for t in ("32x4", "64x4", "128x2", "32x8")}
+    with pytest.raises(H.HfavError):
+        P.schedule = "full:reg:32x4"
+    rules3, ax3, go3 = X.random_dag(3, 3, 1)
+    P3 = H.Plan(X.to_spec(rules3, ax3, go3, 3), [_grid((12, 10, 8), 4)])
+    assert P3.schedule.startswith("unfused")      # 3D: one generated kernel per rule
+    assert P3.variants() == [f"unfused:hbm:{t}" for t in ("32x4", "64x4", "128x2", "32x8")]
+
+
+BAD = [("in0; in1", "character ';'"), ("in2", "input"), ("p1", "parameter"), ("in0 // x", "comments"),
+       ("#define X", "character '#'"), ("hfav_wrap(in0, 1)", "math function"), ("in0 + 'a'", "character"),
+       ("", "1 to 4096"), ("x" * 5000, "1 to 4096"), ("in0 {", "character '{'"), ("*(&in0 + 9)", "'&'"),
+       ("__trap()", "math function"), ("threadIdx.x", "math function"), ("in0[3]", "character '['"),
+       ("printf(in0)", "math function"), ("asm(in0)", "math function")]
+
+
+@pytest.mark.parametrize("body,why", BAD)
+def test_bad_bodies_refused_at_plan_creation(body, why):
+    D = H.DagSpec(2)
+    D.rule("EXPR", [("u", (0, 0)), ("u", (1, 0))], ["o"], params=[1.0], expr=body)
+    D.axiom("u"); D.goal("o")
+    with pytest.raises(H.HfavError) as e:
+        H.analyze(D)
+    assert e.value.args and "EINVAL" in str(e.value) and why in str(e.value)
+
+
+def test_good_bodies_accepted():
+    for body in ("in0 + 1.5e-3 * p0", "fmax(in0, in1) > 0 && in1 < 2 ? (T)1 : (float)0.5f", "-in0 % 1 == 0 ? 1 : 2",
+                 "pow(fabs(in0), 1.5) + hypot(in0, in1) + atan2(in1, 1 + in0 * in0)"):
+        D = H.DagSpec(2)
+        D.rule("EXPR", [("u", (0, 0)), ("u", (1, 0))], ["o"], params=[1.0], expr=body)
+        D.axiom("u"); D.goal("o")
+        H.analyze(D)
+
+
+def test_builtin_plans_have_no_source():
+    P = H.Plan(H.chain2d_dag(), [_grid((64, 64), 2)])
+    with pytest.raises(H.HfavError):
+        P.source()
+
+
+@pytest.mark.parametrize("dtype", [H.HFAV_F64, H.HFAV_F32])
+@pytest.mark.parametrize("seed", range(4))
+def test_generated_source_compiles_with_nvrtc(dtype, seed):
+    L = _nvrtc()
+    rules, axioms, goals = X.random_dag(2, 6, seed)
+    P = H.Plan(X.to_spec(rules, axioms, goals, 2), [_grid((50, 40), 8)], dtype)
+    for sched in ("full:smem:32x4", "full:smem:128x2", "unfused:hbm:32x4"):
+        P.schedule = sched
+        src = P.source()
+        for body in {r["c"] for r in rules}:
+            assert body in src
+        units = src.split("// ---- rule ")[1:] if sched.startswith("unfused") else [src]
+        assert units
+        for u in units:
+            u = u.split("\n", 1)[1] if sched.startswith("unfused") else u
+            rc, log = _compile(L, u)
+            assert rc == 0, log
+
+
+def test_source_is_deterministic_and_mixes_catalogue_ops():
+    D = H.DagSpec(2)
+    D.rule("STENCIL_LINEAR", [("u", (1, 0)), ("u", (-1, 0)), ("u", (0, 1)), ("u", (0, -1)), ("u", (0, 0))], ["L"],
+           params=[1, 1, 1, 1, -4])
+    D.rule("EXPR", [("L", (1, 0)), ("L", (0, 0))], ["d"], params=[0.5], expr="p0 * (in0 - in1)")
+    D.rule("SQUASH", ["d"], ["o"])
+    D.axiom("u"); D.goal("o")
+    a = H.Plan(D, [_grid((64, 64), 2)]).source()
+    b = H.Plan(D, [_grid((64, 64), 2)]).source()
+    assert a == b and "hfav_cg_fused" in a
+    L = _nvrtc()
+    rc, log = _compile(L, a)
+    assert rc == 0, log

@@ -1,8 +1,8 @@
 """Host planner (C ABI, no GPU) pinned by the structural facts the paper prints.
 
-- 1D 3-point Laplace: storage of u contracts to 3 values (Sec. 3.4 "Contraction").
+- 1D 3-point Laplace: storage of u contracts to 3 values (Sec. 3.5 "Contraction").
 - 2D 5-point Laplace in (j, i) order: reuse spans 3 rows, first use at
-  (i, j+1), then (i+1, j), (i, j), (i-1, j), (i, j-1) (Sec. 3.4 "Grouping").
+  (i, j+1), then (i+1, j), (i, j), (i-1, j), (i, j-1) (Sec. 3.5 "Grouping").
 - COSMO diffusion (Sec. 5.3): one nest, rolling buffers of 3 (Laplacians) and
   2 (fluxes); intermediate storage 5 Ni + 2 beside the two full arrays.
 - Hydro2D (Sec. 5.4): the nine kernels of a pass fuse into one nest, rolling
