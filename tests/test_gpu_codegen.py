@@ -50,7 +50,7 @@ def test_chain_as_rule_bodies_f64(schedule):
     assert normwise(got, oracle.chain2d(u)[2]) <= 1e-12
 
 
-@pytest.mark.parametrize("shape", [(13, 7), (100, 37), (130, 67), (1, 1), (257, 3)])
+@pytest.mark.parametrize("shape", [(13, 7), (100, 37), (130, 67), (2, 2), (257, 3)])
 @pytest.mark.parametrize("schedule", ["full:smem:32x4", "full:smem:128x2", "unfused:hbm:32x4"])
 def test_chain_as_rule_bodies_ragged(shape, schedule):
     nx, ny = shape
