@@ -394,7 +394,7 @@ def oracle_sample(workload, n=None):
         return n * n / dt / 1e9, dt, 0.0, f"{n}x{n} u~U[0,1), single thread"
     if workload.startswith("codegen"):
         from oracle import expr as E
-        n = n or 2048
+        n = n or 8192
         u = I.chain2d_input(n, seed=0)[2:-2, 2:-2]
         t0 = time.perf_counter()
         E.evaluate(E.chain2d_rules(), {"u": u})

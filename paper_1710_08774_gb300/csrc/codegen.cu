@@ -28,6 +28,7 @@
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <mutex>
 #include <sstream>
@@ -134,7 +135,11 @@ std::string lit(double v) {
 }
 
 const char* kPrelude = R"(
-__device__ __forceinline__ int hfav_wrap(int a, int n) { int r = a % n; return r < 0 ? r + n : r; }
+__device__ __forceinline__ int hfav_wrap(int a, int n) {
+    if ((unsigned)a < (unsigned)n) return a;
+    const int r = a % n;
+    return r < 0 ? r + n : r;
+}
 __device__ __forceinline__ T hfav_limflux(T u0, T u1, T l0, T l1) {
     const T f = l1 - l0;
     return f * (u1 - u0) > (T)0 ? (T)0 : f;
@@ -288,6 +293,8 @@ struct Fused {
     int TX = 0, TY = 0, NT = 0;
     size_t smem = 0;
     std::vector<Tile> tile;
+    std::vector<char> inl;      // computed inside its readers, never stored
+    std::vector<int> direct;    // goal slot written straight from its rule, else -1
 };
 
 int fused_geometry(const hfav_plan_t* p, const Schedule& s, Fused* G) {
@@ -296,19 +303,53 @@ int fused_geometry(const hfav_plan_t* p, const Schedule& s, Fused* G) {
     G->TX = s.tx;
     G->NT = s.tx * s.ty;
     G->tile.assign(d.n_fields, Tile());
+    std::vector<int> readers(d.n_fields, 0), producer(d.n_fields, -1), goal_slot(d.n_fields, -1);
+    std::vector<char> off0(d.n_fields, 1);
+    for (size_t r = 0; r < d.rules.size(); ++r) {
+        producer[d.rules[r].out[0]] = (int)r;
+        for (const hfav_ref& x : d.rules[r].in) {
+            readers[x.field]++;
+            if (x.off[0] || x.off[1] || x.off[2]) off0[x.field] = 0;
+        }
+    }
+    for (size_t a = 0; a < d.goals.size(); ++a) goal_slot[d.goals[a]] = (int)a;
+    auto same = [](const Tile& x, const Tile& y) { return x.hx == y.hx && x.hy == y.hy && x.w == y.w && x.h == y.h; };
     for (int rows = 8; rows >= 1; rows /= 2) {
         G->TY = s.ty * rows;
-        G->smem = 0;
         for (int f = 0; f < d.n_fields; ++f) {
-            // shared tile of field f over its footprint: [-halo_lo, T + halo_hi) per axis
+            // tile of field f over its footprint: [-halo_lo, T + halo_hi) per axis
             const hfav_field_info& fi = p->an.field[f];
             Tile t;
             t.hx = fi.halo_lo[0]; t.hy = fi.halo_lo[1];
             t.w = G->TX + fi.halo_lo[0] + fi.halo_hi[0];
             t.h = G->TY + fi.halo_lo[1] + fi.halo_hi[1];
-            t.off = G->smem;
-            G->smem += ((size_t)t.w * t.h * es + 15) / 16 * 16;
+            t.off = 0;
             G->tile[f] = t;
+        }
+        // a rule output that every reader takes at offset 0 over the same tile
+        // is evaluated inside the readers (a pointwise stage fused into its
+        // consumer); a goal that nothing reads, over exactly the tile, is
+        // written from its rule to the caller's array
+        G->inl.assign(d.n_fields, 0);
+        G->direct.assign(d.n_fields, -1);
+        for (int f = 0; f < d.n_fields; ++f) {
+            const bool produced = producer[f] >= 0 && goal_slot[f] < 0;
+            if (produced && readers[f] > 0 && off0[f]) {
+                bool ok = true;
+                for (const Rule& R : d.rules)
+                    for (const hfav_ref& x : R.in)
+                        if (x.field == f && !same(G->tile[R.out[0]], G->tile[f])) ok = false;
+                G->inl[f] = ok;
+            }
+            const Tile& t = G->tile[f];
+            if (goal_slot[f] >= 0 && producer[f] >= 0 && readers[f] == 0 && t.w == G->TX && t.h == G->TY)
+                G->direct[f] = goal_slot[f];
+        }
+        G->smem = 0;
+        for (int f = 0; f < d.n_fields; ++f) {
+            if (G->inl[f] || G->direct[f] >= 0) continue;
+            G->tile[f].off = G->smem;
+            G->smem += ((size_t)G->tile[f].w * G->tile[f].h * es + 15) / 16 * 16;
         }
         if (G->smem <= 96 * 1024) break;
     }
@@ -336,6 +377,34 @@ int fused_geometry(const hfav_plan_t* p, const Schedule& s, Fused* G) {
 std::string fused_source(const hfav_plan_t* p, const Fused& G) {
     const Dag& d = p->dag;
     const int TX = G.TX, TY = G.TY, NT = G.NT;
+    // a loop over the w x h cells of a tile, NT threads, unrolled (its trip
+    // count is a constant): cell (a, b) of the tile, q = b * w + a
+    auto tile_loop = [&](std::ostringstream& c, int w, int h) {
+        const int n = w * h, trips = (n + NT - 1) / NT;
+        c << "    #pragma unroll\n"
+          << "    for (int it = 0; it < " << trips << "; ++it) {\n"
+          << "        const int q = tid + it * " << NT << ";\n"
+          << "        if (" << (n % NT ? "q < " + std::to_string(n) : std::string("true")) << ") {\n"
+          << "        const int a = q % " << w << ", b = q / " << w << ";\n";
+    };
+    auto direct = [&](int f) { return G.direct[f] >= 0; };
+    std::vector<int> producer(d.n_fields, -1);
+    for (size_t r = 0; r < d.rules.size(); ++r) producer[d.rules[r].out[0]] = (int)r;
+    // the value of field f at the cell (a, b) of tile t shifted by (ox, oy):
+    // from f's shared tile, or, for an inlined field, its rule's body on its
+    // own inputs at the same cell
+    std::function<std::string(int, const Tile&, int, int)> read = [&](int f, const Tile& t, int ox, int oy) {
+        if (G.inl[f]) {
+            const Rule& R = d.rules[producer[f]];
+            std::string v = "hfav_body" + std::to_string(producer[f]) + "(";
+            for (size_t k = 0; k < R.in.size(); ++k)
+                v += (k ? ", " : "") + read(R.in[k].field, t, R.in[k].off[0], R.in[k].off[1]);
+            return v + ")";
+        }
+        const Tile& u = G.tile[f];
+        return "s" + std::to_string(f) + "[(b + " + std::to_string(u.hy - t.hy + oy) + ") * " + std::to_string(u.w) +
+               " + (a + " + std::to_string(u.hx - t.hx + ox) + ")]";
+    };
     std::ostringstream c;
     c << prelude(p->dtype == HFAV_F64);
     for (int r : p->an.order) c << rule_fn(d.rules[r], "hfav_body" + std::to_string(r));
@@ -345,49 +414,54 @@ std::string fused_source(const hfav_plan_t* p, const Fused& G) {
     c << "int nx, int ny) {\n"
       << "    extern __shared__ __align__(16) unsigned char smem[];\n"
       << "    const int tid = threadIdx.x, i0 = blockIdx.x * " << TX << ", j0 = blockIdx.y * " << TY << ";\n";
-    for (int f = 0; f < d.n_fields; ++f) c << "    T* s" << f << " = (T*)(smem + " << G.tile[f].off << ");\n";
+    for (int f = 0; f < d.n_fields; ++f)
+        if (!direct(f) && !G.inl[f]) c << "    T* s" << f << " = (T*)(smem + " << G.tile[f].off << ");\n";
     // axioms: the footprint, wrapped (periodic) or from the caller's halo
     for (size_t a = 0; a < d.axioms.size(); ++a) {
         const int f = d.axioms[a];
         const Tile& t = G.tile[f];
         const std::string x = "x" + std::to_string(a);
-        c << "    for (int q = tid; q < " << t.w * t.h << "; q += " << NT << ") {\n"
-          << "        const int a = q % " << t.w << ", b = q / " << t.w << ";\n"
-          << "        int gi = i0 - " << t.hx << " + a, gj = j0 - " << t.hy << " + b;\n"
+        tile_loop(c, t.w, t.h);
+        c << "        int gi = i0 - " << t.hx << " + a, gj = j0 - " << t.hy << " + b;\n"
           << "        if (" << x << "_w) { gi = hfav_wrap(gi, nx); gj = hfav_wrap(gj, ny); }\n"
           << "        else { gi = min(max(gi, -" << x << "_o0), nx - 1 + " << x << "_o0); gj = min(max(gj, -" << x
           << "_o1), ny - 1 + " << x << "_o1); }\n"
           << "        s" << f << "[q] = " << x << "[(long long)(gj + " << x << "_o1) * " << x << "_p1 + (gi + " << x
           << "_o0)];\n"
-          << "    }\n";
+          << "    } }\n";
     }
     c << "    __syncthreads();\n";
     for (int r : p->an.order) {
         const Rule& R = d.rules[r];
         const int f = R.out[0];
+        if (G.inl[f]) continue;
         const Tile& t = G.tile[f];
-        c << "    for (int q = tid; q < " << t.w * t.h << "; q += " << NT << ") {\n"
-          << "        const int a = q % " << t.w << ", b = q / " << t.w << ";\n";
-        for (size_t k = 0; k < R.in.size(); ++k) {
-            const hfav_ref& x = R.in[k];
-            const Tile& u = G.tile[x.field];
-            // cell a of t is cell a - t.hx + u.hx of u
-            c << "        const T in" << k << " = s" << x.field << "[(b + " << (u.hy - t.hy + x.off[1]) << ") * " << u.w
-              << " + (a + " << (u.hx - t.hx + x.off[0]) << ")];\n";
+        tile_loop(c, t.w, t.h);
+        for (size_t k = 0; k < R.in.size(); ++k)
+            c << "        const T in" << k << " = " << read(R.in[k].field, t, R.in[k].off[0], R.in[k].off[1]) << ";\n";
+        const std::string val = rule_call(R, "hfav_body" + std::to_string(r));
+        if (direct(f)) {
+            const std::string y = "y" + std::to_string(G.direct[f]);
+            c << "        if (i0 + a < nx && j0 + b < ny)\n"
+              << "            " << y << "[(long long)(j0 + b + " << y << "_o1) * " << y << "_p1 + (i0 + a + " << y
+              << "_o0)] = " << val << ";\n";
+        } else {
+            c << "        s" << f << "[q] = " << val << ";\n";
         }
-        c << "        s" << f << "[q] = " << rule_call(R, "hfav_body" + std::to_string(r)) << ";\n    }\n    __syncthreads();\n";
+        c << "    } }\n";
+        c << "    __syncthreads();\n";
     }
     for (size_t a = 0; a < d.goals.size(); ++a) {
         const int f = d.goals[a];
+        if (direct(f)) continue;
         const Tile& t = G.tile[f];
         const std::string y = "y" + std::to_string(a);
-        c << "    for (int q = tid; q < " << TX * TY << "; q += " << NT << ") {\n"
-          << "        const int a = q % " << TX << ", b = q / " << TX << ";\n"
-          << "        const int gi = i0 + a, gj = j0 + b;\n"
+        tile_loop(c, TX, TY);
+        c << "        const int gi = i0 + a, gj = j0 + b;\n"
           << "        if (gi < nx && gj < ny)\n"
           << "            " << y << "[(long long)(gj + " << y << "_o1) * " << y << "_p1 + (gi + " << y << "_o0)] = s" << f
           << "[(b + " << t.hy << ") * " << t.w << " + (a + " << t.hx << ")];\n"
-          << "    }\n";
+          << "    } }\n";
     }
     c << "}\n";
     return c.str();

@@ -79,3 +79,21 @@ def axiom_values(axioms, shape, seed):
         smooth = sum(np.sin(2 * np.pi * (k + 1 + d) * g / n) for d, (g, n) in enumerate(zip(grids, shape)))
         vals[a] = 0.5 * smooth / len(shape) + 0.5 * rng.uniform(-1, 1, shape)
     return vals
+
+
+def pointwise_dag():
+    """A DAG whose pointwise stages (read only at offset 0) nest: t0 a stencil
+    of a0, t1 = f(t0), t2 = g(t1, t0, a1), t3 a stencil of t2, goal = h(t3)."""
+    z = (0, 0, 0)
+    star = [((1, 0, 0)), ((-1, 0, 0)), ((0, 1, 0)), ((0, -1, 0)), z]
+    rules = [
+        dict(out="t0", refs=[("a0", o) for o in star], c=BODIES[7][0], fn=BODIES[7][1], params=[0.25]),
+        dict(out="t1", refs=[("t0", z)], c="sqrt(in0 * in0 + p0)", fn=lambda a, p0: np.sqrt(a * a + p0),
+             params=[0.5]),
+        dict(out="t2", refs=[("t1", z), ("t0", z), ("a1", z)], c="fmax(in0, in1) - p0 * in2",
+             fn=lambda a, b, c, p0: np.maximum(a, b) - p0 * c, params=[0.3]),
+        dict(out="t3", refs=[("t2", (1, 1, 0)), ("t2", (-1, 0, 0)), ("t2", (0, -1, 0))],
+             c="p0 * in0 + p1 * (in1 - in2)", fn=lambda a, b, c, p0, p1: p0 * a + p1 * (b - c), params=[0.7, 0.4]),
+        dict(out="g", refs=[("t3", z)], c="in0 / (1 + fabs(in0))", fn=lambda a: a / (1 + np.abs(a)), params=[]),
+    ]
+    return rules, ["a0", "a1"], ["g"]

@@ -117,3 +117,20 @@ def test_source_is_deterministic_and_mixes_catalogue_ops():
     L = _nvrtc()
     rc, log = _compile(L, a)
     assert rc == 0, log
+
+
+def test_pointwise_stages_are_inlined_and_the_goal_written_directly():
+    """t0 and t1 (read only at offset 0, over their readers' tiles) get no
+    shared tile; t2 (read at offsets) and the axiom a0 do; the goal is stored
+    from its rule.  The source still compiles."""
+    rules, axioms, goals = X.pointwise_dag()
+    P = H.Plan(X.to_spec(rules, axioms, goals, 2), [_grid((64, 64), 3)], H.HFAV_F32, H.HFAV_BC_PERIODIC,
+               "full:smem:32x4")
+    src = P.source()
+    names = P.spec.names
+    tiles = {names[int(k)] for k in __import__("re").findall(r"T\* s(\d+) = ", src)}
+    assert tiles == {"a0", "a1", "t2"}
+    assert "hfav_body1(hfav_body0(" in src
+    L = _nvrtc()
+    rc, log = _compile(L, src)
+    assert rc == 0, log

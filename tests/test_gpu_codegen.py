@@ -128,6 +128,25 @@ def test_random_dags_halo_given(seed, schedule):
         assert normwise(v, ref[g]) <= 1e-12, g
 
 
+@pytest.mark.parametrize("schedule", ["full:smem:32x4", "full:smem:128x2", "unfused:hbm:32x4"])
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_nested_pointwise_stages(schedule, dtype):
+    """Stages read only at offset 0 are evaluated inside their readers (two
+    levels deep here); the goal goes straight from its rule to memory."""
+    rules, axioms, goals = X.pointwise_dag()
+    spec = X.to_spec(rules, axioms, goals, 2)
+    shape, h = (67, 45), 3
+    core = X.axiom_values(axioms, shape, 3)
+    padded = []
+    for a in axioms:
+        arr = np.full(tuple(n + 2 * h for n in shape), np.nan)
+        arr[h:-h, h:-h] = core[a]
+        padded.append(arr.astype(dtype))
+    (got,), _ = run_plan(spec, padded, h, schedule, dtype)
+    ref = E.evaluate(X.to_oracle(rules), {a: core[a].astype(dtype).astype(np.float64) for a in axioms})["g"]
+    assert normwise(got, ref) <= (1e-12 if dtype == np.float64 else 2e-5)
+
+
 def test_rule_bodies_mixed_with_builtin_ops():
     D = H.DagSpec(2)
     D.rule("STENCIL_LINEAR", [("u", (1, 0)), ("u", (-1, 0)), ("u", (0, 1)), ("u", (0, -1)), ("u", (0, 0))], ["L"],
