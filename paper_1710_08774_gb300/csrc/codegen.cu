@@ -284,186 +284,229 @@ std::vector<int> rule_slots(const Rule& R, std::vector<int>* fields) {
     return slot;
 }
 
-// fused 2D: the CTA's tile geometry.  A CTA of tx x ty threads owns a tile of
-// TX = tx columns and TY = ty x rows_per_thread rows (8 while every field's
-// tile fits in 96 KB of shared memory, so two CTAs share an SM, fewer
-// otherwise): taller tiles recompute less of the halo.
-struct Tile { int hx, hy, w, h; size_t off; };
-struct Fused {
-    int TX = 0, TY = 0, NT = 0;
+// fused 2D: rolling buffers (Sec. 3.5 "Contraction").  A CTA of NT threads
+// owns a strip of TXc = NT - (widest footprint in x) columns and a chunk of
+// rows, and streams down the chunk one row step at a time.  Every field that
+// is read keeps a ring of the last W rows of its strip (its footprint in x)
+// in shared memory; a field computed at step s holds row s - lead, its lead
+// putting every row it reads in an earlier step, so one barrier per step
+// orders the whole DAG.  Axiom rows are fetched P steps ahead with cp.async
+// into P extra ring rows.  A stage that all readers take at offset 0 over
+// the same footprint is evaluated inside them (never stored); goals go from
+// their rule to the caller's arrays.
+constexpr int kAhead = 4;   // axiom rows in flight per CTA
+
+struct SField {
+    int hxlo = 0, hxhi = 0, hylo = 0, hyhi = 0;
+    int w = 0;         // ring row width: TXc + hxlo + hxhi
+    int lead = 0;      // computed at step s: row s - lead
+    int W = 0;         // ring rows (0: not stored)
+    bool axiom = false, inl = false;
+    int goal = -1;     // goal slot, -1 if not a goal
+    int rule = -1;     // producer
+    size_t off = 0;    // shared-memory offset of the ring
+    std::vector<std::array<int, 3>> eff;   // (field, dx, dy) read, inlined stages expanded
+};
+struct Stream {
+    int NT = 0, TXc = 0, ylo = 0, yhi = 0;   // steps [ylo, jn + yhi)
     size_t smem = 0;
-    std::vector<Tile> tile;
-    std::vector<char> inl;      // computed inside its readers, never stored
-    std::vector<int> direct;    // goal slot written straight from its rule, else -1
+    std::vector<SField> f;
 };
 
-int fused_geometry(const hfav_plan_t* p, const Schedule& s, Fused* G) {
+int stream_geometry(const hfav_plan_t* p, const Schedule& s, Stream* S) {
     const Dag& d = p->dag;
     const size_t es = p->dtype == HFAV_F64 ? 8 : 4;
-    G->TX = s.tx;
-    G->NT = s.tx * s.ty;
-    G->tile.assign(d.n_fields, Tile());
-    std::vector<int> readers(d.n_fields, 0), producer(d.n_fields, -1), goal_slot(d.n_fields, -1);
-    std::vector<char> off0(d.n_fields, 1);
+    const int nf = d.n_fields;
+    S->NT = s.tx * s.ty;
+    S->f.assign(nf, SField());
+    std::vector<int> readers(nf, 0);
+    std::vector<char> off0(nf, 1);
     for (size_t r = 0; r < d.rules.size(); ++r) {
-        producer[d.rules[r].out[0]] = (int)r;
+        S->f[d.rules[r].out[0]].rule = (int)r;
         for (const hfav_ref& x : d.rules[r].in) {
             readers[x.field]++;
             if (x.off[0] || x.off[1] || x.off[2]) off0[x.field] = 0;
         }
     }
-    for (size_t a = 0; a < d.goals.size(); ++a) goal_slot[d.goals[a]] = (int)a;
-    auto same = [](const Tile& x, const Tile& y) { return x.hx == y.hx && x.hy == y.hy && x.w == y.w && x.h == y.h; };
-    for (int rows = 8; rows >= 1; rows /= 2) {
-        G->TY = s.ty * rows;
-        for (int f = 0; f < d.n_fields; ++f) {
-            // tile of field f over its footprint: [-halo_lo, T + halo_hi) per axis
-            const hfav_field_info& fi = p->an.field[f];
-            Tile t;
-            t.hx = fi.halo_lo[0]; t.hy = fi.halo_lo[1];
-            t.w = G->TX + fi.halo_lo[0] + fi.halo_hi[0];
-            t.h = G->TY + fi.halo_lo[1] + fi.halo_hi[1];
-            t.off = 0;
-            G->tile[f] = t;
-        }
-        // a rule output that every reader takes at offset 0 over the same tile
-        // is evaluated inside the readers (a pointwise stage fused into its
-        // consumer); a goal that nothing reads, over exactly the tile, is
-        // written from its rule to the caller's array
-        G->inl.assign(d.n_fields, 0);
-        G->direct.assign(d.n_fields, -1);
-        for (int f = 0; f < d.n_fields; ++f) {
-            const bool produced = producer[f] >= 0 && goal_slot[f] < 0;
-            if (produced && readers[f] > 0 && off0[f]) {
-                bool ok = true;
-                for (const Rule& R : d.rules)
-                    for (const hfav_ref& x : R.in)
-                        if (x.field == f && !same(G->tile[R.out[0]], G->tile[f])) ok = false;
-                G->inl[f] = ok;
-            }
-            const Tile& t = G->tile[f];
-            if (goal_slot[f] >= 0 && producer[f] >= 0 && readers[f] == 0 && t.w == G->TX && t.h == G->TY)
-                G->direct[f] = goal_slot[f];
-        }
-        G->smem = 0;
-        for (int f = 0; f < d.n_fields; ++f) {
-            if (G->inl[f] || G->direct[f] >= 0) continue;
-            G->tile[f].off = G->smem;
-            G->smem += ((size_t)G->tile[f].w * G->tile[f].h * es + 15) / 16 * 16;
-        }
-        if (G->smem <= 96 * 1024) break;
+    int hxmax = 0;
+    for (int f = 0; f < nf; ++f) {
+        const hfav_field_info& fi = p->an.field[f];
+        SField& F = S->f[f];
+        F.hxlo = fi.halo_lo[0]; F.hxhi = fi.halo_hi[0]; F.hylo = fi.halo_lo[1]; F.hyhi = fi.halo_hi[1];
+        hxmax = std::max(hxmax, F.hxlo + F.hxhi);
     }
-    if (G->smem > 200 * 1024)
-        return set_error(HFAV_EUNSUPPORTED, "the fields' tiles exceed shared memory; use a narrower tile");
-    // every read of a rule stays inside its input's tile: the footprint of an
-    // input covers the footprint of each consumer shifted by the offset
+    for (int a : d.axioms) S->f[a].axiom = true;
+    for (size_t a = 0; a < d.goals.size(); ++a) S->f[d.goals[a]].goal = (int)a;
+    S->TXc = S->NT - hxmax;
+    if (S->TXc < 32) return set_error(HFAV_EUNSUPPORTED, "this DAG's footprint is too wide for the tile; use a wider one");
+    auto same = [&](int a, int b) {
+        const SField &A = S->f[a], &B = S->f[b];
+        return A.hxlo == B.hxlo && A.hxhi == B.hxhi && A.hylo == B.hylo && A.hyhi == B.hyhi;
+    };
+    for (int f = 0; f < nf; ++f) {
+        SField& F = S->f[f];
+        F.w = S->TXc + F.hxlo + F.hxhi;
+        if (F.rule >= 0 && F.goal < 0 && readers[f] > 0 && off0[f]) {
+            bool ok = true;
+            for (const Rule& R : d.rules)
+                for (const hfav_ref& x : R.in)
+                    if (x.field == f && !same(R.out[0], f)) ok = false;
+            F.inl = ok;
+        }
+    }
+    // the rows each computed field reads, inlined stages expanded
+    std::function<void(int, int, int, std::vector<std::array<int, 3>>*)> expand =
+        [&](int f, int dx, int dy, std::vector<std::array<int, 3>>* out) {
+            for (const hfav_ref& x : d.rules[S->f[f].rule].in) {
+                if (S->f[x.field].inl) expand(x.field, dx + x.off[0], dy + x.off[1], out);
+                else out->push_back({x.field, dx + x.off[0], dy + x.off[1]});
+            }
+        };
     for (int r : p->an.order) {
-        const Rule& R = d.rules[r];
-        const Tile& t = G->tile[R.out[0]];
-        for (const hfav_ref& x : R.in) {
-            const Tile& u = G->tile[x.field];
-            const int lo_x = -t.hx + x.off[0], hi_x = t.w - t.hx - 1 + x.off[0];
-            const int lo_y = -t.hy + x.off[1], hi_y = t.h - t.hy - 1 + x.off[1];
-            if (lo_x < -u.hx || hi_x > u.w - u.hx - 1 || lo_y < -u.hy || hi_y > u.h - u.hy - 1)
-                return set_error(HFAV_EINVAL, "internal: a rule's footprint leaves its input's tile");
+        const int f = d.rules[r].out[0];
+        SField& F = S->f[f];
+        if (F.inl) continue;
+        expand(f, 0, 0, &F.eff);
+        int lead = -(1 << 20);
+        for (auto& e : F.eff) lead = std::max(lead, S->f[e[0]].lead + e[2]);
+        F.lead = lead + 1;
+    }
+    // ring rows: from the oldest row a reader still needs to the newest written
+    for (int f = 0; f < nf; ++f) {
+        SField& F = S->f[f];
+        if (F.inl) continue;
+        for (int c = 0; c < nf; ++c)
+            for (auto& e : S->f[c].eff)
+                if (e[0] == f) F.W = std::max(F.W, S->f[c].lead - F.lead - e[2] + 1);
+        if (F.axiom) F.W = std::max(F.W, 1) + kAhead;
+    }
+    S->smem = 0;
+    S->ylo = 1 << 20;
+    S->yhi = -(1 << 20);
+    for (int f = 0; f < nf; ++f) {
+        SField& F = S->f[f];
+        if (F.inl) continue;
+        if (F.W > 0) {
+            F.off = S->smem;
+            S->smem += ((size_t)F.W * F.w * es + 15) / 16 * 16;
+        }
+        if (F.axiom || F.rule >= 0) {
+            S->ylo = std::min(S->ylo, -F.hylo + F.lead);
+            S->yhi = std::max(S->yhi, F.hyhi + F.lead);
+        }
+    }
+    if (S->smem > 200 * 1024) return set_error(HFAV_EUNSUPPORTED, "the fields' rings exceed shared memory");
+    // every read stays inside the ring it reads: columns within the input's
+    // footprint, rows within its footprint and still in the ring
+    for (int f = 0; f < nf; ++f) {
+        const SField& F = S->f[f];
+        if (F.inl || F.rule < 0) continue;
+        for (auto& e : F.eff) {
+            const SField& G = S->f[e[0]];
+            const bool cols = -F.hxlo + e[1] >= -G.hxlo && F.hxhi + e[1] <= G.hxhi;
+            const bool rows = -F.hylo + e[2] >= -G.hylo && F.hyhi + e[2] <= G.hyhi;
+            const bool ring = F.lead - G.lead - e[2] >= 1 && F.lead - G.lead - e[2] + 1 <= G.W - (G.axiom ? kAhead : 0);
+            if (!cols || !rows || !ring) return set_error(HFAV_EINVAL, "internal: a rule reads outside its input's ring");
         }
     }
     return HFAV_OK;
 }
 
-// the fused kernel: load the axioms' footprints, evaluate the rules in
-// topological order over their own footprints (a barrier between rules), store
-// the goals' tiles
-std::string fused_source(const hfav_plan_t* p, const Fused& G) {
+std::string stream_source(const hfav_plan_t* p, const Stream& S) {
     const Dag& d = p->dag;
-    const int TX = G.TX, TY = G.TY, NT = G.NT;
-    // a loop over the w x h cells of a tile, NT threads, unrolled (its trip
-    // count is a constant): cell (a, b) of the tile, q = b * w + a
-    auto tile_loop = [&](std::ostringstream& c, int w, int h) {
-        const int n = w * h, trips = (n + NT - 1) / NT;
-        c << "    #pragma unroll\n"
-          << "    for (int it = 0; it < " << trips << "; ++it) {\n"
-          << "        const int q = tid + it * " << NT << ";\n"
-          << "        if (" << (n % NT ? "q < " + std::to_string(n) : std::string("true")) << ") {\n"
-          << "        const int a = q % " << w << ", b = q / " << w << ";\n";
-    };
-    auto direct = [&](int f) { return G.direct[f] >= 0; };
-    std::vector<int> producer(d.n_fields, -1);
-    for (size_t r = 0; r < d.rules.size(); ++r) producer[d.rules[r].out[0]] = (int)r;
-    // the value of field f at the cell (a, b) of tile t shifted by (ox, oy):
-    // from f's shared tile, or, for an inlined field, its rule's body on its
-    // own inputs at the same cell
-    std::function<std::string(int, const Tile&, int, int)> read = [&](int f, const Tile& t, int ox, int oy) {
-        if (G.inl[f]) {
-            const Rule& R = d.rules[producer[f]];
-            std::string v = "hfav_body" + std::to_string(producer[f]) + "(";
-            for (size_t k = 0; k < R.in.size(); ++k)
-                v += (k ? ", " : "") + read(R.in[k].field, t, R.in[k].off[0], R.in[k].off[1]);
-            return v + ")";
-        }
-        const Tile& u = G.tile[f];
-        return "s" + std::to_string(f) + "[(b + " + std::to_string(u.hy - t.hy + oy) + ") * " + std::to_string(u.w) +
-               " + (a + " + std::to_string(u.hx - t.hx + ox) + ")]";
+    const bool f64 = p->dtype == HFAV_F64;
+    const int NT = S.NT, TXc = S.TXc;
+    auto slot = [](const std::string& row, int W) {   // ring row of a (possibly negative) row index
+        return "((unsigned)(" + row + " + " + std::to_string(1024 * W) + ") % " + std::to_string(W) + "u)";
     };
     std::ostringstream c;
-    c << prelude(p->dtype == HFAV_F64);
+    c << prelude(f64)
+      << "__device__ __forceinline__ void hfav_cp(void* dst, const void* src) {\n"
+      << "    const unsigned sa = (unsigned)__cvta_generic_to_shared(dst);\n"
+      << "    asm volatile(\"cp.async.ca.shared.global [%0], [%1], " << (f64 ? 8 : 4)
+      << ";\\n\" :: \"r\"(sa), \"l\"(src) : \"memory\");\n"
+      << "}\n"
+      << "__device__ __forceinline__ void hfav_commit() { asm volatile(\"cp.async.commit_group;\\n\" ::: \"memory\"); }\n"
+      << "__device__ __forceinline__ void hfav_wait() { asm volatile(\"cp.async.wait_group " << kAhead
+      << ";\\n\" ::: \"memory\"); }\n";
     for (int r : p->an.order) c << rule_fn(d.rules[r], "hfav_body" + std::to_string(r));
     c << "extern \"C\" __global__ void __launch_bounds__(" << NT << ") hfav_cg_fused(";
     for (size_t a = 0; a < d.axioms.size(); ++a) c << array_params("x" + std::to_string(a), false) << ", ";
     for (size_t a = 0; a < d.goals.size(); ++a) c << array_params("y" + std::to_string(a), true) << ", ";
-    c << "int nx, int ny) {\n"
+    c << "int nx, int ny, int CH) {\n"
       << "    extern __shared__ __align__(16) unsigned char smem[];\n"
-      << "    const int tid = threadIdx.x, i0 = blockIdx.x * " << TX << ", j0 = blockIdx.y * " << TY << ";\n";
+      << "    const int tid = threadIdx.x, i0 = blockIdx.x * " << TXc << ", j0 = blockIdx.y * CH;\n"
+      << "    const int jn = min(CH, ny - j0);\n";
     for (int f = 0; f < d.n_fields; ++f)
-        if (!direct(f) && !G.inl[f]) c << "    T* s" << f << " = (T*)(smem + " << G.tile[f].off << ");\n";
-    // axioms: the footprint, wrapped (periodic) or from the caller's halo
+        if (!S.f[f].inl && S.f[f].W > 0) c << "    T* s" << f << " = (T*)(smem + " << S.f[f].off << ");\n";
+    // axioms: each thread's column (fixed), a row fetch issued kAhead steps ahead
     for (size_t a = 0; a < d.axioms.size(); ++a) {
         const int f = d.axioms[a];
-        const Tile& t = G.tile[f];
+        const SField& F = S.f[f];
         const std::string x = "x" + std::to_string(a);
-        tile_loop(c, t.w, t.h);
-        c << "        int gi = i0 - " << t.hx << " + a, gj = j0 - " << t.hy << " + b;\n"
-          << "        if (" << x << "_w) { gi = hfav_wrap(gi, nx); gj = hfav_wrap(gj, ny); }\n"
-          << "        else { gi = min(max(gi, -" << x << "_o0), nx - 1 + " << x << "_o0); gj = min(max(gj, -" << x
-          << "_o1), ny - 1 + " << x << "_o1); }\n"
-          << "        s" << f << "[q] = " << x << "[(long long)(gj + " << x << "_o1) * " << x << "_p1 + (gi + " << x
-          << "_o0)];\n"
-          << "    } }\n";
+        c << "    const bool act" << a << " = tid < " << F.w << ";\n"
+          << "    int col" << a << " = i0 - " << F.hxlo << " + tid;\n"
+          << "    if (" << x << "_w) col" << a << " = hfav_wrap(col" << a << ", nx);\n"
+          << "    else col" << a << " = min(max(col" << a << ", -" << x << "_o0), nx - 1 + " << x << "_o0);\n"
+          << "    const T* src" << a << " = " << x << " + col" << a << " + " << x << "_o0;\n"
+          << "    auto fetch" << a << " = [&](int r) {\n"
+          << "        if (act" << a << " && r >= -" << F.hylo << " && r < jn + " << F.hyhi << ") {\n"
+          << "            int gj = j0 + r;\n"
+          << "            if (" << x << "_w) gj = hfav_wrap(gj, ny);\n"
+          << "            else gj = min(max(gj, -" << x << "_o1), ny - 1 + " << x << "_o1);\n"
+          << "            hfav_cp(s" << f << " + " << slot("r", F.W) << " * " << F.w << " + tid, src" << a
+          << " + (long long)(gj + " << x << "_o1) * " << x << "_p1);\n"
+          << "        }\n"
+          << "    };\n";
     }
-    c << "    __syncthreads();\n";
+    c << "    #pragma unroll 1\n"
+      << "    for (int r = " << S.ylo << "; r < " << S.ylo + kAhead << "; ++r) {\n";
+    for (size_t a = 0; a < d.axioms.size(); ++a) c << "        fetch" << a << "(r);\n";
+    c << "        hfav_commit();\n    }\n";
+    c << "    #pragma unroll 1\n"
+      << "    for (int s = " << S.ylo << "; s < jn + " << S.yhi << "; ++s) {\n";
+    for (size_t a = 0; a < d.axioms.size(); ++a) c << "        fetch" << a << "(s + " << kAhead << ");\n";
+    c << "        hfav_commit();\n";
+    // computed fields in topological order: row s - lead
     for (int r : p->an.order) {
         const Rule& R = d.rules[r];
         const int f = R.out[0];
-        if (G.inl[f]) continue;
-        const Tile& t = G.tile[f];
-        tile_loop(c, t.w, t.h);
+        const SField& F = S.f[f];
+        if (F.inl) continue;
+        c << "        {\n"
+          << "            const int r = s - " << F.lead << ";\n"
+          << "            if (r >= -" << F.hylo << " && r < jn + " << F.hyhi << " && tid < " << F.w << ") {\n";
+        // the value of field g at this thread's cell shifted by (dx, dy)
+        std::function<std::string(int, int, int)> read = [&](int g, int dx, int dy) -> std::string {
+            const SField& G = S.f[g];
+            if (G.inl) {
+                const Rule& Q = d.rules[G.rule];
+                std::string v = "hfav_body" + std::to_string(G.rule) + "(";
+                for (size_t k = 0; k < Q.in.size(); ++k)
+                    v += (k ? ", " : "") + read(Q.in[k].field, dx + Q.in[k].off[0], dy + Q.in[k].off[1]);
+                return v + ")";
+            }
+            return "s" + std::to_string(g) + "[" + slot("r + " + std::to_string(dy), G.W) + " * " +
+                   std::to_string(G.w) + " + tid + " + std::to_string(dx + G.hxlo - F.hxlo) + "]";
+        };
         for (size_t k = 0; k < R.in.size(); ++k)
-            c << "        const T in" << k << " = " << read(R.in[k].field, t, R.in[k].off[0], R.in[k].off[1]) << ";\n";
-        const std::string val = rule_call(R, "hfav_body" + std::to_string(r));
-        if (direct(f)) {
-            const std::string y = "y" + std::to_string(G.direct[f]);
-            c << "        if (i0 + a < nx && j0 + b < ny)\n"
-              << "            " << y << "[(long long)(j0 + b + " << y << "_o1) * " << y << "_p1 + (i0 + a + " << y
-              << "_o0)] = " << val << ";\n";
-        } else {
-            c << "        s" << f << "[q] = " << val << ";\n";
+            c << "                const T in" << k << " = " << read(R.in[k].field, R.in[k].off[0], R.in[k].off[1]) << ";\n";
+        c << "                const T v = " << rule_call(R, "hfav_body" + std::to_string(r)) << ";\n";
+        if (F.W > 0) c << "                s" << f << "[" << slot("r", F.W) << " * " << F.w << " + tid] = v;\n";
+        if (F.goal >= 0) {
+            const std::string y = "y" + std::to_string(F.goal);
+            c << "                const int x = tid - " << F.hxlo << ";\n"
+              << "                if (r >= 0 && r < jn && x >= 0 && x < " << TXc << " && i0 + x < nx)\n"
+              << "                    " << y << "[(long long)(j0 + r + " << y << "_o1) * " << y << "_p1 + (i0 + x + " << y
+              << "_o0)] = v;\n";
         }
-        c << "    } }\n";
-        c << "    __syncthreads();\n";
+        c << "            }\n        }\n";
     }
-    for (size_t a = 0; a < d.goals.size(); ++a) {
-        const int f = d.goals[a];
-        if (direct(f)) continue;
-        const Tile& t = G.tile[f];
-        const std::string y = "y" + std::to_string(a);
-        tile_loop(c, TX, TY);
-        c << "        const int gi = i0 + a, gj = j0 + b;\n"
-          << "        if (gi < nx && gj < ny)\n"
-          << "            " << y << "[(long long)(gj + " << y << "_o1) * " << y << "_p1 + (gi + " << y << "_o0)] = s" << f
-          << "[(b + " << t.hy << ") * " << t.w << " + (a + " << t.hx << ")];\n"
-          << "    } }\n";
-    }
-    c << "}\n";
+    c << "        hfav_wait();\n"
+      << "        __syncthreads();\n"
+      << "    }\n"
+      << "    asm volatile(\"cp.async.wait_all;\\n\" ::: \"memory\");\n"
+      << "}\n";
     return c.str();
 }
 
@@ -472,10 +515,10 @@ std::string fused_source(const hfav_plan_t* p, const Fused& G) {
 int plan_source(const hfav_plan_t* p, std::string* out) {
     if (p->pipeline != PIPE_CODEGEN) return set_error(HFAV_EUNSUPPORTED, "the plan runs no generated kernels");
     if (p->sched.fusion != FUSE_UNFUSED) {
-        Fused G;
-        int rc = fused_geometry(p, p->sched, &G);
+        Stream S;
+        int rc = stream_geometry(p, p->sched, &S);
         if (rc) return rc;
-        *out = fused_source(p, G);
+        *out = stream_source(p, S);
         return HFAV_OK;
     }
     std::ostringstream o;
@@ -513,13 +556,31 @@ int launch_codegen(hfav_plan_t* p, const Schedule& s, void* const* ax, void* con
     if (s.fusion == FUSE_UNFUSED) return launch_generic(p, ax, go, st);
     const Dag& d = p->dag;
     const hfav_grid& g = p->grids[0];
-    Fused G;
-    int rc = fused_geometry(p, s, &G);
+    Stream S;
+    int rc = stream_geometry(p, s, &S);
     if (rc) return rc;
     cudaKernel_t k;
-    if ((rc = compile(fused_source(p, G), "hfav_cg_fused", &k))) return rc;
-    if (G.smem > 48 * 1024)
-        HFAV_CUDA(cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G.smem));
+    if ((rc = compile(stream_source(p, S), "hfav_cg_fused", &k))) return rc;
+    if (S.smem > 48 * 1024)
+        HFAV_CUDA(cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem));
+    const int nx = (int)g.extent[0], ny = (int)g.extent[1];
+    // rows per chunk: the wave count that costs least, each chunk paying the
+    // pipeline's fill (yhi - ylo steps beyond its rows)
+    int dev = 0, sms = 0, per_sm = 0;
+    HFAV_CUDA(cudaGetDevice(&dev));
+    HFAV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    HFAV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k, S.NT, S.smem));
+    const int64_t resident = (int64_t)std::max(1, sms) * std::max(1, per_sm);
+    const int64_t strips = (nx + S.TXc - 1) / S.TXc;
+    const int fill = S.yhi - S.ylo;
+    int CH = ny;
+    double best = 1e300;
+    for (int64_t chunks = 1; chunks <= ny; chunks = chunks < 8 ? chunks + 1 : chunks * 5 / 4) {
+        const int ch = (int)((ny + chunks - 1) / chunks);
+        const int64_t ctas = strips * ((ny + ch - 1) / ch);
+        const double cost = (double)(ch + fill) * (double)((ctas + resident - 1) / resident);
+        if (cost < best) { best = cost; CH = ch; }
+    }
     ArgPack A;
     for (size_t a = 0; a < d.axioms.size(); ++a) add_array(A, caller_view_cg(p, ax[a]));
     for (size_t a = 0; a < d.goals.size(); ++a) {
@@ -527,12 +588,12 @@ int launch_codegen(hfav_plan_t* p, const Schedule& s, void* const* ax, void* con
         y.wrap = 0;
         add_array(A, y);
     }
-    const int nx = (int)g.extent[0], ny = (int)g.extent[1];
     A.add(nx);
     A.add(ny);
+    A.add(CH);
     auto args = A.ptrs();
-    dim3 grd((nx + G.TX - 1) / G.TX, (ny + G.TY - 1) / G.TY);
-    HFAV_CUDA(cudaLaunchKernel((const void*)k, grd, dim3(G.NT), args.data(), G.smem, st));
+    dim3 grd((unsigned)strips, (unsigned)((ny + CH - 1) / CH));
+    HFAV_CUDA(cudaLaunchKernel((const void*)k, grd, dim3(S.NT), args.data(), S.smem, st));
     HFAV_LAUNCHED(p->rt, "codegen_fused", st);
     return HFAV_OK;
 }
