@@ -309,6 +309,7 @@ struct SField {
 };
 struct Stream {
     int NT = 0, TXc = 0, ylo = 0, yhi = 0;   // steps [ylo, jn + yhi)
+    int U = 1;                               // steps per unrolled pass
     size_t smem = 0;
     std::vector<SField> f;
 };
@@ -379,6 +380,10 @@ int stream_geometry(const hfav_plan_t* p, const Schedule& s, Stream* S) {
             for (auto& e : S->f[c].eff)
                 if (e[0] == f) F.W = std::max(F.W, S->f[c].lead - F.lead - e[2] + 1);
         if (F.axiom) F.W = std::max(F.W, 1) + kAhead;
+        // a power of two, so that one unrolled pass of U = max W steps sees
+        // every ring at fixed rows
+        if (F.W > 0) { int w2 = 1; while (w2 < F.W) w2 *= 2; F.W = w2; }
+        S->U = std::max(S->U, F.W);
     }
     S->smem = 0;
     S->ylo = 1 << 20;
@@ -459,52 +464,68 @@ std::string stream_source(const hfav_plan_t* p, const Stream& S) {
           << "        }\n"
           << "    };\n";
     }
+    for (int f = 0; f < d.n_fields; ++f) {
+        const SField& F = S.f[f];
+        if (F.goal < 0) continue;
+        const std::string y = "y" + std::to_string(F.goal), g = std::to_string(F.goal);
+        c << "    const int gx" << g << " = tid - " << F.hxlo << ";\n"
+          << "    const bool gok" << g << " = gx" << g << " >= 0 && gx" << g << " < " << TXc << " && i0 + gx" << g
+          << " < nx;\n"
+          << "    T* const gcol" << g << " = " << y << " + (long long)" << y << "_o1 * " << y << "_p1 + (i0 + gx" << g
+          << " + " << y << "_o0);\n";
+    }
     c << "    #pragma unroll 1\n"
       << "    for (int r = " << S.ylo << "; r < " << S.ylo + kAhead << "; ++r) {\n";
     for (size_t a = 0; a < d.axioms.size(); ++a) c << "        fetch" << a << "(r);\n";
     c << "        hfav_commit();\n    }\n";
+    // the step loop in passes of U steps: step s = sp + k with sp - ylo a
+    // multiple of U, so the ring row of row sp + k - lead + dy is a constant
+    const int U = S.U;
+    auto cslot = [&](int k, int lead, int dy, int W) { return ((S.ylo + k - lead + dy) % W + W) % W; };
     c << "    #pragma unroll 1\n"
-      << "    for (int s = " << S.ylo << "; s < jn + " << S.yhi << "; ++s) {\n";
-    for (size_t a = 0; a < d.axioms.size(); ++a) c << "        fetch" << a << "(s + " << kAhead << ");\n";
-    c << "        hfav_commit();\n";
-    // computed fields in topological order: row s - lead
-    for (int r : p->an.order) {
-        const Rule& R = d.rules[r];
-        const int f = R.out[0];
-        const SField& F = S.f[f];
-        if (F.inl) continue;
-        c << "        {\n"
-          << "            const int r = s - " << F.lead << ";\n"
-          << "            if (r >= -" << F.hylo << " && r < jn + " << F.hyhi << " && tid < " << F.w << ") {\n";
-        // the value of field g at this thread's cell shifted by (dx, dy)
-        std::function<std::string(int, int, int)> read = [&](int g, int dx, int dy) -> std::string {
-            const SField& G = S.f[g];
-            if (G.inl) {
-                const Rule& Q = d.rules[G.rule];
-                std::string v = "hfav_body" + std::to_string(G.rule) + "(";
-                for (size_t k = 0; k < Q.in.size(); ++k)
-                    v += (k ? ", " : "") + read(Q.in[k].field, dx + Q.in[k].off[0], dy + Q.in[k].off[1]);
-                return v + ")";
+      << "    for (int sp = " << S.ylo << "; sp < jn + " << S.yhi << "; sp += " << U << ") {\n";
+    for (int k = 0; k < U; ++k) {
+        c << "    {   // step sp + " << k << "\n"
+          << "        const int s = sp + " << k << ";\n";
+        for (size_t a = 0; a < d.axioms.size(); ++a) c << "        fetch" << a << "(s + " << kAhead << ");\n";
+        c << "        hfav_commit();\n";
+        for (int r : p->an.order) {
+            const Rule& R = d.rules[r];
+            const int f = R.out[0];
+            const SField& F = S.f[f];
+            if (F.inl) continue;
+            c << "        {\n"
+              << "            const int r = s - " << F.lead << ";\n"
+              << "            if (r >= -" << F.hylo << " && r < jn + " << F.hyhi << " && tid < " << F.w << ") {\n";
+            // the value of field g at this thread's cell shifted by (dx, dy)
+            std::function<std::string(int, int, int)> read = [&](int g, int dx, int dy) -> std::string {
+                const SField& G = S.f[g];
+                if (G.inl) {
+                    const Rule& Q = d.rules[G.rule];
+                    std::string v = "hfav_body" + std::to_string(G.rule) + "(";
+                    for (size_t q = 0; q < Q.in.size(); ++q)
+                        v += (q ? ", " : "") + read(Q.in[q].field, dx + Q.in[q].off[0], dy + Q.in[q].off[1]);
+                    return v + ")";
+                }
+                return "s" + std::to_string(g) + "[" +
+                       std::to_string(cslot(k, F.lead, dy, G.W) * G.w + dx + G.hxlo - F.hxlo) + " + tid]";
+            };
+            for (size_t q = 0; q < R.in.size(); ++q)
+                c << "                const T in" << q << " = " << read(R.in[q].field, R.in[q].off[0], R.in[q].off[1])
+                  << ";\n";
+            c << "                const T v = " << rule_call(R, "hfav_body" + std::to_string(r)) << ";\n";
+            if (F.W > 0) c << "                s" << f << "[" << cslot(k, F.lead, 0, F.W) * F.w << " + tid] = v;\n";
+            if (F.goal >= 0) {
+                c << "                if (r >= 0 && r < jn && gok" << F.goal << ")\n"
+                  << "                    gcol" << F.goal << "[(long long)(j0 + r) * y" << F.goal << "_p1] = v;\n";
             }
-            return "s" + std::to_string(g) + "[" + slot("r + " + std::to_string(dy), G.W) + " * " +
-                   std::to_string(G.w) + " + tid + " + std::to_string(dx + G.hxlo - F.hxlo) + "]";
-        };
-        for (size_t k = 0; k < R.in.size(); ++k)
-            c << "                const T in" << k << " = " << read(R.in[k].field, R.in[k].off[0], R.in[k].off[1]) << ";\n";
-        c << "                const T v = " << rule_call(R, "hfav_body" + std::to_string(r)) << ";\n";
-        if (F.W > 0) c << "                s" << f << "[" << slot("r", F.W) << " * " << F.w << " + tid] = v;\n";
-        if (F.goal >= 0) {
-            const std::string y = "y" + std::to_string(F.goal);
-            c << "                const int x = tid - " << F.hxlo << ";\n"
-              << "                if (r >= 0 && r < jn && x >= 0 && x < " << TXc << " && i0 + x < nx)\n"
-              << "                    " << y << "[(long long)(j0 + r + " << y << "_o1) * " << y << "_p1 + (i0 + x + " << y
-              << "_o0)] = v;\n";
+            c << "            }\n        }\n";
         }
-        c << "            }\n        }\n";
+        c << "        hfav_wait();\n"
+          << "        __syncthreads();\n"
+          << "    }\n";
     }
-    c << "        hfav_wait();\n"
-      << "        __syncthreads();\n"
-      << "    }\n"
+    c << "    }\n"
       << "    asm volatile(\"cp.async.wait_all;\\n\" ::: \"memory\");\n"
       << "}\n";
     return c.str();
