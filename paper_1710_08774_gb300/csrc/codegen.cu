@@ -308,13 +308,13 @@ struct SField {
     std::vector<std::array<int, 3>> eff;   // (field, dx, dy) read, inlined stages expanded
 };
 struct Stream {
-    int NT = 0, TXc = 0, ylo = 0, yhi = 0;   // steps [ylo, jn + yhi)
+    int NT = 0, V = 1, TXc = 0, ylo = 0, yhi = 0;   // steps [ylo, jn + yhi)
     int U = 1;                               // steps per unrolled pass
     size_t smem = 0;
     std::vector<SField> f;
 };
 
-int stream_geometry(const hfav_plan_t* p, const Schedule& s, Stream* S) {
+int stream_geometry_v(const hfav_plan_t* p, const Schedule& s, int V, Stream* S) {
     const Dag& d = p->dag;
     const size_t es = p->dtype == HFAV_F64 ? 8 : 4;
     const int nf = d.n_fields;
@@ -338,7 +338,8 @@ int stream_geometry(const hfav_plan_t* p, const Schedule& s, Stream* S) {
     }
     for (int a : d.axioms) S->f[a].axiom = true;
     for (size_t a = 0; a < d.goals.size(); ++a) S->f[d.goals[a]].goal = (int)a;
-    S->TXc = S->NT - hxmax;
+    S->V = V;
+    S->TXc = S->V * S->NT - hxmax;
     if (S->TXc < 32) return set_error(HFAV_EUNSUPPORTED, "this DAG's footprint is too wide for the tile; use a wider one");
     auto same = [&](int a, int b) {
         const SField &A = S->f[a], &B = S->f[b];
@@ -417,6 +418,19 @@ int stream_geometry(const hfav_plan_t* p, const Schedule& s, Stream* S) {
     return HFAV_OK;
 }
 
+// each thread takes V columns of a row (tid, tid + NT, ...): the per-step
+// work (row checks, fetch set-up, barrier) is shared by V cells.  V = 4 (FP32)
+// or 2 (FP64), halved while the rings need more than 96 KB of shared memory.
+int stream_geometry(const hfav_plan_t* p, const Schedule& s, Stream* S) {
+    int rc = HFAV_EUNSUPPORTED;
+    for (int V = p->dtype == HFAV_F64 ? 2 : 4; V >= 1; V /= 2) {
+        *S = Stream();
+        rc = stream_geometry_v(p, s, V, S);
+        if (rc == HFAV_OK && S->smem <= 96 * 1024) return HFAV_OK;
+    }
+    return rc;
+}
+
 std::string stream_source(const hfav_plan_t* p, const Stream& S) {
     const Dag& d = p->dag;
     const bool f64 = p->dtype == HFAV_F64;
@@ -444,35 +458,56 @@ std::string stream_source(const hfav_plan_t* p, const Stream& S) {
       << "    const int jn = min(CH, ny - j0);\n";
     for (int f = 0; f < d.n_fields; ++f)
         if (!S.f[f].inl && S.f[f].W > 0) c << "    T* s" << f << " = (T*)(smem + " << S.f[f].off << ");\n";
-    // axioms: each thread's column (fixed), a row fetch issued kAhead steps ahead
+    // a thread's columns tid + v NT, v < V, of a ring row of width w: the
+    // condition that column set v is inside ("" when always, "-" never)
+    const int V = S.V;
+    auto inside = [&](int v, int w) -> std::string {
+        if (w - v * NT >= NT) return "";
+        if (w - v * NT <= 0) return "-";
+        return "tid < " + std::to_string(w - v * NT);
+    };
+    // axioms: each thread's columns (fixed), a row fetch issued kAhead steps ahead
     for (size_t a = 0; a < d.axioms.size(); ++a) {
         const int f = d.axioms[a];
         const SField& F = S.f[f];
         const std::string x = "x" + std::to_string(a);
-        c << "    const bool act" << a << " = tid < " << F.w << ";\n"
-          << "    int col" << a << " = i0 - " << F.hxlo << " + tid;\n"
-          << "    if (" << x << "_w) col" << a << " = hfav_wrap(col" << a << ", nx);\n"
-          << "    else col" << a << " = min(max(col" << a << ", -" << x << "_o0), nx - 1 + " << x << "_o0);\n"
-          << "    const T* src" << a << " = " << x << " + col" << a << " + " << x << "_o0;\n"
-          << "    auto fetch" << a << " = [&](int r) {\n"
-          << "        if (act" << a << " && r >= -" << F.hylo << " && r < jn + " << F.hyhi << ") {\n"
+        for (int v = 0; v < V; ++v) {
+            const std::string cv = std::to_string(a) + "_" + std::to_string(v);
+            if (inside(v, F.w) == "-") continue;
+            c << "    int col" << cv << " = i0 - " << F.hxlo << " + tid + " << v * NT << ";\n"
+              << "    if (" << x << "_w) col" << cv << " = hfav_wrap(col" << cv << ", nx);\n"
+              << "    else col" << cv << " = min(max(col" << cv << ", -" << x << "_o0), nx - 1 + " << x << "_o0);\n"
+              << "    const T* src" << cv << " = " << x << " + col" << cv << " + " << x << "_o0;\n";
+        }
+        c << "    auto fetch" << a << " = [&](int r) {\n"
+          << "        if (r >= -" << F.hylo << " && r < jn + " << F.hyhi << ") {\n"
           << "            int gj = j0 + r;\n"
           << "            if (" << x << "_w) gj = hfav_wrap(gj, ny);\n"
           << "            else gj = min(max(gj, -" << x << "_o1), ny - 1 + " << x << "_o1);\n"
-          << "            hfav_cp(s" << f << " + " << slot("r", F.W) << " * " << F.w << " + tid, src" << a
-          << " + (long long)(gj + " << x << "_o1) * " << x << "_p1);\n"
-          << "        }\n"
+          << "            const long long ro = (long long)(gj + " << x << "_o1) * " << x << "_p1;\n"
+          << "            T* const dst = s" << f << " + " << slot("r", F.W) << " * " << F.w << " + tid;\n";
+        for (int v = 0; v < V; ++v) {
+            const std::string in = inside(v, F.w), cv = std::to_string(a) + "_" + std::to_string(v);
+            if (in == "-") continue;
+            c << "            " << (in.empty() ? "" : "if (" + in + ") ") << "hfav_cp(dst + " << v * NT << ", src" << cv
+              << " + ro);\n";
+        }
+        c << "        }\n"
           << "    };\n";
     }
     for (int f = 0; f < d.n_fields; ++f) {
         const SField& F = S.f[f];
         if (F.goal < 0) continue;
-        const std::string y = "y" + std::to_string(F.goal), g = std::to_string(F.goal);
-        c << "    const int gx" << g << " = tid - " << F.hxlo << ";\n"
-          << "    const bool gok" << g << " = gx" << g << " >= 0 && gx" << g << " < " << TXc << " && i0 + gx" << g
-          << " < nx;\n"
-          << "    T* const gcol" << g << " = " << y << " + (long long)" << y << "_o1 * " << y << "_p1 + (i0 + gx" << g
-          << " + " << y << "_o0);\n";
+        const std::string y = "y" + std::to_string(F.goal);
+        for (int v = 0; v < V; ++v) {
+            const std::string g = std::to_string(F.goal) + "_" + std::to_string(v);
+            if (inside(v, F.w) == "-") continue;
+            c << "    const int gx" << g << " = tid + " << v * NT - F.hxlo << ";\n"
+              << "    const bool gok" << g << " = gx" << g << " >= 0 && gx" << g << " < " << TXc << " && i0 + gx" << g
+              << " < nx;\n"
+              << "    T* const gcol" << g << " = " << y << " + (long long)" << y << "_o1 * " << y << "_p1 + (i0 + gx"
+              << g << " + " << y << "_o0);\n";
+        }
     }
     c << "    #pragma unroll 1\n"
       << "    for (int r = " << S.ylo << "; r < " << S.ylo + kAhead << "; ++r) {\n";
@@ -496,28 +531,36 @@ std::string stream_source(const hfav_plan_t* p, const Stream& S) {
             if (F.inl) continue;
             c << "        {\n"
               << "            const int r = s - " << F.lead << ";\n"
-              << "            if (r >= -" << F.hylo << " && r < jn + " << F.hyhi << " && tid < " << F.w << ") {\n";
-            // the value of field g at this thread's cell shifted by (dx, dy)
-            std::function<std::string(int, int, int)> read = [&](int g, int dx, int dy) -> std::string {
-                const SField& G = S.f[g];
-                if (G.inl) {
-                    const Rule& Q = d.rules[G.rule];
-                    std::string v = "hfav_body" + std::to_string(G.rule) + "(";
-                    for (size_t q = 0; q < Q.in.size(); ++q)
-                        v += (q ? ", " : "") + read(Q.in[q].field, dx + Q.in[q].off[0], dy + Q.in[q].off[1]);
-                    return v + ")";
+              << "            if (r >= -" << F.hylo << " && r < jn + " << F.hyhi << ") {\n";
+            for (int v = 0; v < V; ++v) {
+                const std::string in = inside(v, F.w);
+                if (in == "-") continue;
+                // the value of field g at this thread's cell (column set v) shifted by (dx, dy)
+                std::function<std::string(int, int, int)> read = [&](int g, int dx, int dy) -> std::string {
+                    const SField& G = S.f[g];
+                    if (G.inl) {
+                        const Rule& Q = d.rules[G.rule];
+                        std::string val = "hfav_body" + std::to_string(G.rule) + "(";
+                        for (size_t q = 0; q < Q.in.size(); ++q)
+                            val += (q ? ", " : "") + read(Q.in[q].field, dx + Q.in[q].off[0], dy + Q.in[q].off[1]);
+                        return val + ")";
+                    }
+                    return "s" + std::to_string(g) + "[" +
+                           std::to_string(cslot(k, F.lead, dy, G.W) * G.w + dx + G.hxlo - F.hxlo + v * NT) + " + tid]";
+                };
+                c << "            " << (in.empty() ? "{" : "if (" + in + ") {") << "\n";
+                for (size_t q = 0; q < R.in.size(); ++q)
+                    c << "                const T in" << q << " = " << read(R.in[q].field, R.in[q].off[0], R.in[q].off[1])
+                      << ";\n";
+                c << "                const T v = " << rule_call(R, "hfav_body" + std::to_string(r)) << ";\n";
+                if (F.W > 0)
+                    c << "                s" << f << "[" << cslot(k, F.lead, 0, F.W) * F.w + v * NT << " + tid] = v;\n";
+                if (F.goal >= 0) {
+                    const std::string g = std::to_string(F.goal) + "_" + std::to_string(v);
+                    c << "                if (r >= 0 && r < jn && gok" << g << ")\n"
+                      << "                    gcol" << g << "[(long long)(j0 + r) * y" << F.goal << "_p1] = v;\n";
                 }
-                return "s" + std::to_string(g) + "[" +
-                       std::to_string(cslot(k, F.lead, dy, G.W) * G.w + dx + G.hxlo - F.hxlo) + " + tid]";
-            };
-            for (size_t q = 0; q < R.in.size(); ++q)
-                c << "                const T in" << q << " = " << read(R.in[q].field, R.in[q].off[0], R.in[q].off[1])
-                  << ";\n";
-            c << "                const T v = " << rule_call(R, "hfav_body" + std::to_string(r)) << ";\n";
-            if (F.W > 0) c << "                s" << f << "[" << cslot(k, F.lead, 0, F.W) * F.w << " + tid] = v;\n";
-            if (F.goal >= 0) {
-                c << "                if (r >= 0 && r < jn && gok" << F.goal << ")\n"
-                  << "                    gcol" << F.goal << "[(long long)(j0 + r) * y" << F.goal << "_p1] = v;\n";
+                c << "            }\n";
             }
             c << "            }\n        }\n";
         }
