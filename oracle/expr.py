@@ -42,9 +42,14 @@ def evaluate(rules, axioms):
 
     rules:  list of (out, refs, fn, params): out a field name, refs a list of
             (field, offset) read in this order, fn(*inputs, *params) -> array.
+            fn may instead be the string "sum" or "max": a reduction (Sec.
+            3.4) of its one input over the whole grid to a scalar.  Scalars
+            read by a grid rule take the same value at every cell (a
+            broadcast); offsets on them are ignored.
     axioms: dict field -> array (..., j, i); every other field is produced by
             exactly one rule.
-    Returns a dict with every field (axioms included) as an FP64 array."""
+    Returns a dict with every field (axioms included) as an FP64 array
+    (0-d for scalars)."""
     vals = {k: np.asarray(v, dtype=np.float64) for k, v in axioms.items()}
     outs = [r[0] for r in rules]
     if len(set(outs)) != len(outs) or set(outs) & set(vals):
@@ -57,8 +62,14 @@ def evaluate(rules, axioms):
         for r in ready:
             out, refs, fn, params = rules[r]
             ins = [shifted(vals[f], off) for f, off in refs]
-            # a rule body that ignores its inputs still yields a field
-            vals[out] = np.broadcast_to(np.asarray(fn(*ins, *params), dtype=np.float64), ins[0].shape).copy()
+            if isinstance(fn, str):
+                red = {"sum": np.sum, "max": np.max}[fn]
+                vals[out] = np.asarray(red(ins[0]), dtype=np.float64)
+                continue
+            # the output has the shape of the largest input (a grid rule that
+            # reads scalars, or ignores its inputs, still yields a field)
+            shape = max((a.shape for a in ins), key=len)
+            vals[out] = np.broadcast_to(np.asarray(fn(*ins, *params), dtype=np.float64), shape).copy()
         pending = [r for r in pending if r not in ready]
     return vals
 
@@ -81,3 +92,17 @@ def chain2d_rules():
             lambda a, b, c, d: np.sqrt((a - b) * (a - b) + (c - d) * (c - d)) * 0.5, [])
     squash = ("out", [("G", (0, 0))], lambda g: g / (1 + g), [])
     return [lap, grad, squash]
+
+
+def normalization_rules():
+    """The normalization example (Sec. 5.2) in the reading taken here: flux =
+    u(i+1) - u(i), diff = flux(i) - flux(i-1), the norm accumulation acc =
+    sum of diff^2 over the grid, the norm root = sqrt(acc), out = diff / root."""
+    return [
+        ("flux", [("u", (1, 0)), ("u", (0, 0))], lambda a, b: a - b, []),
+        ("diff", [("flux", (0, 0)), ("flux", (-1, 0))], lambda a, b: a - b, []),
+        ("sq", [("diff", (0, 0))], lambda a: a * a, []),
+        ("acc", [("sq", (0, 0))], "sum", []),
+        ("root", [("acc", (0, 0))], lambda a: np.sqrt(a), []),
+        ("out", [("diff", (0, 0)), ("root", (0, 0))], lambda a, b: a / b, []),
+    ]

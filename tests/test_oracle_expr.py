@@ -10,6 +10,10 @@
   (two producers, a missing input, a cycle).
 - The 2D chain written as three rule bodies equals the C oracle of the chain,
   itself pinned separately.
+- Reductions and broadcasts: sums and maxima with closed forms (a constant,
+  the index i, a full period of a sine), brute force with a loop, and the
+  normalization example's invariants (unit 2-norm, invariance under scaling
+  and shifting u, the second difference of a quadratic).
 """
 import itertools
 
@@ -101,3 +105,47 @@ def test_chain_as_rule_bodies_equals_c_oracle():
     ref = oracle.chain2d(up)[2]
     got = E.evaluate(E.chain2d_rules(), {"u": core})["out"]
     assert np.max(np.abs(got - ref)) < 1e-14
+
+
+def test_reductions_closed_forms():
+    ny, nx = 12, 20
+    j, i = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    u = i.astype(float)
+    v = E.evaluate([("s", [("u", (0, 0))], "sum", []), ("m", [("u", (0, 0))], "max", []),
+                    ("c", [("u", (0, 0))], lambda a: 0 * a + 2.5, []), ("sc", [("c", (0, 0))], "sum", []),
+                    ("w", [("u", (1, 0))], lambda a: np.sin(2 * np.pi * a / nx), []), ("sw", [("w", (0, 0))], "sum", [])],
+                   {"u": u})
+    assert v["s"] == ny * nx * (nx - 1) / 2 and v["m"] == nx - 1
+    assert v["sc"] == 2.5 * nx * ny
+    assert abs(v["sw"]) < 1e-12
+    assert v["s"].shape == () and v["w"].shape == (ny, nx)
+
+
+def test_broadcast_and_reduction_brute_force():
+    rng = np.random.default_rng(11)
+    ny, nx = 4, 5
+    u = rng.uniform(-1, 1, (ny, nx))
+    rules = [("d", [("u", (1, 0)), ("u", (0, -1))], lambda a, b: a - 2 * b, []),
+             ("m", [("d", (0, 1))], "max", []), ("s", [("d", (-1, 0))], "sum", []),
+             ("k", [("m", (0, 0)), ("s", (0, 0))], lambda a, b: a * b + 1, []),
+             ("o", [("d", (0, 0)), ("k", (0, 0)), ("u", (-1, 1))], lambda a, b, c: a * b - c, [])]
+    got = E.evaluate(rules, {"u": u})
+    d = np.array([[u[jj, (ii + 1) % nx] - 2 * u[(jj - 1) % ny, ii] for ii in range(nx)] for jj in range(ny)])
+    m = max(d[(jj + 1) % ny, ii] for jj in range(ny) for ii in range(nx))
+    s = sum(d[jj, (ii - 1) % nx] for jj in range(ny) for ii in range(nx))
+    k = m * s + 1
+    o = np.array([[d[jj, ii] * k - u[(jj + 1) % ny, (ii - 1) % nx] for ii in range(nx)] for jj in range(ny)])
+    assert got["m"] == m and abs(got["s"] - s) < 1e-13 and np.allclose(got["o"], o, rtol=0, atol=1e-13)
+
+
+def test_normalization_invariants():
+    rng = np.random.default_rng(3)
+    u = rng.uniform(0, 1, (16, 24))
+    out = E.evaluate(E.normalization_rules(), {"u": u})["out"]
+    assert abs(np.sum(out * out) - 1) < 1e-13
+    for v in (7.5 * u, u + 3.0):
+        assert np.allclose(E.evaluate(E.normalization_rules(), {"u": v})["out"], out, rtol=0, atol=1e-13)
+    # u = i^2 along i (periodic wrap aside): the second difference is 2 in the interior columns
+    q = np.broadcast_to((np.arange(24.0) ** 2), (16, 24)).copy()
+    diff = E.evaluate(E.normalization_rules(), {"u": q})["diff"]
+    assert np.all(diff[:, 1:-1] == 2)
