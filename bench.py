@@ -338,8 +338,49 @@ class Chain(Workload):
         return None, None, None
 
 
+class Norm(Workload):
+    """The normalization example (Sec. 5.2) on an n x n grid: flux, second
+    difference, norm accumulation (a reduction) and root, division (a
+    broadcast after the split), all as rule bodies on generated kernels."""
+    fused_prefix = ("full",)
+
+    def __init__(self, H, I, torch, dev, n, dtype, seed=0):
+        self.n, self.dtype = n, dtype
+        self.name = f"normalization2d_{'fp64' if dtype == 'f64' else 'fp32'}_{n}x{n}"
+        td = torch.float64 if dtype == "f64" else torch.float32
+        self.u = torch.from_numpy(I.chain2d_input(n, seed=seed, halo=1)).to(dev).to(td)
+        self.out = torch.empty_like(self.u)
+        self.dag = H.normalization_dag()
+        self.hdt = H.HFAV_F64 if dtype == "f64" else H.HFAV_F32
+        self.grids = [H.Grid.of(self.u, 1)]
+        self.plan = H.Plan(self.dag, self.grids, self.hdt, H.HFAV_BC_PERIODIC, "full:smem:32x8")
+        self.esize = 8 if dtype == "f64" else 4
+
+    def unfused_plan(self, H):
+        return H.Plan(self.dag, self.grids, self.hdt, H.HFAV_BC_PERIODIC, "unfused")
+
+    def run(self, plan):
+        plan.run([self.u], [self.out], 1)
+
+    def cells_per_step(self):
+        return self.n * self.n
+
+    def compulsory_bytes(self, sched):
+        # fused: nest 1 reads u, writes diff; nest 2 reads diff, writes out.  Unfused:
+        # flux (u -> flux), diff (flux -> diff), sq (diff -> sq), the sum (reads sq), out (diff -> out)
+        return (9 if sched.startswith("unfused") else 4) * self.esize * self.cells_per_step()
+
+    def kernel_work(self, kernel, it):
+        # each fused nest reads one array and writes one
+        return "hbm", 2 * self.esize * self.cells_per_step(), "GB/s", peaks().get("hbm_gbs", 6787.6), \
+            "measured copy bandwidth (MEASURED_PEAKS.json)"
+
+    def io(self):
+        return None, None, None
+
+
 WORKLOADS = ["godunov1024_f64", "godunov4096_f32", "batch64_f32", "chain2d256_f64", "chain2d16384_f32", "chain3d512_f32",
-             "cosmo1024_f32", "codegen2d16384_f32"]
+             "cosmo1024_f32", "codegen2d16384_f32", "norm2d16384_f32"]
 
 
 def make(name, H, I, torch, dev):
@@ -365,6 +406,9 @@ def make(name, H, I, torch, dev):
     m = re.fullmatch(r"codegen2d(\d+)_(f32|f64)", name)
     if m:
         return Chain(H, I, torch, dev, 2, int(m.group(1)), m.group(2), 0, expr=True)
+    m = re.fullmatch(r"norm2d(\d+)_(f32|f64)", name)
+    if m:
+        return Norm(H, I, torch, dev, int(m.group(1)), m.group(2))
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -392,6 +436,14 @@ def oracle_sample(workload, n=None):
         oracle.chain2d(u)
         dt = time.perf_counter() - t0
         return n * n / dt / 1e9, dt, 0.0, f"{n}x{n} u~U[0,1), single thread"
+    if workload.startswith("norm"):
+        from oracle import expr as E
+        n = n or 4096
+        u = I.chain2d_input(n, seed=0, halo=1)[1:-1, 1:-1]
+        t0 = time.perf_counter()
+        E.evaluate(E.normalization_rules(), {"u": u})
+        dt = time.perf_counter() - t0
+        return n * n / dt / 1e9, dt, 0.0, f"{n}x{n} u~U[0,1), expression oracle (numpy), single thread"
     if workload.startswith("codegen"):
         from oracle import expr as E
         n = n or 8192
@@ -434,6 +486,9 @@ def workload_name(key):
     m = re.fullmatch(r"codegen2d(\d+)_(f32|f64)", key)
     if m:
         return f"codegen_chain2d_{'fp64' if m.group(2) == 'f64' else 'fp32'}_{m.group(1)}x{m.group(1)}"
+    m = re.fullmatch(r"norm2d(\d+)_(f32|f64)", key)
+    if m:
+        return f"normalization2d_{'fp64' if m.group(2) == 'f64' else 'fp32'}_{m.group(1)}x{m.group(1)}"
     raise SystemExit(f"unknown workload {key}")
 
 
@@ -626,13 +681,13 @@ def bench(args, name, torch, H, I, dev, ws, rank, local):
 
 
 def _axg(w):
-    if isinstance(w, (Chain, Cosmo)):
+    if isinstance(w, (Chain, Cosmo, Norm)):
         return [w.u], [w.out]
     return w.ins, w.outs
 
 
 def _nsteps(w):
-    return 1 if isinstance(w, (Chain, Cosmo)) else w.tsteps
+    return 1 if isinstance(w, (Chain, Cosmo, Norm)) else w.tsteps
 
 
 def main():
@@ -641,7 +696,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=WORKLOADS[0], help="one of " + ", ".join(WORKLOADS + ["all"]) + ", or chain2d<N>_f32|f64 / chain3d<N>_f32|f64 / cosmo<N>_f32|f64 / codegen2d<N>_f32|f64 (other sizes)")
+    ap.add_argument("--workload", default=WORKLOADS[0], help="one of " + ", ".join(WORKLOADS + ["all"]) + ", or chain2d<N>_f32|f64 / chain3d<N>_f32|f64 / cosmo<N>_f32|f64 / codegen2d<N>_f32|f64 / norm2d<N>_f32|f64 (other sizes)")
     ap.add_argument("--schedule", default=None, help="fixed schedule (default: autotuned among fused ones)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--once", action="store_true", help="profiling case: build the plan and run it once")

@@ -128,9 +128,19 @@ typedef enum {
     /* reduction: dt = params[0] * dx / max over interior cells of max(|u|+c, |v|+c)
      * in: U0 U1 U2 U3; out: one rank-0 field; params: cfl, gamma */
     HFAV_OP_CFL_DT = 20,
-    /* reduction / broadcast pair used by planner-only examples */
+    /* reductions (Sec. 3.4), in: one grid field (any offset); out: one rank-0
+     * field = the sum / the maximum of the input over the interior cells,
+     * accumulated in FP64.  Rule bodies (HFAV_OP_EXPR) over rank-0 inputs
+     * finalize such results (e.g. a root); a rule body over the grid reads a
+     * rank-0 field at offset 0 as one value (a broadcast).  A rank-0 field is
+     * neither an axiom nor a goal.  Such DAGs run on generated kernels, 2D
+     * only: the fused form is one kernel per fusion group (the reduction
+     * splits the DAG), the unfused form one kernel per rule; the partials of
+     * each reduction are combined in a fixed order (bitwise repeatable). */
     HFAV_OP_REDUCE_SUM = 21,
-    HFAV_OP_BROADCAST = 22
+    /* planner-only broadcast op of the analysis examples */
+    HFAV_OP_BROADCAST = 22,
+    HFAV_OP_REDUCE_MAX = 23
 } hfav_op;
 
 /* A reference to a field at a relative offset (i, j, k): the paper's

@@ -37,7 +37,7 @@ def shifted(a, off):
     return out
 
 
-def evaluate(rules, axioms):
+def evaluate(rules, axioms, halo=0):
     """Run a DAG of rules to completion.
 
     rules:  list of (out, refs, fn, params): out a field name, refs a list of
@@ -48,6 +48,8 @@ def evaluate(rules, axioms):
             broadcast); offsets on them are ignored.
     axioms: dict field -> array (..., j, i); every other field is produced by
             exactly one rule.
+    halo:   with halo-padded axioms (see evaluate_padded), the reductions run
+            over the interior only.
     Returns a dict with every field (axioms included) as an FP64 array
     (0-d for scalars)."""
     vals = {k: np.asarray(v, dtype=np.float64) for k, v in axioms.items()}
@@ -64,7 +66,8 @@ def evaluate(rules, axioms):
             ins = [shifted(vals[f], off) for f, off in refs]
             if isinstance(fn, str):
                 red = {"sum": np.sum, "max": np.max}[fn]
-                vals[out] = np.asarray(red(ins[0]), dtype=np.float64)
+                a = ins[0][tuple(slice(halo, n - halo) for n in ins[0].shape)] if halo else ins[0]
+                vals[out] = np.asarray(red(a), dtype=np.float64)
                 continue
             # the output has the shape of the largest input (a grid rule that
             # reads scalars, or ignores its inputs, still yields a field)
@@ -77,15 +80,16 @@ def evaluate(rules, axioms):
 def evaluate_padded(rules, axioms_padded, halo, fields):
     """The given fields on the interior of halo-padded axioms (halo given by
     the caller, not periodic): evaluate on the padded arrays, crop `halo`
-    cells off every axis.  Exact when the halo covers the DAG's footprint."""
-    vals = evaluate(rules, axioms_padded)
+    cells off every axis; reductions run over the interior.  Exact when the
+    halo covers the DAG's footprint."""
+    vals = evaluate(rules, axioms_padded, halo)
     crop = lambda a: a[tuple(slice(halo, s - halo) for s in a.shape)]
     return {f: crop(vals[f]) for f in fields}
 
 
 def chain2d_rules():
-    """The 2D chain (Sec. 5.1's three-stage pattern: 5-point Laplacian L, half
-    gradient magnitude G of L, squash out = G / (1 + G)) as rule bodies."""
+    """The synthetic three-stage 2D chain (5-point Laplacian L, half gradient
+    magnitude G of L, squash out = G / (1 + G)) as rule bodies."""
     lap = ("L", [("u", (1, 0)), ("u", (-1, 0)), ("u", (0, 1)), ("u", (0, -1)), ("u", (0, 0))],
            lambda a, b, c, d, e, p0: a + b + c + d - p0 * e, [4.0])
     grad = ("G", [("L", (1, 0)), ("L", (-1, 0)), ("L", (0, 1)), ("L", (0, -1))],

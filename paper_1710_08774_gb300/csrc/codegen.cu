@@ -30,6 +30,7 @@
 #include <cstring>
 #include <functional>
 #include <map>
+#include <set>
 #include <mutex>
 #include <sstream>
 
@@ -284,61 +285,101 @@ std::vector<int> rule_slots(const Rule& R, std::vector<int>* fields) {
     return slot;
 }
 
-// fused 2D: rolling buffers (Sec. 3.5 "Contraction").  A CTA of NT threads
-// owns a strip of TXc = NT - (widest footprint in x) columns and a chunk of
-// rows, and streams down the chunk one row step at a time.  Every field that
-// is read keeps a ring of the last W rows of its strip (its footprint in x)
-// in shared memory; a field computed at step s holds row s - lead, its lead
-// putting every row it reads in an earlier step, so one barrier per step
-// orders the whole DAG.  Axiom rows are fetched P steps ahead with cp.async
-// into P extra ring rows.  A stage that all readers take at offset 0 over
-// the same footprint is evaluated inside them (never stored); goals go from
-// their rule to the caller's arrays.
-constexpr int kAhead = 4;   // axiom rows in flight per CTA
+// Fused 2D: rolling buffers (Sec. 3.5 "Contraction").  A streaming kernel
+// evaluates a part of the DAG: a fusion group of the analysis (the fused
+// form) or one rule (the unfused form of DAGs with reductions).  A CTA of NT
+// threads owns a strip of TXc = V NT - (widest footprint in x) columns, V
+// columns per thread, and a chunk of rows, and streams down the chunk one row
+// step at a time.  Every field the part reads keeps a ring of the last W rows
+// of its strip (its footprint in x) in shared memory; a field computed at
+// step s holds row s - lead, its lead putting every row it reads in an
+// earlier step, so one barrier per step orders the part.  Rows of the fields
+// the part reads from memory arrive P steps ahead by cp.async into P extra
+// ring rows.  A stage that all its readers take at offset 0 over the same
+// footprint is evaluated inside them (never stored).
+//
+// Reductions (Sec. 3.4) accumulate over the interior in the part that
+// produces their input (the steady state), one FP64 partial per CTA; a
+// one-CTA kernel then combines the partials in a fixed order and evaluates
+// the scalar rules (the finalization), and later parts read the scalars (the
+// broadcast).  Fields that cross from one part to a later one (the split)
+// are full arrays over their footprint.
+constexpr int kAhead = 4;   // rows in flight per CTA for the fields read from memory
+
+struct Part {
+    std::vector<int> rules;   // grid rules and reductions, topological order
+};
 
 struct SField {
     int hxlo = 0, hxhi = 0, hylo = 0, hyhi = 0;
-    int w = 0;         // ring row width: TXc + hxlo + hxhi
-    int lead = 0;      // computed at step s: row s - lead
-    int W = 0;         // ring rows (0: not stored)
-    bool axiom = false, inl = false;
-    int goal = -1;     // goal slot, -1 if not a goal
-    int rule = -1;     // producer
-    size_t off = 0;    // shared-memory offset of the ring
+    int w = 0;          // ring row width: TXc + hxlo + hxhi
+    int lead = 0;       // computed at step s: row s - lead
+    int W = 0;          // ring rows (0: not stored)
+    bool scalar = false, inl = false;
+    int load = -1;      // kernel array it is read from (x<load>), -1 if computed here or unused
+    int goal = -1;      // caller goal array it is written to (y<goal>, interior)
+    int cross = -1;     // plan array it is written to (z<cross>, owned cells of its footprint)
+    int red = -1;       // reduction slot: the part's reduction writing this rank-0 field
+    int rule = -1;      // producer inside the part
+    size_t off = 0;     // shared-memory offset of the ring
     std::vector<std::array<int, 3>> eff;   // (field, dx, dy) read, inlined stages expanded
 };
+
 struct Stream {
     int NT = 0, V = 1, TXc = 0, ylo = 0, yhi = 0;   // steps [ylo, jn + yhi)
-    int U = 1;                               // steps per unrolled pass
+    int U = 1;                                      // steps per unrolled pass
     size_t smem = 0;
     std::vector<SField> f;
+    std::vector<int> loads, goals, crosses, reds, scalars;   // fields, in parameter / slot order
+    std::vector<int> goal_slot;                              // caller goal index of each goals[k]
 };
 
-int stream_geometry_v(const hfav_plan_t* p, const Schedule& s, int V, Stream* S) {
+bool in_part(const Part& P, int r) { return std::find(P.rules.begin(), P.rules.end(), r) != P.rules.end(); }
+
+int stream_geometry_v(const hfav_plan_t* p, const Schedule& s, const Part& P, int V, Stream* S) {
     const Dag& d = p->dag;
     const size_t es = p->dtype == HFAV_F64 ? 8 : 4;
     const int nf = d.n_fields;
     S->NT = s.tx * s.ty;
+    S->V = V;
     S->f.assign(nf, SField());
     std::vector<int> readers(nf, 0);
-    std::vector<char> off0(nf, 1);
+    std::vector<char> off0(nf, 1), outside(nf, 0), involved(nf, 0);
     for (size_t r = 0; r < d.rules.size(); ++r) {
-        S->f[d.rules[r].out[0]].rule = (int)r;
+        const bool mine = in_part(P, (int)r);
         for (const hfav_ref& x : d.rules[r].in) {
+            if (!mine) { outside[x.field] = 1; continue; }
             readers[x.field]++;
+            involved[x.field] = 1;
             if (x.off[0] || x.off[1] || x.off[2]) off0[x.field] = 0;
         }
     }
+    for (int r : P.rules) { S->f[d.rules[r].out[0]].rule = r; involved[d.rules[r].out[0]] = 1; }
     int hxmax = 0;
     for (int f = 0; f < nf; ++f) {
         const hfav_field_info& fi = p->an.field[f];
         SField& F = S->f[f];
+        F.scalar = d.rank[f] == 0;
         F.hxlo = fi.halo_lo[0]; F.hxhi = fi.halo_hi[0]; F.hylo = fi.halo_lo[1]; F.hyhi = fi.halo_hi[1];
-        hxmax = std::max(hxmax, F.hxlo + F.hxhi);
+        if (involved[f]) hxmax = std::max(hxmax, F.hxlo + F.hxhi);
     }
-    for (int a : d.axioms) S->f[a].axiom = true;
-    for (size_t a = 0; a < d.goals.size(); ++a) S->f[d.goals[a]].goal = (int)a;
-    S->V = V;
+    for (int f = 0; f < nf; ++f) {
+        SField& F = S->f[f];
+        if (!involved[f]) continue;
+        if (F.scalar) {
+            if (F.rule >= 0) { F.red = (int)S->reds.size(); S->reds.push_back(f); }
+            else if (readers[f]) S->scalars.push_back(f);
+            continue;
+        }
+        if (F.rule < 0) { F.load = (int)S->loads.size(); S->loads.push_back(f); continue; }
+        const auto g = std::find(d.goals.begin(), d.goals.end(), f);
+        if (g != d.goals.end()) {
+            F.goal = (int)S->goals.size();
+            S->goals.push_back(f);
+            S->goal_slot.push_back((int)(g - d.goals.begin()));
+        }
+        if (outside[f]) { F.cross = (int)S->crosses.size(); S->crosses.push_back(f); }
+    }
     S->TXc = S->V * S->NT - hxmax;
     if (S->TXc < 32) return set_error(HFAV_EUNSUPPORTED, "this DAG's footprint is too wide for the tile; use a wider one");
     auto same = [&](int a, int b) {
@@ -348,41 +389,44 @@ int stream_geometry_v(const hfav_plan_t* p, const Schedule& s, int V, Stream* S)
     for (int f = 0; f < nf; ++f) {
         SField& F = S->f[f];
         F.w = S->TXc + F.hxlo + F.hxhi;
-        if (F.rule >= 0 && F.goal < 0 && readers[f] > 0 && off0[f]) {
+        if (F.rule >= 0 && !F.scalar && F.goal < 0 && F.cross < 0 && readers[f] > 0 && off0[f]) {
             bool ok = true;
-            for (const Rule& R : d.rules)
-                for (const hfav_ref& x : R.in)
-                    if (x.field == f && !same(R.out[0], f)) ok = false;
+            for (int r : P.rules)
+                for (const hfav_ref& x : d.rules[r].in)
+                    if (x.field == f && !same(d.rules[r].out[0], f)) ok = false;
             F.inl = ok;
         }
     }
-    // the rows each computed field reads, inlined stages expanded
+    // the rows each computed field reads, inlined stages expanded (scalars are
+    // kernel constants, not rows)
     std::function<void(int, int, int, std::vector<std::array<int, 3>>*)> expand =
         [&](int f, int dx, int dy, std::vector<std::array<int, 3>>* out) {
             for (const hfav_ref& x : d.rules[S->f[f].rule].in) {
+                if (S->f[x.field].scalar) continue;
                 if (S->f[x.field].inl) expand(x.field, dx + x.off[0], dy + x.off[1], out);
                 else out->push_back({x.field, dx + x.off[0], dy + x.off[1]});
             }
         };
     for (int r : p->an.order) {
+        if (!in_part(P, r)) continue;
         const int f = d.rules[r].out[0];
         SField& F = S->f[f];
         if (F.inl) continue;
         expand(f, 0, 0, &F.eff);
-        int lead = -(1 << 20);
+        int lead = F.eff.empty() ? -1 : -(1 << 20);
         for (auto& e : F.eff) lead = std::max(lead, S->f[e[0]].lead + e[2]);
         F.lead = lead + 1;
     }
-    // ring rows: from the oldest row a reader still needs to the newest written
+    // ring rows: from the oldest row a reader still needs to the newest written,
+    // a power of two, so that one unrolled pass of U = max W steps sees every
+    // ring at fixed rows
     for (int f = 0; f < nf; ++f) {
         SField& F = S->f[f];
-        if (F.inl) continue;
+        if (F.inl || F.scalar || !involved[f]) continue;
         for (int c = 0; c < nf; ++c)
             for (auto& e : S->f[c].eff)
                 if (e[0] == f) F.W = std::max(F.W, S->f[c].lead - F.lead - e[2] + 1);
-        if (F.axiom) F.W = std::max(F.W, 1) + kAhead;
-        // a power of two, so that one unrolled pass of U = max W steps sees
-        // every ring at fixed rows
+        if (F.load >= 0) F.W = std::max(F.W, 1) + kAhead;
         if (F.W > 0) { int w2 = 1; while (w2 < F.W) w2 *= 2; F.W = w2; }
         S->U = std::max(S->U, F.W);
     }
@@ -391,15 +435,13 @@ int stream_geometry_v(const hfav_plan_t* p, const Schedule& s, int V, Stream* S)
     S->yhi = -(1 << 20);
     for (int f = 0; f < nf; ++f) {
         SField& F = S->f[f];
-        if (F.inl) continue;
+        if (F.inl || !involved[f] || (F.scalar && F.red < 0)) continue;
         if (F.W > 0) {
             F.off = S->smem;
             S->smem += ((size_t)F.W * F.w * es + 15) / 16 * 16;
         }
-        if (F.axiom || F.rule >= 0) {
-            S->ylo = std::min(S->ylo, -F.hylo + F.lead);
-            S->yhi = std::max(S->yhi, F.hyhi + F.lead);
-        }
+        S->ylo = std::min(S->ylo, -F.hylo + F.lead);
+        S->yhi = std::max(S->yhi, F.hyhi + F.lead);
     }
     if (S->smem > 200 * 1024) return set_error(HFAV_EUNSUPPORTED, "the fields' rings exceed shared memory");
     // every read stays inside the ring it reads: columns within the input's
@@ -411,7 +453,7 @@ int stream_geometry_v(const hfav_plan_t* p, const Schedule& s, int V, Stream* S)
             const SField& G = S->f[e[0]];
             const bool cols = -F.hxlo + e[1] >= -G.hxlo && F.hxhi + e[1] <= G.hxhi;
             const bool rows = -F.hylo + e[2] >= -G.hylo && F.hyhi + e[2] <= G.hyhi;
-            const bool ring = F.lead - G.lead - e[2] >= 1 && F.lead - G.lead - e[2] + 1 <= G.W - (G.axiom ? kAhead : 0);
+            const bool ring = F.lead - G.lead - e[2] >= 1 && F.lead - G.lead - e[2] + 1 <= G.W - (G.load >= 0 ? kAhead : 0);
             if (!cols || !rows || !ring) return set_error(HFAV_EINVAL, "internal: a rule reads outside its input's ring");
         }
     }
@@ -421,22 +463,29 @@ int stream_geometry_v(const hfav_plan_t* p, const Schedule& s, int V, Stream* S)
 // each thread takes V columns of a row (tid, tid + NT, ...): the per-step
 // work (row checks, fetch set-up, barrier) is shared by V cells.  V = 4 (FP32)
 // or 2 (FP64), halved while the rings need more than 96 KB of shared memory.
-int stream_geometry(const hfav_plan_t* p, const Schedule& s, Stream* S) {
+int stream_geometry(const hfav_plan_t* p, const Schedule& s, const Part& P, Stream* S) {
     int rc = HFAV_EUNSUPPORTED;
     for (int V = p->dtype == HFAV_F64 ? 2 : 4; V >= 1; V /= 2) {
         *S = Stream();
-        rc = stream_geometry_v(p, s, V, S);
+        rc = stream_geometry_v(p, s, P, V, S);
         if (rc == HFAV_OK && S->smem <= 96 * 1024) return HFAV_OK;
     }
     return rc;
 }
 
-std::string stream_source(const hfav_plan_t* p, const Stream& S) {
+std::string stream_source(const hfav_plan_t* p, const Stream& S, const Part& P, const std::string& name) {
     const Dag& d = p->dag;
     const bool f64 = p->dtype == HFAV_F64;
-    const int NT = S.NT, TXc = S.TXc;
+    const int NT = S.NT, TXc = S.TXc, V = S.V;
     auto slot = [](const std::string& row, int W) {   // ring row of a (possibly negative) row index
         return "((unsigned)(" + row + " + " + std::to_string(1024 * W) + ") % " + std::to_string(W) + "u)";
+    };
+    // a thread's columns tid + v NT, v < V, of a ring row of width w: the
+    // condition that column set v is inside ("" when always, "-" never)
+    auto inside = [&](int v, int w) -> std::string {
+        if (w - v * NT >= NT) return "";
+        if (w - v * NT <= 0) return "-";
+        return "tid < " + std::to_string(w - v * NT);
     };
     std::ostringstream c;
     c << prelude(f64)
@@ -448,46 +497,47 @@ std::string stream_source(const hfav_plan_t* p, const Stream& S) {
       << "__device__ __forceinline__ void hfav_commit() { asm volatile(\"cp.async.commit_group;\\n\" ::: \"memory\"); }\n"
       << "__device__ __forceinline__ void hfav_wait() { asm volatile(\"cp.async.wait_group " << kAhead
       << ";\\n\" ::: \"memory\"); }\n";
-    for (int r : p->an.order) c << rule_fn(d.rules[r], "hfav_body" + std::to_string(r));
-    c << "extern \"C\" __global__ void __launch_bounds__(" << NT << ") hfav_cg_fused(";
-    for (size_t a = 0; a < d.axioms.size(); ++a) c << array_params("x" + std::to_string(a), false) << ", ";
-    for (size_t a = 0; a < d.goals.size(); ++a) c << array_params("y" + std::to_string(a), true) << ", ";
-    c << "int nx, int ny, int CH) {\n"
+    for (int r : p->an.order)
+        if (in_part(P, r)) c << rule_fn(d.rules[r], "hfav_body" + std::to_string(r));
+    c << "extern \"C\" __global__ void __launch_bounds__(" << NT << ") " << name << "(";
+    for (size_t a = 0; a < S.loads.size(); ++a) c << array_params("x" + std::to_string(a), false) << ", ";
+    for (size_t a = 0; a < S.goals.size(); ++a) c << array_params("y" + std::to_string(a), true) << ", ";
+    for (size_t a = 0; a < S.crosses.size(); ++a) c << array_params("z" + std::to_string(a), true) << ", ";
+    c << "const double* __restrict__ scal, double* __restrict__ part, int nx, int ny, int CH) {\n"
       << "    extern __shared__ __align__(16) unsigned char smem[];\n"
       << "    const int tid = threadIdx.x, i0 = blockIdx.x * " << TXc << ", j0 = blockIdx.y * CH;\n"
-      << "    const int jn = min(CH, ny - j0);\n";
+      << "    const int jn = min(CH, ny - j0);\n"
+      << "    const bool last_x = i0 + " << TXc << " >= nx, last_y = j0 + jn >= ny;\n";
     for (int f = 0; f < d.n_fields; ++f)
         if (!S.f[f].inl && S.f[f].W > 0) c << "    T* s" << f << " = (T*)(smem + " << S.f[f].off << ");\n";
-    // a thread's columns tid + v NT, v < V, of a ring row of width w: the
-    // condition that column set v is inside ("" when always, "-" never)
-    const int V = S.V;
-    auto inside = [&](int v, int w) -> std::string {
-        if (w - v * NT >= NT) return "";
-        if (w - v * NT <= 0) return "-";
-        return "tid < " + std::to_string(w - v * NT);
-    };
-    // axioms: each thread's columns (fixed), a row fetch issued kAhead steps ahead
-    for (size_t a = 0; a < d.axioms.size(); ++a) {
-        const int f = d.axioms[a];
+    for (int f : S.scalars) c << "    const T sv" << f << " = (T)scal[" << f << "];\n";
+    for (size_t k = 0; k < S.reds.size(); ++k)
+        c << "    double racc" << k << " = "
+          << (d.rules[S.f[S.reds[k]].rule].op == HFAV_OP_REDUCE_MAX ? "__longlong_as_double(0xfff0000000000000ULL)" : "0.0")
+          << ";\n";
+    // fields read from memory: each thread's columns (fixed), a row fetch
+    // issued kAhead steps ahead, indices wrapped (periodic axioms) or clamped
+    // into the field's footprint
+    for (int f : S.loads) {
         const SField& F = S.f[f];
-        const std::string x = "x" + std::to_string(a);
+        const std::string a = std::to_string(F.load), x = "x" + a;
         for (int v = 0; v < V; ++v) {
-            const std::string cv = std::to_string(a) + "_" + std::to_string(v);
+            const std::string cv = a + "_" + std::to_string(v);
             if (inside(v, F.w) == "-") continue;
             c << "    int col" << cv << " = i0 - " << F.hxlo << " + tid + " << v * NT << ";\n"
               << "    if (" << x << "_w) col" << cv << " = hfav_wrap(col" << cv << ", nx);\n"
-              << "    else col" << cv << " = min(max(col" << cv << ", -" << x << "_o0), nx - 1 + " << x << "_o0);\n"
+              << "    else col" << cv << " = min(max(col" << cv << ", -" << F.hxlo << "), nx - 1 + " << F.hxhi << ");\n"
               << "    const T* src" << cv << " = " << x << " + col" << cv << " + " << x << "_o0;\n";
         }
         c << "    auto fetch" << a << " = [&](int r) {\n"
           << "        if (r >= -" << F.hylo << " && r < jn + " << F.hyhi << ") {\n"
           << "            int gj = j0 + r;\n"
           << "            if (" << x << "_w) gj = hfav_wrap(gj, ny);\n"
-          << "            else gj = min(max(gj, -" << x << "_o1), ny - 1 + " << x << "_o1);\n"
+          << "            else gj = min(max(gj, -" << F.hylo << "), ny - 1 + " << F.hyhi << ");\n"
           << "            const long long ro = (long long)(gj + " << x << "_o1) * " << x << "_p1;\n"
           << "            T* const dst = s" << f << " + " << slot("r", F.W) << " * " << F.w << " + tid;\n";
         for (int v = 0; v < V; ++v) {
-            const std::string in = inside(v, F.w), cv = std::to_string(a) + "_" + std::to_string(v);
+            const std::string in = inside(v, F.w), cv = a + "_" + std::to_string(v);
             if (in == "-") continue;
             c << "            " << (in.empty() ? "" : "if (" + in + ") ") << "hfav_cp(dst + " << v * NT << ", src" << cv
               << " + ro);\n";
@@ -495,23 +545,35 @@ std::string stream_source(const hfav_plan_t* p, const Stream& S) {
         c << "        }\n"
           << "    };\n";
     }
+    // written fields: each thread's column pointers (fixed); caller goals take
+    // the interior, crossing arrays the cells of their footprint this CTA owns
+    // (the interior part of its strip and chunk, plus the outer halo at the
+    // grid's edges)
     for (int f = 0; f < d.n_fields; ++f) {
         const SField& F = S.f[f];
-        if (F.goal < 0) continue;
-        const std::string y = "y" + std::to_string(F.goal);
-        for (int v = 0; v < V; ++v) {
-            const std::string g = std::to_string(F.goal) + "_" + std::to_string(v);
-            if (inside(v, F.w) == "-") continue;
-            c << "    const int gx" << g << " = tid + " << v * NT - F.hxlo << ";\n"
-              << "    const bool gok" << g << " = gx" << g << " >= 0 && gx" << g << " < " << TXc << " && i0 + gx" << g
-              << " < nx;\n"
-              << "    T* const gcol" << g << " = " << y << " + (long long)" << y << "_o1 * " << y << "_p1 + (i0 + gx"
-              << g << " + " << y << "_o0);\n";
+        for (int kind = 0; kind < 2; ++kind) {
+            const int idx = kind == 0 ? F.goal : F.cross;
+            if (idx < 0) continue;
+            const std::string y = (kind == 0 ? "y" : "z") + std::to_string(idx);
+            for (int v = 0; v < V; ++v) {
+                const std::string g = y + "_" + std::to_string(v);
+                if (inside(v, F.w) == "-") continue;
+                c << "    const int gx" << g << " = tid + " << v * NT - F.hxlo << ";\n";
+                if (kind == 0)
+                    c << "    const bool gok" << g << " = gx" << g << " >= 0 && gx" << g << " < " << TXc << " && i0 + gx" << g
+                      << " < nx;\n";
+                else
+                    c << "    const bool gok" << g << " = (gx" << g << " >= 0 && gx" << g << " < " << TXc << " && i0 + gx"
+                      << g << " < nx) || (i0 + gx" << g << " < 0) || (last_x && i0 + gx" << g << " >= nx && i0 + gx" << g
+                      << " < nx + " << F.hxhi << ");\n";
+                c << "    T* const gcol" << g << " = " << y << " + (long long)" << y << "_o1 * " << y << "_p1 + (i0 + gx" << g
+                  << " + " << y << "_o0);\n";
+            }
         }
     }
     c << "    #pragma unroll 1\n"
       << "    for (int r = " << S.ylo << "; r < " << S.ylo + kAhead << "; ++r) {\n";
-    for (size_t a = 0; a < d.axioms.size(); ++a) c << "        fetch" << a << "(r);\n";
+    for (int f : S.loads) c << "        fetch" << S.f[f].load << "(r);\n";
     c << "        hfav_commit();\n    }\n";
     // the step loop in passes of U steps: step s = sp + k with sp - ylo a
     // multiple of U, so the ring row of row sp + k - lead + dy is a constant
@@ -522,9 +584,10 @@ std::string stream_source(const hfav_plan_t* p, const Stream& S) {
     for (int k = 0; k < U; ++k) {
         c << "    {   // step sp + " << k << "\n"
           << "        const int s = sp + " << k << ";\n";
-        for (size_t a = 0; a < d.axioms.size(); ++a) c << "        fetch" << a << "(s + " << kAhead << ");\n";
+        for (int f : S.loads) c << "        fetch" << S.f[f].load << "(s + " << kAhead << ");\n";
         c << "        hfav_commit();\n";
         for (int r : p->an.order) {
+            if (!in_part(P, r)) continue;
             const Rule& R = d.rules[r];
             const int f = R.out[0];
             const SField& F = S.f[f];
@@ -538,6 +601,7 @@ std::string stream_source(const hfav_plan_t* p, const Stream& S) {
                 // the value of field g at this thread's cell (column set v) shifted by (dx, dy)
                 std::function<std::string(int, int, int)> read = [&](int g, int dx, int dy) -> std::string {
                     const SField& G = S.f[g];
+                    if (G.scalar) return "sv" + std::to_string(g);
                     if (G.inl) {
                         const Rule& Q = d.rules[G.rule];
                         std::string val = "hfav_body" + std::to_string(G.rule) + "(";
@@ -552,13 +616,28 @@ std::string stream_source(const hfav_plan_t* p, const Stream& S) {
                 for (size_t q = 0; q < R.in.size(); ++q)
                     c << "                const T in" << q << " = " << read(R.in[q].field, R.in[q].off[0], R.in[q].off[1])
                       << ";\n";
+                if (F.red >= 0) {
+                    // a reduction: the input's value over this CTA's interior cells
+                    const std::string x = "(tid + " + std::to_string(v * NT - F.hxlo) + ")";
+                    const std::string acc = "racc" + std::to_string(F.red);
+                    c << "                if (" << x << " < " << TXc << " && i0 + " << x << " < nx)\n"
+                      << "                    " << acc << " = "
+                      << (R.op == HFAV_OP_REDUCE_MAX ? "fmax(" + acc + ", (double)in0)" : acc + " + (double)in0") << ";\n";
+                    c << "            }\n";
+                    continue;
+                }
                 c << "                const T v = " << rule_call(R, "hfav_body" + std::to_string(r)) << ";\n";
                 if (F.W > 0)
                     c << "                s" << f << "[" << cslot(k, F.lead, 0, F.W) * F.w + v * NT << " + tid] = v;\n";
                 if (F.goal >= 0) {
-                    const std::string g = std::to_string(F.goal) + "_" + std::to_string(v);
+                    const std::string g = "y" + std::to_string(F.goal) + "_" + std::to_string(v);
                     c << "                if (r >= 0 && r < jn && gok" << g << ")\n"
                       << "                    gcol" << g << "[(long long)(j0 + r) * y" << F.goal << "_p1] = v;\n";
+                }
+                if (F.cross >= 0) {
+                    const std::string g = "z" + std::to_string(F.cross) + "_" + std::to_string(v);
+                    c << "                if (gok" << g << " && ((r >= 0 && r < jn) || j0 + r < 0 || (last_y && j0 + r >= ny)))\n"
+                      << "                    gcol" << g << "[(long long)(j0 + r) * z" << F.cross << "_p1] = v;\n";
                 }
                 c << "            }\n";
             }
@@ -569,29 +648,201 @@ std::string stream_source(const hfav_plan_t* p, const Stream& S) {
           << "    }\n";
     }
     c << "    }\n"
-      << "    asm volatile(\"cp.async.wait_all;\\n\" ::: \"memory\");\n"
-      << "}\n";
+      << "    asm volatile(\"cp.async.wait_all;\\n\" ::: \"memory\");\n";
+    // one partial per CTA and reduction, combined in a fixed order
+    if (!S.reds.empty()) {
+        c << "    __shared__ double hfav_red[" << NT / 32 << "];\n"
+          << "    const long long cta = (long long)blockIdx.y * gridDim.x + blockIdx.x, nb = (long long)gridDim.x * gridDim.y;\n";
+        for (size_t k = 0; k < S.reds.size(); ++k) {
+            const bool mx = d.rules[S.f[S.reds[k]].rule].op == HFAV_OP_REDUCE_MAX;
+            const std::string op = mx ? "fmax(a, b)" : "a + b";
+            c << "    {\n"
+              << "        double a = racc" << k << ";\n"
+              << "        for (int o = 16; o > 0; o >>= 1) { const double b = __shfl_xor_sync(0xffffffffu, a, o); a = " << op
+              << "; }\n"
+              << "        __syncthreads();\n"
+              << "        if ((tid & 31) == 0) hfav_red[tid >> 5] = a;\n"
+              << "        __syncthreads();\n"
+              << "        if (tid == 0) {\n"
+              << "            for (int w = 1; w < " << NT / 32 << "; ++w) { const double b = hfav_red[w]; a = " << op << "; }\n"
+              << "            part[" << k << " * nb + cta] = a;\n"
+              << "        }\n"
+              << "    }\n";
+        }
+    }
+    c << "}\n";
     return c.str();
+}
+
+// the finalization after a part with reductions: one CTA combines each
+// reduction's partials in a fixed order (so runs are bitwise repeatable), then
+// evaluates, in FP64, the scalar rules whose inputs are now known
+std::string finalize_source(const hfav_plan_t* p, const std::vector<int>& red_fields, const std::vector<int>& rules) {
+    const Dag& d = p->dag;
+    std::ostringstream c;
+    c << prelude(true);
+    for (int r : rules) c << rule_fn(d.rules[r], "hfav_body" + std::to_string(r));
+    c << "extern \"C\" __global__ void __launch_bounds__(256) hfav_cg_finalize(const double* __restrict__ part, "
+      << "long long nparts, double* __restrict__ scal) {\n"
+      << "    __shared__ double red[8];\n"
+      << "    const int tid = threadIdx.x;\n";
+    for (size_t k = 0; k < red_fields.size(); ++k) {
+        const int f = red_fields[k];
+        int rr = -1;
+        for (size_t r = 0; r < d.rules.size(); ++r) if (d.rules[r].out[0] == f) rr = (int)r;
+        const bool mx = d.rules[rr].op == HFAV_OP_REDUCE_MAX;
+        const std::string op = mx ? "fmax(a, b)" : "a + b";
+        c << "    {\n"
+          << "        double a = " << (mx ? "__longlong_as_double(0xfff0000000000000ULL)" : "0.0") << ";\n"
+          << "        for (long long i = tid; i < nparts; i += 256) { const double b = part[" << k << " * nparts + i]; a = "
+          << op << "; }\n"
+          << "        for (int o = 16; o > 0; o >>= 1) { const double b = __shfl_xor_sync(0xffffffffu, a, o); a = " << op
+          << "; }\n"
+          << "        if ((tid & 31) == 0) red[tid >> 5] = a;\n"
+          << "        __syncthreads();\n"
+          << "        if (tid == 0) {\n"
+          << "            for (int w = 1; w < 8; ++w) { const double b = red[w]; a = " << op << "; }\n"
+          << "            scal[" << f << "] = a;\n"
+          << "        }\n"
+          << "        __syncthreads();\n"
+          << "    }\n";
+    }
+    if (!rules.empty()) {
+        c << "    if (tid == 0) {\n";
+        for (int r : rules) {
+            const Rule& R = d.rules[r];
+            c << "        scal[" << R.out[0] << "] = hfav_body" << r << "(";
+            for (size_t k = 0; k < R.in.size(); ++k) c << (k ? ", " : "") << "scal[" << R.in[k].field << "]";
+            c << ");\n";
+        }
+        c << "    }\n";
+    }
+    c << "}\n";
+    return c.str();
+}
+
+// The parts of a plan in execution order: the analysis's fusion groups
+// (fused) or single rules (unfused), scalar rules set aside for the
+// finalizations.  Also: after each part, the scalar rules it makes ready.
+struct Program {
+    std::vector<Part> parts;
+    std::vector<std::vector<int>> fin_reds;    // per part: rank-0 fields its reductions write
+    std::vector<std::vector<int>> fin_rules;   // per part: scalar rules evaluated after it
+};
+
+int make_program(const hfav_plan_t* p, bool fused, Program* G) {
+    const Dag& d = p->dag;
+    const int nr = (int)d.rules.size();
+    auto scalar_rule = [&](int r) {
+        for (const hfav_ref& x : d.rules[r].in) if (d.rank[x.field] != 0) return false;
+        return d.rank[d.rules[r].out[0]] == 0;
+    };
+    std::map<int, int> part_of_group;
+    std::vector<int> part_of(nr, -1);
+    std::vector<Part> parts;
+    for (int r : p->an.order) {
+        if (scalar_rule(r)) continue;
+        int k;
+        if (fused) {
+            auto it = part_of_group.find(p->an.rule_group[r]);
+            if (it == part_of_group.end()) {
+                k = (int)parts.size();
+                part_of_group[p->an.rule_group[r]] = k;
+                parts.push_back(Part());
+            } else {
+                k = it->second;
+            }
+        } else {
+            k = (int)parts.size();
+            parts.push_back(Part());
+        }
+        parts[k].rules.push_back(r);
+        part_of[r] = k;
+    }
+    // execution order: a part runs after every part whose grid fields or
+    // scalars it reads
+    std::vector<int> producer(d.n_fields, -1);
+    for (int r = 0; r < nr; ++r) producer[d.rules[r].out[0]] = r;
+    std::function<void(int, std::set<int>*)> sources = [&](int f, std::set<int>* out) {
+        const int r = producer[f];
+        if (r < 0) return;
+        if (part_of[r] >= 0) { out->insert(part_of[r]); return; }
+        for (const hfav_ref& x : d.rules[r].in) sources(x.field, out);   // a scalar rule: its inputs' parts
+    };
+    const int np = (int)parts.size();
+    std::vector<std::set<int>> deps(np);
+    for (int k = 0; k < np; ++k)
+        for (int r : parts[k].rules)
+            for (const hfav_ref& x : d.rules[r].in) {
+                std::set<int> src;
+                sources(x.field, &src);
+                for (int q : src) if (q != k) deps[k].insert(q);
+            }
+    std::vector<char> done(np, 0);
+    std::vector<char> scal_ready(d.n_fields, 0), scal_done(nr, 0);
+    for (int step = 0; step < np; ++step) {
+        int pick = -1;
+        for (int k = 0; k < np && pick < 0; ++k) {
+            if (done[k]) continue;
+            bool ok = true;
+            for (int q : deps[k]) if (!done[q]) ok = false;
+            if (ok) pick = k;
+        }
+        if (pick < 0) return set_error(HFAV_EUNSUPPORTED, "the DAG's parts form a cycle");
+        done[pick] = 1;
+        G->parts.push_back(parts[pick]);
+        std::vector<int> reds, rules;
+        for (int r : parts[pick].rules)
+            if (d.rank[d.rules[r].out[0]] == 0) { reds.push_back(d.rules[r].out[0]); scal_ready[d.rules[r].out[0]] = 1; }
+        for (bool more = true; more;) {
+            more = false;
+            for (int r : p->an.order) {
+                if (!scalar_rule(r) || scal_done[r]) continue;
+                bool ok = true;
+                for (const hfav_ref& x : d.rules[r].in) if (!scal_ready[x.field]) ok = false;
+                if (!ok) continue;
+                scal_done[r] = 1;
+                scal_ready[d.rules[r].out[0]] = 1;
+                rules.push_back(r);
+                more = true;
+            }
+        }
+        G->fin_reds.push_back(reds);
+        G->fin_rules.push_back(rules);
+    }
+    return HFAV_OK;
+}
+
+bool has_scalars(const hfav_plan_t* p) {
+    for (int rk : p->dag.rank) if (rk == 0) return true;
+    return false;
 }
 
 }  // namespace
 
 int plan_source(const hfav_plan_t* p, std::string* out) {
     if (p->pipeline != PIPE_CODEGEN) return set_error(HFAV_EUNSUPPORTED, "the plan runs no generated kernels");
-    if (p->sched.fusion != FUSE_UNFUSED) {
-        Stream S;
-        int rc = stream_geometry(p, p->sched, &S);
+    std::ostringstream o;
+    if (p->sched.fusion != FUSE_UNFUSED || has_scalars(p)) {
+        Program G;
+        int rc = make_program(p, p->sched.fusion != FUSE_UNFUSED, &G);
         if (rc) return rc;
-        *out = stream_source(p, S);
+        for (size_t k = 0; k < G.parts.size(); ++k) {
+            Stream S;
+            if ((rc = stream_geometry(p, p->sched, G.parts[k], &S))) return rc;
+            o << "// ---- kernel " << k << "\n" << stream_source(p, S, G.parts[k], "hfav_cg_part");
+            if (!G.fin_reds[k].empty() || !G.fin_rules[k].empty())
+                o << "// ---- kernel " << k << " finalize\n" << finalize_source(p, G.fin_reds[k], G.fin_rules[k]);
+        }
+        *out = o.str();
         return HFAV_OK;
     }
-    std::ostringstream o;
     for (int r : p->an.order) {
         const Rule& R = p->dag.rules[r];
         if (R.op != HFAV_OP_EXPR) continue;
         std::vector<int> fields;
         const std::vector<int> slot = rule_slots(R, &fields);
-        o << "// ---- rule " << r << "\n" << rule_source(p, R, slot, (int)fields.size());
+        o << "// ---- kernel rule " << r << "\n" << rule_source(p, R, slot, (int)fields.size());
     }
     *out = o.str();
     return HFAV_OK;
@@ -617,48 +868,108 @@ int launch_cg_rule(hfav_plan_t* p, const Rule& R, const std::vector<int>& ref_sl
 }
 
 int launch_codegen(hfav_plan_t* p, const Schedule& s, void* const* ax, void* const* go, cudaStream_t st) {
-    if (s.fusion == FUSE_UNFUSED) return launch_generic(p, ax, go, st);
+    const bool fused = s.fusion != FUSE_UNFUSED;
+    if (!fused && !has_scalars(p)) return launch_generic(p, ax, go, st);
     const Dag& d = p->dag;
     const hfav_grid& g = p->grids[0];
-    Stream S;
-    int rc = stream_geometry(p, s, &S);
-    if (rc) return rc;
-    cudaKernel_t k;
-    if ((rc = compile(stream_source(p, S), "hfav_cg_fused", &k))) return rc;
-    if (S.smem > 48 * 1024)
-        HFAV_CUDA(cudaFuncSetAttribute((const void*)k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem));
     const int nx = (int)g.extent[0], ny = (int)g.extent[1];
-    // rows per chunk: the wave count that costs least, each chunk paying the
-    // pipeline's fill (yhi - ylo steps beyond its rows)
-    int dev = 0, sms = 0, per_sm = 0;
+    Program G;
+    int rc = make_program(p, fused, &G);
+    if (rc) return rc;
+    int dev = 0, sms = 0;
     HFAV_CUDA(cudaGetDevice(&dev));
     HFAV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    HFAV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)k, S.NT, S.smem));
-    const int64_t resident = (int64_t)std::max(1, sms) * std::max(1, per_sm);
-    const int64_t strips = (nx + S.TXc - 1) / S.TXc;
-    const int fill = S.yhi - S.ylo;
-    int CH = ny;
-    double best = 1e300;
-    for (int64_t chunks = 1; chunks <= ny; chunks = chunks < 8 ? chunks + 1 : chunks * 5 / 4) {
-        const int ch = (int)((ny + chunks - 1) / chunks);
-        const int64_t ctas = strips * ((ny + ch - 1) / ch);
-        const double cost = (double)(ch + fill) * (double)((ctas + resident - 1) / resident);
-        if (cost < best) { best = cost; CH = ch; }
+    // plan arrays: the fields that cross between parts, over their footprint;
+    // the scalars (FP64, by field id); the reductions' partials
+    const size_t es = p->dtype == HFAV_F64 ? 8 : 4;
+    std::vector<GArr> cross(d.n_fields);
+    for (size_t k = 0; k < G.parts.size(); ++k) {
+        Stream S;
+        if ((rc = stream_geometry(p, s, G.parts[k], &S))) return rc;
+        for (int f : S.crosses) {
+            const hfav_field_info& fi = p->an.field[f];
+            GArr a;
+            const int64_t e0 = nx + fi.halo_lo[0] + fi.halo_hi[0], e1 = ny + fi.halo_lo[1] + fi.halo_hi[1];
+            a.pitch[0] = 1; a.pitch[1] = e0; a.pitch[2] = e0 * e1;
+            a.org[0] = fi.halo_lo[0]; a.org[1] = fi.halo_lo[1]; a.org[2] = 0;
+            a.ext[0] = nx; a.ext[1] = ny; a.ext[2] = 1;
+            a.wrap = 0;
+            void* ptr;
+            if ((rc = scratch(p, "codegen_f" + std::to_string(f), (size_t)(e0 * e1) * es, &ptr))) return rc;
+            a.p = ptr;
+            cross[f] = a;
+        }
     }
-    ArgPack A;
-    for (size_t a = 0; a < d.axioms.size(); ++a) add_array(A, caller_view_cg(p, ax[a]));
-    for (size_t a = 0; a < d.goals.size(); ++a) {
-        GArr y = caller_view_cg(p, go[a]);
-        y.wrap = 0;
-        add_array(A, y);
+    void* scal;
+    if ((rc = scratch(p, "codegen_scalars", sizeof(double) * d.n_fields, &scal))) return rc;
+    // every part's kernel, launch shape and partials first, so the partials
+    // buffer is sized once for the largest part
+    struct Launch { Stream S; cudaKernel_t kern, fin = nullptr; int CH; int64_t strips, nblocks; };
+    std::vector<Launch> L(G.parts.size());
+    size_t part_bytes = 0;
+    for (size_t k = 0; k < G.parts.size(); ++k) {
+        Launch& X = L[k];
+        if ((rc = stream_geometry(p, s, G.parts[k], &X.S))) return rc;
+        const Stream& S = X.S;
+        if ((rc = compile(stream_source(p, S, G.parts[k], "hfav_cg_part"), "hfav_cg_part", &X.kern))) return rc;
+        if (S.smem > 48 * 1024)
+            HFAV_CUDA(cudaFuncSetAttribute((const void*)X.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem));
+        if (!G.fin_reds[k].empty() || !G.fin_rules[k].empty())
+            if ((rc = compile(finalize_source(p, G.fin_reds[k], G.fin_rules[k]), "hfav_cg_finalize", &X.fin))) return rc;
+        // rows per chunk: the wave count that costs least, each chunk paying
+        // the pipeline's fill (yhi - ylo steps beyond its rows)
+        int per_sm = 0;
+        HFAV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)X.kern, S.NT, S.smem));
+        const int64_t resident = (int64_t)std::max(1, sms) * std::max(1, per_sm);
+        X.strips = (nx + S.TXc - 1) / S.TXc;
+        const int fill = S.yhi - S.ylo;
+        X.CH = ny;
+        double best = 1e300;
+        for (int64_t chunks = 1; chunks <= ny; chunks = chunks < 8 ? chunks + 1 : chunks * 5 / 4) {
+            const int ch = (int)((ny + chunks - 1) / chunks);
+            const int64_t ctas = X.strips * ((ny + ch - 1) / ch);
+            const double cost = (double)(ch + fill) * (double)((ctas + resident - 1) / resident);
+            if (cost < best) { best = cost; X.CH = ch; }
+        }
+        X.nblocks = X.strips * ((ny + X.CH - 1) / X.CH);
+        part_bytes = std::max(part_bytes, sizeof(double) * S.reds.size() * (size_t)X.nblocks);
     }
-    A.add(nx);
-    A.add(ny);
-    A.add(CH);
-    auto args = A.ptrs();
-    dim3 grd((unsigned)strips, (unsigned)((ny + CH - 1) / CH));
-    HFAV_CUDA(cudaLaunchKernel((const void*)k, grd, dim3(S.NT), args.data(), S.smem, st));
-    HFAV_LAUNCHED(p->rt, "codegen_fused", st);
+    void* part = nullptr;
+    if (part_bytes && (rc = scratch(p, "codegen_partials", part_bytes, &part))) return rc;
+    for (size_t k = 0; k < G.parts.size(); ++k) {
+        const Launch& X = L[k];
+        const Stream& S = X.S;
+        ArgPack A;
+        for (int f : S.loads) {
+            const auto ai = std::find(d.axioms.begin(), d.axioms.end(), f);
+            if (ai != d.axioms.end()) add_array(A, caller_view_cg(p, ax[ai - d.axioms.begin()]));
+            else add_array(A, cross[f]);
+        }
+        for (size_t q = 0; q < S.goals.size(); ++q) {
+            GArr y = caller_view_cg(p, go[S.goal_slot[q]]);
+            y.wrap = 0;
+            add_array(A, y);
+        }
+        for (int f : S.crosses) add_array(A, cross[f]);
+        A.add((const void*)scal);
+        A.add(part);
+        A.add(nx);
+        A.add(ny);
+        A.add(X.CH);
+        auto args = A.ptrs();
+        dim3 grd((unsigned)X.strips, (unsigned)((ny + X.CH - 1) / X.CH));
+        HFAV_CUDA(cudaLaunchKernel((const void*)X.kern, grd, dim3(S.NT), args.data(), S.smem, st));
+        HFAV_LAUNCHED(p->rt, fused ? "codegen_fused" : "codegen_rule", st);
+        if (X.fin) {
+            ArgPack B;
+            B.add((const void*)part);
+            B.add((long long)X.nblocks);
+            B.add(scal);
+            auto bargs = B.ptrs();
+            HFAV_CUDA(cudaLaunchKernel((const void*)X.fin, dim3(1), dim3(256), bargs.data(), 0, st));
+            HFAV_LAUNCHED(p->rt, "codegen_finalize", st);
+        }
+    }
     return HFAV_OK;
 }
 

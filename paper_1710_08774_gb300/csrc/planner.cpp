@@ -37,7 +37,7 @@ bool op_known(int op) {
         case HFAV_OP_STENCIL_LINEAR: case HFAV_OP_GRADMAG_HALF: case HFAV_OP_SQUASH:
         case HFAV_OP_GENERIC: case HFAV_OP_LIMFLUX: case HFAV_OP_DIFFUSE: case HFAV_OP_EXPR: case HFAV_OP_CONSTOPRIM: case HFAV_OP_EOS: case HFAV_OP_SLOPE:
         case HFAV_OP_TRACE: case HFAV_OP_QLEFTRIGHT: case HFAV_OP_RIEMANN: case HFAV_OP_CMPFLX:
-        case HFAV_OP_UPDATE: case HFAV_OP_CFL_DT: case HFAV_OP_REDUCE_SUM: case HFAV_OP_BROADCAST:
+        case HFAV_OP_UPDATE: case HFAV_OP_CFL_DT: case HFAV_OP_REDUCE_SUM: case HFAV_OP_REDUCE_MAX: case HFAV_OP_BROADCAST:
             return true;
         default:
             return false;
@@ -840,18 +840,43 @@ int recognise(hfav_plan_t* p) {
     if (recognise_godunov(p)) return HFAV_OK;
     if (recognise_cosmo(p)) return HFAV_OK;
     // generic DAGs of the stencil catalogue run unfused, one kernel per rule;
-    // DAGs with user rule bodies get generated kernels
-    bool expr = false;
-    for (auto& r : p->dag.rules) {
-        if (r.op == HFAV_OP_EXPR) { expr = true; continue; }
+    // DAGs with user rule bodies or reductions get generated kernels.  Fields
+    // are grid fields (rank ndim) or scalars (rank 0): a scalar comes from a
+    // reduction of one grid field or from a rule body over scalars, and rule
+    // bodies over the grid read scalars at offset 0 (broadcasts, Sec. 3.4)
+    const Dag& d = p->dag;
+    bool expr = false, scal = false;
+    auto grid = [&](int f) { return d.rank[f] == d.ndim; };
+    for (auto& r : d.rules) {
+        if (r.out.size() != 1) return HFAV_EUNSUPPORTED;
+        const int o = r.out[0];
+        if (r.op == HFAV_OP_EXPR) {
+            expr = true;
+            for (auto& x : r.in) {
+                if (grid(x.field) && !grid(o)) return HFAV_EUNSUPPORTED;   // grid -> scalar only by a reduction
+                if (!grid(x.field) && (x.off[0] || x.off[1] || x.off[2])) return HFAV_EUNSUPPORTED;
+            }
+            continue;
+        }
+        if (r.op == HFAV_OP_REDUCE_SUM || r.op == HFAV_OP_REDUCE_MAX) {
+            if (r.in.size() != 1 || !grid(r.in[0].field) || d.rank[o] != 0) return HFAV_EUNSUPPORTED;
+            scal = true;
+            continue;
+        }
         if (r.op != HFAV_OP_STENCIL_LINEAR && r.op != HFAV_OP_GRADMAG_HALF && r.op != HFAV_OP_SQUASH &&
             r.op != HFAV_OP_LIMFLUX && r.op != HFAV_OP_DIFFUSE)
             return HFAV_EUNSUPPORTED;
-        if (r.out.size() != 1) return HFAV_EUNSUPPORTED;
+        for (auto& x : r.in) if (!grid(x.field)) return HFAV_EUNSUPPORTED;
+        if (!grid(o)) return HFAV_EUNSUPPORTED;
     }
-    for (int rk : p->dag.rank)
-        if (rk != p->dag.ndim) return expr ? HFAV_EUNSUPPORTED : HFAV_OK;
-    if (expr) p->pipeline = PIPE_CODEGEN;
+    for (int f = 0; f < d.n_fields; ++f) {
+        if (grid(f)) continue;
+        if (d.rank[f] != 0 || !scal) return expr ? HFAV_EUNSUPPORTED : HFAV_OK;
+        for (int a : d.axioms) if (a == f) return HFAV_EUNSUPPORTED;
+        for (int g : d.goals) if (g == f) return HFAV_EUNSUPPORTED;
+    }
+    if (scal && d.ndim != 2) return HFAV_EUNSUPPORTED;
+    if (expr || scal) p->pipeline = PIPE_CODEGEN;
     return HFAV_OK;
 }
 

@@ -23,7 +23,7 @@ ERRORS = {-1: "EINVAL", -2: "ECYCLE", -3: "EPRODUCER", -4: "EMISSING", -5: "EHAL
 HFAV_F64, HFAV_F32 = 0, 1
 HFAV_BC_PERIODIC, HFAV_BC_HALO_GIVEN = 0, 1
 OP = dict(STENCIL_LINEAR=1, GRADMAG_HALF=2, SQUASH=3, GENERIC=4, LIMFLUX=5, DIFFUSE=6, EXPR=7, CONSTOPRIM=10, EOS=11, SLOPE=12, TRACE=13,
-          QLEFTRIGHT=14, RIEMANN=15, CMPFLX=16, UPDATE=17, CFL_DT=20, REDUCE_SUM=21, BROADCAST=22)
+          QLEFTRIGHT=14, RIEMANN=15, CMPFLX=16, UPDATE=17, CFL_DT=20, REDUCE_SUM=21, BROADCAST=22, REDUCE_MAX=23)
 STORAGE = ["axiom", "goal", "hbm", "rolling", "scalar"]
 N_FEATURES = 16
 
@@ -268,6 +268,25 @@ def chain2d_expr_dag():
     D.rule("EXPR", [("L", (1, 0)), ("L", (-1, 0)), ("L", (0, 1)), ("L", (0, -1))], ["G"],
            expr="sqrt((in0 - in1) * (in0 - in1) + (in2 - in3) * (in2 - in3)) * (T)0.5")
     D.rule("EXPR", ["G"], ["out"], expr="in0 / (1 + in0)")
+    D.axiom("u")
+    D.goal("out")
+    return D
+
+
+def normalization_dag():
+    """The normalization example (Sec. 5.2) as rule bodies: flux = u(i+1) - u(i),
+    diff = flux(i) - flux(i-1), the norm accumulation acc = sum of diff^2 (a
+    reduction), its root, out = diff / root (a broadcast).  The reduction feeding
+    the broadcast splits the DAG into two nests."""
+    D = DagSpec(2, stream_axis=1)
+    D.rule("EXPR", [("u", (1, 0)), ("u", (0, 0))], ["flux"], expr="in0 - in1")
+    D.rule("EXPR", [("flux", (0, 0)), ("flux", (-1, 0))], ["diff"], expr="in0 - in1")
+    D.rule("EXPR", ["diff"], ["sq"], expr="in0 * in0")
+    D.field("acc", rank=0)
+    D.field("root", rank=0)
+    D.rule("REDUCE_SUM", ["sq"], ["acc"])
+    D.rule("EXPR", ["acc"], ["root"], expr="sqrt(in0)")
+    D.rule("EXPR", ["diff", "root"], ["out"], expr="in0 / in1")
     D.axiom("u")
     D.goal("out")
     return D

@@ -97,3 +97,67 @@ def pointwise_dag():
         dict(out="g", refs=[("t3", z)], c="in0 / (1 + fabs(in0))", fn=lambda a: a / (1 + np.abs(a)), params=[]),
     ]
     return rules, ["a0", "a1"], ["g"]
+
+
+# scalar finalization bodies (C, numpy, n_in, parameter ranges) and broadcast
+# consumers (a grid field and a scalar)
+SCALAR_BODIES = [
+    ("sqrt(fabs(in0) + p0)", lambda a, p0: np.sqrt(np.abs(a) + p0), 1, [(0.5, 2.0)]),
+    ("in0 * p0 + 1", lambda a, p0: a * p0 + 1, 1, [(-0.01, 0.01)]),
+]
+BROADCAST_BODIES = [
+    ("in0 / in1", lambda a, b: a / b, [(0.0, 0.0)]),
+    ("in0 - p0 * in1", lambda a, b, p0: a - p0 * b, [(0.001, 0.01)]),
+]
+
+
+def random_reduce_dag(seed, n_grid=4):
+    """A random grid DAG (as random_dag), reductions (sum or max) of two of its
+    fields, a scalar rule on each, and broadcast consumers: a split between a
+    nest that reduces and one that reads the scalars.  Returns rules in the
+    tests' dict form with `op` set for reductions, the axioms and goals."""
+    rng = np.random.default_rng(1000 + seed)
+    rules, axioms, _ = random_dag(2, n_grid, seed)
+    grid_fields = [r["out"] for r in rules]
+    extra = []
+    for k, f in enumerate(rng.choice(grid_fields, size=2, replace=False)):
+        op = "sum" if k == 0 else "max"
+        extra.append(dict(out=f"acc{k}", refs=[(str(f), (0, 0, 0))], op=op))
+        c, fn, _, prange = SCALAR_BODIES[k]
+        params = [float(rng.uniform(lo, hi)) for lo, hi in prange]
+        extra.append(dict(out=f"sc{k}", refs=[(f"acc{k}", (0, 0, 0))], c=c, fn=fn, params=params))
+    for k in range(2):
+        c, fn, prange = BROADCAST_BODIES[k]
+        params = [float(rng.uniform(lo, hi)) for lo, hi in prange if hi > 0]
+        src = str(rng.choice(grid_fields))
+        off = tuple(int(v) for v in rng.integers(-1, 2, size=2)) + (0,)
+        extra.append(dict(out=f"b{k}", refs=[(src, off), (f"sc{k}", (0, 0, 0))], c=c, fn=fn, params=params))
+    rules = rules + extra
+    read = {f for r in rules for f, _ in r["refs"]}
+    goals = [r["out"] for r in rules if r["out"] not in read and not r["out"].startswith(("acc", "sc"))]
+    return rules, axioms, goals
+
+
+def to_spec_reduce(rules, axioms, goals):
+    """DagSpec of random_reduce_dag's rules (scalars rank 0)."""
+    from paper_1710_08774_gb300 import hfav as H
+    D = H.DagSpec(2)
+    for a in axioms:
+        D.field(a)
+    for r in rules:
+        if r["out"].startswith(("acc", "sc")):
+            D.field(r["out"], rank=0)
+    for r in rules:
+        refs = [(f, off[:2]) for f, off in r["refs"]]
+        if "op" in r:
+            D.rule("REDUCE_SUM" if r["op"] == "sum" else "REDUCE_MAX", refs, [r["out"]])
+        else:
+            D.rule("EXPR", refs, [r["out"]], params=r["params"], expr=r["c"])
+    D.axiom(*axioms)
+    D.goal(*goals)
+    return D
+
+
+def to_oracle_reduce(rules):
+    return [(r["out"], r["refs"], r["op"], []) if "op" in r else (r["out"], r["refs"], r["fn"], r["params"])
+            for r in rules]

@@ -38,6 +38,11 @@ def _compile(L, src):
     return rc, log.value.decode(errors="replace")
 
 
+def _units(src):
+    """The separately compiled units of a plan's source (each after a '// ---- kernel' line)."""
+    return [u.split("\n", 1)[1] for u in src.split("// ---- kernel ")[1:]]
+
+
 def test_expr_dag_plans_onto_generated_kernels():
     rules, axioms, goals = X.random_dag(2, 5, 0)
     P = H.Plan(X.to_spec(rules, axioms, goals, 2), [_grid((40, 30), 6)])
@@ -96,10 +101,9 @@ def test_generated_source_compiles_with_nvrtc(dtype, seed):
         src = P.source()
         for body in {r["c"] for r in rules}:
             assert body in src
-        units = src.split("// ---- rule ")[1:] if sched.startswith("unfused") else [src]
+        units = _units(src)
         assert units
         for u in units:
-            u = u.split("\n", 1)[1] if sched.startswith("unfused") else u
             rc, log = _compile(L, u)
             assert rc == 0, log
 
@@ -113,10 +117,11 @@ def test_source_is_deterministic_and_mixes_catalogue_ops():
     D.axiom("u"); D.goal("o")
     a = H.Plan(D, [_grid((64, 64), 2)]).source()
     b = H.Plan(D, [_grid((64, 64), 2)]).source()
-    assert a == b and "hfav_cg_fused" in a
+    assert a == b and "hfav_cg_part" in a
     L = _nvrtc()
-    rc, log = _compile(L, a)
-    assert rc == 0, log
+    for u in _units(a):
+        rc, log = _compile(L, u)
+        assert rc == 0, log
 
 
 def test_pointwise_stages_are_inlined_and_the_goal_written_directly():
@@ -132,5 +137,6 @@ def test_pointwise_stages_are_inlined_and_the_goal_written_directly():
     assert tiles == {"a0", "a1", "t2"}
     assert "hfav_body1(hfav_body0(" in src
     L = _nvrtc()
-    rc, log = _compile(L, src)
-    assert rc == 0, log
+    for u in _units(src):
+        rc, log = _compile(L, u)
+        assert rc == 0, log

@@ -149,3 +149,14 @@ def test_normalization_invariants():
     q = np.broadcast_to((np.arange(24.0) ** 2), (16, 24)).copy()
     diff = E.evaluate(E.normalization_rules(), {"u": q})["diff"]
     assert np.all(diff[:, 1:-1] == 2)
+
+
+def test_padded_evaluation_reduces_over_the_interior():
+    """Halo-given grids: the reduction sees only the interior (the halo holds
+    a value that would change every sum); the broadcast reaches every cell."""
+    rng = np.random.default_rng(5)
+    core = rng.uniform(-1, 1, (6, 9))
+    pad = np.pad(core, 2, constant_values=100.0)
+    rules = [("s", [("u", (0, 0))], "sum", []), ("o", [("u", (0, 0)), ("s", (0, 0))], lambda a, b: a - b, [])]
+    got = E.evaluate_padded(rules, {"u": pad}, 2, ["o"])["o"]
+    assert np.allclose(got, core - core.sum(), rtol=0, atol=1e-13)
