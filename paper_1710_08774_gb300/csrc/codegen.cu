@@ -167,6 +167,7 @@ std::string rule_expr(const Rule& R) {
             e << ") * (T)0.5)";
             break;
         case HFAV_OP_SQUASH: e << "(in0 / ((T)1 + in0))"; break;
+        case HFAV_OP_REDUCE_SUM: case HFAV_OP_REDUCE_MAX: e << "in0"; break;   // the value reduced
         case HFAV_OP_LIMFLUX: e << "hfav_limflux(in0, in1, in2, in3)"; break;
         case HFAV_OP_DIFFUSE: e << "(in0 - " << lit(R.params.empty() ? 0.0 : R.params[0]) << " * ((in2 - in1) + (in4 - in3)))"; break;
         default: e << "(" << R.expr << ")"; break;   // HFAV_OP_EXPR

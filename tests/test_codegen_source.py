@@ -140,3 +140,24 @@ def test_pointwise_stages_are_inlined_and_the_goal_written_directly():
     for u in _units(src):
         rc, log = _compile(L, u)
         assert rc == 0, log
+
+
+@pytest.mark.parametrize("dtype", [H.HFAV_F64, H.HFAV_F32])
+@pytest.mark.parametrize("schedule", ["full:smem:32x4", "unfused:hbm:32x4"])
+def test_reduction_sources_compile_with_nvrtc(dtype, schedule):
+    """The normalization example and random DAGs with reductions: per-part
+    kernels and finalizations all compile; the fused form has 2 grid kernels
+    and 1 finalization for the normalization example, the unfused form 5 and 1."""
+    L = _nvrtc()
+    P = H.Plan(H.normalization_dag(), [_grid((64, 48), 1)], dtype, H.HFAV_BC_PERIODIC, schedule)
+    src = P.source()
+    heads = [l for l in src.splitlines() if l.startswith("// ---- kernel")]
+    assert len(heads) == (3 if schedule.startswith("full") else 6)
+    assert sum(h.endswith("finalize") for h in heads) == 1
+    for seed in range(3):
+        rules, axioms, goals = X.random_reduce_dag(seed)
+        Q = H.Plan(X.to_spec_reduce(rules, axioms, goals), [_grid((64, 48), 6)], dtype, H.HFAV_BC_PERIODIC, schedule)
+        src += "// ---- kernel x\n" + Q.source()
+    for u in _units(src):
+        rc, log = _compile(L, u)
+        assert rc == 0, log
