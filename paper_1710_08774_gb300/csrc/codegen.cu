@@ -913,8 +913,9 @@ int launch_codegen(hfav_plan_t* p, const Schedule& s, void* const* ax, void* con
         if ((rc = stream_geometry(p, s, G.parts[k], &X.S))) return rc;
         const Stream& S = X.S;
         if ((rc = compile(stream_source(p, S, G.parts[k], "hfav_cg_part"), "hfav_cg_part", &X.kern))) return rc;
+        // a library kernel takes its attributes per device
         if (S.smem > 48 * 1024)
-            HFAV_CUDA(cudaFuncSetAttribute((const void*)X.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem));
+            HFAV_CUDA(cudaKernelSetAttributeForDevice(X.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem, dev));
         if (!G.fin_reds[k].empty() || !G.fin_rules[k].empty())
             if ((rc = compile(finalize_source(p, G.fin_reds[k], G.fin_rules[k]), "hfav_cg_finalize", &X.fin))) return rc;
         // rows per chunk: the wave count that costs least, each chunk paying
