@@ -463,13 +463,17 @@ int stream_geometry_v(const hfav_plan_t* p, const Schedule& s, const Part& P, in
 
 // each thread takes V columns of a row (tid, tid + NT, ...): the per-step
 // work (row checks, fetch set-up, barrier) is shared by V cells.  V = 4 (FP32)
-// or 2 (FP64), halved while the rings need more than 96 KB of shared memory.
+// or 2 (FP64), halved while the rings need more than kSmemDefault of shared
+// memory (the default launch limit, less the kernel's static reduction
+// buffer); larger rings take an opt-in limit.
+constexpr size_t kSmemDefault = 47 * 1024;
+
 int stream_geometry(const hfav_plan_t* p, const Schedule& s, const Part& P, Stream* S) {
     int rc = HFAV_EUNSUPPORTED;
     for (int V = p->dtype == HFAV_F64 ? 2 : 4; V >= 1; V /= 2) {
         *S = Stream();
         rc = stream_geometry_v(p, s, P, V, S);
-        if (rc == HFAV_OK && S->smem <= 96 * 1024) return HFAV_OK;
+        if (rc == HFAV_OK && S->smem <= kSmemDefault) return HFAV_OK;
     }
     return rc;
 }
@@ -914,8 +918,9 @@ int launch_codegen(hfav_plan_t* p, const Schedule& s, void* const* ax, void* con
         const Stream& S = X.S;
         if ((rc = compile(stream_source(p, S, G.parts[k], "hfav_cg_part"), "hfav_cg_part", &X.kern))) return rc;
         // a library kernel takes its attributes per device
-        if (S.smem > 48 * 1024)
-            HFAV_CUDA(cudaKernelSetAttributeForDevice(X.kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.smem, dev));
+        if (S.smem > kSmemDefault)
+            HFAV_CUDA(cudaKernelSetAttributeForDevice(X.kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                      (int)S.smem + 1024, dev));
         if (!G.fin_reds[k].empty() || !G.fin_rules[k].empty())
             if ((rc = compile(finalize_source(p, G.fin_reds[k], G.fin_rules[k]), "hfav_cg_finalize", &X.fin))) return rc;
         // rows per chunk: the wave count that costs least, each chunk paying

@@ -204,3 +204,29 @@ def test_chain_as_rule_bodies_16384_f32_full_size_sampled(schedule):
     ref = np.array([oracle.chain2d(np.pad(_block_wrap(interior, p, 2).astype(np.float64), 2))[2][2, 2] for p in pts])
     assert np.all(np.isfinite(got))
     assert normwise(got, ref) <= 2e-5
+
+
+def test_rings_above_the_default_shared_memory_limit():
+    """A DAG whose rings need more than 48 KB even at one column per thread
+    (FP64, 256 threads, many wide fields) runs with the opt-in limit."""
+    D = H.DagSpec(2)
+    prev = "u"
+    for k in range(7):
+        refs = [(prev, (dx, dy)) for dx in (-2, 0, 2) for dy in (-2, 0, 2)]
+        D.rule("EXPR", refs, [f"t{k}"], params=[0.1],
+               expr="p0 * (in0 + in1 + in2 + in3 + in5 + in6 + in7 + in8) + (1 - 8 * p0) * in4")
+        prev = f"t{k}"
+    D.axiom("u"); D.goal(prev)
+    rng = np.random.default_rng(8)
+    core = rng.uniform(-1, 1, (200, 300))
+    u = np.full((228, 328), np.nan)
+    u[14:-14, 14:-14] = core
+    (got,), _ = run_plan(D, [u], 14, "full:smem:128x2")
+    rules = []
+    prev = "u"
+    for k in range(7):
+        refs = [(prev, (dx, dy)) for dx in (-2, 0, 2) for dy in (-2, 0, 2)]
+        rules.append((f"t{k}", refs, lambda *a: 0.1 * (sum(a[:4]) + sum(a[5:9])) + (1 - 0.8) * a[4], []))
+        prev = f"t{k}"
+    ref = E.evaluate(rules, {"u": core})[prev]
+    assert normwise(got, ref) <= 1e-12
