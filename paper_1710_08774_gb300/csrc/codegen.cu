@@ -327,6 +327,7 @@ struct SField {
 };
 
 struct Stream {
+    bool pointwise = false;                          // no offsets, no halos: no rings
     int NT = 0, V = 1, TXc = 0, ylo = 0, yhi = 0;   // steps [ylo, jn + yhi)
     int U = 1;                                      // steps per unrolled pass
     size_t smem = 0;
@@ -380,6 +381,21 @@ int stream_geometry_v(const hfav_plan_t* p, const Schedule& s, const Part& P, in
             S->goal_slot.push_back((int)(g - d.goals.begin()));
         }
         if (outside[f]) { F.cross = (int)S->crosses.size(); S->crosses.push_back(f); }
+    }
+    // a pointwise part (every read at offset 0, every field without a halo)
+    // needs no rings: each cell is loaded, computed and stored in registers
+    bool pw = hxmax == 0;
+    for (int f = 0; f < nf; ++f)
+        if (involved[f] && (S->f[f].hylo || S->f[f].hyhi || (!S->f[f].scalar && !off0[f] && readers[f]))) pw = false;
+    if (pw) {
+        S->pointwise = true;
+        S->TXc = S->V * S->NT;
+        for (int f = 0; f < nf; ++f) {
+            SField& F = S->f[f];
+            F.w = S->TXc;
+            F.inl = F.rule >= 0 && !F.scalar && F.goal < 0 && F.cross < 0;   // every stored value goes to memory
+        }
+        return HFAV_OK;
     }
     S->TXc = S->V * S->NT - hxmax;
     if (S->TXc < 32) return set_error(HFAV_EUNSUPPORTED, "this DAG's footprint is too wide for the tile; use a wider one");
@@ -478,7 +494,101 @@ int stream_geometry(const hfav_plan_t* p, const Schedule& s, const Part& P, Stre
     return rc;
 }
 
+// a pointwise part: each CTA row loop loads, computes and stores its cells
+// in registers (V columns per thread), no shared memory, no barrier
+std::string pointwise_source(const hfav_plan_t* p, const Stream& S, const Part& P, const std::string& name) {
+    const Dag& d = p->dag;
+    const int NT = S.NT, V = S.V, TXc = S.TXc;
+    std::ostringstream c;
+    c << prelude(p->dtype == HFAV_F64);
+    for (int r : p->an.order)
+        if (in_part(P, r)) c << rule_fn(d.rules[r], "hfav_body" + std::to_string(r));
+    c << "extern \"C\" __global__ void __launch_bounds__(" << NT << ") " << name << "(";
+    for (size_t a = 0; a < S.loads.size(); ++a) c << array_params("x" + std::to_string(a), false) << ", ";
+    for (size_t a = 0; a < S.goals.size(); ++a) c << array_params("y" + std::to_string(a), true) << ", ";
+    for (size_t a = 0; a < S.crosses.size(); ++a) c << array_params("z" + std::to_string(a), true) << ", ";
+    c << "const double* __restrict__ scal, double* __restrict__ part, int nx, int ny, int CH) {\n"
+      << "    const int tid = threadIdx.x, i0 = blockIdx.x * " << TXc << ", j0 = blockIdx.y * CH;\n"
+      << "    const int jn = min(CH, ny - j0);\n";
+    for (int f : S.scalars) c << "    const T sv" << f << " = (T)scal[" << f << "];\n";
+    for (size_t k = 0; k < S.reds.size(); ++k)
+        c << "    double racc" << k << " = "
+          << (d.rules[S.f[S.reds[k]].rule].op == HFAV_OP_REDUCE_MAX ? "__longlong_as_double(0xfff0000000000000ULL)" : "0.0")
+          << ";\n";
+    c << "    #pragma unroll 1\n"
+      << "    for (int r = 0; r < jn; ++r) {\n"
+      << "        const int gj = j0 + r;\n";
+    for (size_t a = 0; a < S.loads.size(); ++a) {
+        const std::string x = "x" + std::to_string(a);
+        c << "        const T* const " << x << "r = " << x << " + (long long)(gj + " << x << "_o1) * " << x << "_p1 + " << x
+          << "_o0 + i0 + tid;\n";
+    }
+    for (int kind = 0; kind < 2; ++kind)
+        for (size_t a = 0; a < (kind ? S.crosses.size() : S.goals.size()); ++a) {
+            const std::string y = (kind ? "z" : "y") + std::to_string(a);
+            c << "        T* const " << y << "r = " << y << " + (long long)(gj + " << y << "_o1) * " << y << "_p1 + " << y
+              << "_o0 + i0 + tid;\n";
+        }
+    for (int v = 0; v < V; ++v) {
+        c << "        if (i0 + tid + " << v * NT << " < nx) {\n";
+        std::function<std::string(int)> read = [&](int g) -> std::string {
+            const SField& G = S.f[g];
+            if (G.scalar) return "sv" + std::to_string(g);
+            if (G.load >= 0) return "x" + std::to_string(G.load) + "r[" + std::to_string(v * NT) + "]";
+            const Rule& Q = d.rules[G.rule];
+            std::string val = "hfav_body" + std::to_string(G.rule) + "(";
+            for (size_t q = 0; q < Q.in.size(); ++q) val += (q ? ", " : "") + read(Q.in[q].field);
+            return val + ")";
+        };
+        for (int r : p->an.order) {
+            if (!in_part(P, r)) continue;
+            const Rule& R = d.rules[r];
+            const int f = R.out[0];
+            const SField& F = S.f[f];
+            if (F.red >= 0) {
+                const std::string acc = "racc" + std::to_string(F.red);
+                c << "            { const double in0 = (double)" << read(R.in[0].field) << ";\n"
+                  << "              " << acc << " = "
+                  << (R.op == HFAV_OP_REDUCE_MAX ? "fmax(" + acc + ", in0)" : acc + " + in0") << "; }\n";
+                continue;
+            }
+            if (F.goal < 0 && F.cross < 0) continue;   // inlined into its readers
+            c << "            { const T v = hfav_body" << r << "(";
+            for (size_t q = 0; q < R.in.size(); ++q) c << (q ? ", " : "") << read(R.in[q].field);
+            c << ");\n";
+            if (F.goal >= 0) c << "              y" << F.goal << "r[" << v * NT << "] = v;\n";
+            if (F.cross >= 0) c << "              z" << F.cross << "r[" << v * NT << "] = v;\n";
+            c << "            }\n";
+        }
+        c << "        }\n";
+    }
+    c << "    }\n";
+    if (!S.reds.empty()) {
+        c << "    __shared__ double hfav_red[" << NT / 32 << "];\n"
+          << "    const long long cta = (long long)blockIdx.y * gridDim.x + blockIdx.x, nb = (long long)gridDim.x * gridDim.y;\n";
+        for (size_t k = 0; k < S.reds.size(); ++k) {
+            const bool mx = d.rules[S.f[S.reds[k]].rule].op == HFAV_OP_REDUCE_MAX;
+            const std::string op = mx ? "fmax(a, b)" : "a + b";
+            c << "    {\n"
+              << "        double a = racc" << k << ";\n"
+              << "        for (int o = 16; o > 0; o >>= 1) { const double b = __shfl_xor_sync(0xffffffffu, a, o); a = " << op
+              << "; }\n"
+              << "        __syncthreads();\n"
+              << "        if ((tid & 31) == 0) hfav_red[tid >> 5] = a;\n"
+              << "        __syncthreads();\n"
+              << "        if (tid == 0) {\n"
+              << "            for (int w = 1; w < " << NT / 32 << "; ++w) { const double b = hfav_red[w]; a = " << op << "; }\n"
+              << "            part[" << k << " * nb + cta] = a;\n"
+              << "        }\n"
+              << "    }\n";
+        }
+    }
+    c << "}\n";
+    return c.str();
+}
+
 std::string stream_source(const hfav_plan_t* p, const Stream& S, const Part& P, const std::string& name) {
+    if (S.pointwise) return pointwise_source(p, S, P, name);
     const Dag& d = p->dag;
     const bool f64 = p->dtype == HFAV_F64;
     const int NT = S.NT, TXc = S.TXc, V = S.V;
