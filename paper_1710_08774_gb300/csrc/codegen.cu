@@ -311,6 +311,31 @@ struct Part {
     std::vector<int> rules;   // grid rules and reductions, topological order
 };
 
+// A reduction's per-thread accumulator.  FP64 plans add in FP64.  FP32 plans
+// keep an FP32 sum with Neumaier's compensation (Neumaier 1974, the improved
+// Kahan-Babuska summation: a second FP32 term collects each addition's
+// rounding error) -- FP64 adds run at a small fraction of the FP32 rate on
+// this part -- and the maximum in FP32 (exact); each thread's result then
+// joins the CTA's FP64 partial.
+std::string red_decl(int k, bool mx, bool f64) {
+    const std::string K = std::to_string(k);
+    if (mx) return "    T racc" + K + " = (T)__longlong_as_double(0xfff0000000000000ULL);\n";
+    if (f64) return "    double racc" + K + " = 0.0;\n";
+    return "    float racc" + K + " = 0.f, rcmp" + K + " = 0.f;\n";
+}
+std::string red_add(int k, bool mx, bool f64, const std::string& x) {
+    const std::string K = std::to_string(k), a = "racc" + K;
+    if (mx) return a + " = fmax(" + a + ", " + x + ");";
+    if (f64) return a + " = " + a + " + " + x + ";";
+    return "{ const float hx = " + x + ", ht = " + a + " + hx; rcmp" + K + " += fabsf(" + a + ") >= fabsf(hx) ? (" + a +
+           " - ht) + hx : (hx - ht) + " + a + "; " + a + " = ht; }";
+}
+std::string red_final(int k, bool mx, bool f64) {
+    const std::string K = std::to_string(k);
+    if (mx || f64) return "(double)racc" + K;
+    return "((double)racc" + K + " + (double)rcmp" + K + ")";
+}
+
 struct SField {
     int hxlo = 0, hxhi = 0, hylo = 0, hyhi = 0;
     int w = 0;          // ring row width: TXc + hxlo + hxhi
@@ -498,9 +523,10 @@ int stream_geometry(const hfav_plan_t* p, const Schedule& s, const Part& P, Stre
 // in registers (V columns per thread), no shared memory, no barrier
 std::string pointwise_source(const hfav_plan_t* p, const Stream& S, const Part& P, const std::string& name) {
     const Dag& d = p->dag;
+    const bool f64 = p->dtype == HFAV_F64;
     const int NT = S.NT, V = S.V, TXc = S.TXc;
     std::ostringstream c;
-    c << prelude(p->dtype == HFAV_F64);
+    c << prelude(f64);
     for (int r : p->an.order)
         if (in_part(P, r)) c << rule_fn(d.rules[r], "hfav_body" + std::to_string(r));
     c << "extern \"C\" __global__ void __launch_bounds__(" << NT << ") " << name << "(";
@@ -512,9 +538,7 @@ std::string pointwise_source(const hfav_plan_t* p, const Stream& S, const Part& 
       << "    const int jn = min(CH, ny - j0);\n";
     for (int f : S.scalars) c << "    const T sv" << f << " = (T)scal[" << f << "];\n";
     for (size_t k = 0; k < S.reds.size(); ++k)
-        c << "    double racc" << k << " = "
-          << (d.rules[S.f[S.reds[k]].rule].op == HFAV_OP_REDUCE_MAX ? "__longlong_as_double(0xfff0000000000000ULL)" : "0.0")
-          << ";\n";
+        c << red_decl((int)k, d.rules[S.f[S.reds[k]].rule].op == HFAV_OP_REDUCE_MAX, f64);
     c << "    #pragma unroll 1\n"
       << "    for (int r = 0; r < jn; ++r) {\n"
       << "        const int gj = j0 + r;\n";
@@ -546,10 +570,8 @@ std::string pointwise_source(const hfav_plan_t* p, const Stream& S, const Part& 
             const int f = R.out[0];
             const SField& F = S.f[f];
             if (F.red >= 0) {
-                const std::string acc = "racc" + std::to_string(F.red);
-                c << "            { const double in0 = (double)" << read(R.in[0].field) << ";\n"
-                  << "              " << acc << " = "
-                  << (R.op == HFAV_OP_REDUCE_MAX ? "fmax(" + acc + ", in0)" : acc + " + in0") << "; }\n";
+                c << "            { const T in0 = " << read(R.in[0].field) << ";\n"
+                  << "              " << red_add(F.red, R.op == HFAV_OP_REDUCE_MAX, f64, "in0") << " }\n";
                 continue;
             }
             if (F.goal < 0 && F.cross < 0) continue;   // inlined into its readers
@@ -570,7 +592,7 @@ std::string pointwise_source(const hfav_plan_t* p, const Stream& S, const Part& 
             const bool mx = d.rules[S.f[S.reds[k]].rule].op == HFAV_OP_REDUCE_MAX;
             const std::string op = mx ? "fmax(a, b)" : "a + b";
             c << "    {\n"
-              << "        double a = racc" << k << ";\n"
+              << "        double a = " << red_final((int)k, mx, f64) << ";\n"
               << "        for (int o = 16; o > 0; o >>= 1) { const double b = __shfl_xor_sync(0xffffffffu, a, o); a = " << op
               << "; }\n"
               << "        __syncthreads();\n"
@@ -627,9 +649,7 @@ std::string stream_source(const hfav_plan_t* p, const Stream& S, const Part& P, 
         if (!S.f[f].inl && S.f[f].W > 0) c << "    T* s" << f << " = (T*)(smem + " << S.f[f].off << ");\n";
     for (int f : S.scalars) c << "    const T sv" << f << " = (T)scal[" << f << "];\n";
     for (size_t k = 0; k < S.reds.size(); ++k)
-        c << "    double racc" << k << " = "
-          << (d.rules[S.f[S.reds[k]].rule].op == HFAV_OP_REDUCE_MAX ? "__longlong_as_double(0xfff0000000000000ULL)" : "0.0")
-          << ";\n";
+        c << red_decl((int)k, d.rules[S.f[S.reds[k]].rule].op == HFAV_OP_REDUCE_MAX, f64);
     // fields read from memory: each thread's columns (fixed), a row fetch
     // issued kAhead steps ahead, indices wrapped (periodic axioms) or clamped
     // into the field's footprint
@@ -734,10 +754,8 @@ std::string stream_source(const hfav_plan_t* p, const Stream& S, const Part& P, 
                 if (F.red >= 0) {
                     // a reduction: the input's value over this CTA's interior cells
                     const std::string x = "(tid + " + std::to_string(v * NT - F.hxlo) + ")";
-                    const std::string acc = "racc" + std::to_string(F.red);
                     c << "                if (" << x << " < " << TXc << " && i0 + " << x << " < nx)\n"
-                      << "                    " << acc << " = "
-                      << (R.op == HFAV_OP_REDUCE_MAX ? "fmax(" + acc + ", (double)in0)" : acc + " + (double)in0") << ";\n";
+                      << "                    " << red_add(F.red, R.op == HFAV_OP_REDUCE_MAX, f64, "in0") << "\n";
                     c << "            }\n";
                     continue;
                 }
@@ -772,7 +790,7 @@ std::string stream_source(const hfav_plan_t* p, const Stream& S, const Part& P, 
             const bool mx = d.rules[S.f[S.reds[k]].rule].op == HFAV_OP_REDUCE_MAX;
             const std::string op = mx ? "fmax(a, b)" : "a + b";
             c << "    {\n"
-              << "        double a = racc" << k << ";\n"
+              << "        double a = " << red_final((int)k, mx, f64) << ";\n"
               << "        for (int o = 16; o > 0; o >>= 1) { const double b = __shfl_xor_sync(0xffffffffu, a, o); a = " << op
               << "; }\n"
               << "        __syncthreads();\n"
