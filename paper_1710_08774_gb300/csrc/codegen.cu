@@ -413,9 +413,7 @@ int stream_geometry_v(const hfav_plan_t* p, const Schedule& s, const Part& P, in
     for (int f = 0; f < nf; ++f)
         if (involved[f] && (S->f[f].hylo || S->f[f].hyhi || (!S->f[f].scalar && !off0[f] && readers[f]))) pw = false;
     if (pw) {
-        // more loads in flight per thread: twice the columns of a ring kernel
         S->pointwise = true;
-        S->V *= 2;
         S->TXc = S->V * S->NT;
         for (int f = 0; f < nf; ++f) {
             SField& F = S->f[f];
@@ -541,7 +539,7 @@ std::string pointwise_source(const hfav_plan_t* p, const Stream& S, const Part& 
     for (int f : S.scalars) c << "    const T sv" << f << " = (T)scal[" << f << "];\n";
     for (size_t k = 0; k < S.reds.size(); ++k)
         c << red_decl((int)k, d.rules[S.f[S.reds[k]].rule].op == HFAV_OP_REDUCE_MAX, f64);
-    c << "    #pragma unroll 2\n"
+    c << "    #pragma unroll 1\n"
       << "    for (int r = 0; r < jn; ++r) {\n"
       << "        const int gj = j0 + r;\n";
     for (size_t a = 0; a < S.loads.size(); ++a) {
