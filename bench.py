@@ -438,7 +438,7 @@ def oracle_sample(workload, n=None):
         return n * n / dt / 1e9, dt, 0.0, f"{n}x{n} u~U[0,1), single thread"
     if workload.startswith("norm"):
         from oracle import expr as E
-        n = n or 4096
+        n = n or 8192
         u = I.chain2d_input(n, seed=0, halo=1)[1:-1, 1:-1]
         t0 = time.perf_counter()
         E.evaluate(E.normalization_rules(), {"u": u})
