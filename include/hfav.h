@@ -179,6 +179,11 @@ typedef struct {
     int ndim;                /* 1, 2 or 3 */
     int stream_axis;         /* outermost loop axis of the fused nest (global loop order) */
     int feedback;            /* 1: goal g is the next time level of axiom g (time stepping) */
+    /* Declared in/out aliasing (Sec. 3.5 "In/out chaining"): NULL, or n_goals
+     * entries, inout[g] = the index in `axioms` of the axiom whose array goal g
+     * may share (an in-place update), -1 for none.  The result is the one the
+     * non-aliased run gives.  Not with feedback; each axiom at most once. */
+    const int* inout;
 } hfav_dag;
 
 /* One grid: interior extents, allocation pitches and halo width of every
@@ -296,8 +301,13 @@ int hfav_plan_features(const hfav_plan_t* plan, const char* schedule, float* fea
  *               step s+1 (the plan ping-pongs through its own scratch so the
  *               axiom arrays are never written and the last step lands in
  *               the goal arrays); without feedback n_steps must be 1.
- * Goals must not alias axioms (declared aliasing, Sec. 3.5 "In/out chaining",
- * is not supported).  The halo cells of goal arrays are left unspecified.
+ * A goal pointer may equal an axiom pointer only where dag.inout declares
+ * it; any other overlap of goals and axioms is refused (HFAV_EINVAL).  For a
+ * declared in-place run the plan copies the axiom values the update still
+ * needs to temporaries first (Sec. 3.5 "In/out chaining"): the generated
+ * fused 2D kernels save only the halo bands at their CTA boundaries (a few
+ * rows and columns per CTA), every other pipeline the whole axiom array
+ * (plan-owned).  The halo cells of goal arrays are left unspecified.
  * Plan-owned scratch (ping-pong state, HBM intermediates of split or unfused
  * schedules, per-grid time-step slots, counters) is allocated on first use and
  * kept until hfav_free.  Asynchronous: returns after queueing the kernels.

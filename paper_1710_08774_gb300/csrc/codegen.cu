@@ -38,6 +38,48 @@
 
 namespace hfav {
 
+// The halo bands an in-place streaming kernel cannot read live (Sec. 3.5 "In/
+// out chaining": the input values still needed are copied to temporaries
+// before the outputs overwrite them).  For strip b (columns i0 = b TXc ..,
+// interior width wint = min(TXc, nx - i0)) the column band holds, for every
+// row g in [-hylo, ny + hyhi), the hxlo columns left of the interior and the
+// hxhi right of it; for chunk c (rows j0 = c CH .., jn = min(CH, ny - j0))
+// the row band holds the hylo rows above and the hyhi below, over all columns
+// [-hxlo, nx + hxhi).  Indices wrap (periodic) or clamp into the caller's halo
+// exactly as the kernel's own fetches do.  HXa, HYa: band widths, at least 1.
+template <typename T>
+__global__ void __launch_bounds__(256) inout_bands(const GArr src, T* __restrict__ cb, T* __restrict__ rb, int nx,
+                                                   int ny, int TXc, int CH, int hxlo, int hxhi, int hylo, int hyhi,
+                                                   int HXa, int HYa, int strips, int chunks) {
+    const int64_t rows = (int64_t)ny + hylo + hyhi, cols = (int64_t)nx + hxlo + hxhi;
+    const int64_t ncb = (int64_t)strips * rows * HXa, total = ncb + (int64_t)chunks * HYa * cols;
+    auto load = [&](int gi, int gj) -> T {
+        if (!src.wrap) {
+            gi = min(max(gi, -src.org[0]), nx - 1 + src.org[0]);
+            gj = min(max(gj, -src.org[1]), ny - 1 + src.org[1]);
+        }
+        return garr_ld<T>(src, gi, gj, 0);
+    };
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
+        if (q < ncb) {
+            const int k = (int)(q % HXa);
+            const int64_t t = q / HXa;
+            const int g = (int)(t % rows) - hylo, b = (int)(t / rows);
+            const int i0 = b * TXc, wint = min(TXc, nx - i0);
+            const int x = k < hxlo ? k - hxlo : wint + (k - hxlo);
+            cb[q] = load(i0 + x, g);
+        } else {
+            const int64_t u = q - ncb;
+            const int col = (int)(u % cols);
+            const int64_t t = u / cols;
+            const int k = (int)(t % HYa), c = (int)(t / HYa);
+            const int j0 = c * CH, jn = min(CH, ny - j0);
+            const int r = k < hylo ? k - hylo : jn + (k - hylo);
+            rb[u] = load(col - hxlo, j0 + r);
+        }
+    }
+}
+
 namespace {
 
 // ---- NVRTC, opened at first use ---------------------------------------------
@@ -359,6 +401,7 @@ struct Stream {
     std::vector<SField> f;
     std::vector<int> loads, goals, crosses, reds, scalars;   // fields, in parameter / slot order
     std::vector<int> goal_slot;                              // caller goal index of each goals[k]
+    std::vector<char> inplace;                               // per load: its array is also written (in/out)
 };
 
 bool in_part(const Part& P, int r) { return std::find(P.rules.begin(), P.rules.end(), r) != P.rules.end(); }
@@ -413,6 +456,7 @@ int stream_geometry_v(const hfav_plan_t* p, const Schedule& s, const Part& P, in
     for (int f = 0; f < nf; ++f)
         if (involved[f] && (S->f[f].hylo || S->f[f].hyhi || (!S->f[f].scalar && !off0[f] && readers[f]))) pw = false;
     if (pw) {
+        S->inplace.assign(S->loads.size(), 0);
         S->pointwise = true;
         S->TXc = S->V * S->NT;
         for (int f = 0; f < nf; ++f) {
@@ -422,6 +466,7 @@ int stream_geometry_v(const hfav_plan_t* p, const Schedule& s, const Part& P, in
         }
         return HFAV_OK;
     }
+    S->inplace.assign(S->loads.size(), 0);
     S->TXc = S->V * S->NT - hxmax;
     if (S->TXc < 32) return set_error(HFAV_EUNSUPPORTED, "this DAG's footprint is too wide for the tile; use a wider one");
     auto same = [&](int a, int b) {
@@ -530,7 +575,11 @@ std::string pointwise_source(const hfav_plan_t* p, const Stream& S, const Part& 
     for (int r : p->an.order)
         if (in_part(P, r)) c << rule_fn(d.rules[r], "hfav_body" + std::to_string(r));
     c << "extern \"C\" __global__ void __launch_bounds__(" << NT << ") " << name << "(";
-    for (size_t a = 0; a < S.loads.size(); ++a) c << array_params("x" + std::to_string(a), false) << ", ";
+    // a load may share its array with a goal (in/out): no __restrict__ on loads
+    for (size_t a = 0; a < S.loads.size(); ++a) {
+        const std::string x = "x" + std::to_string(a), ap = array_params(x, false);
+        c << "const T* " << x << ap.substr(ap.find(',')) << ", ";
+    }
     for (size_t a = 0; a < S.goals.size(); ++a) c << array_params("y" + std::to_string(a), true) << ", ";
     for (size_t a = 0; a < S.crosses.size(); ++a) c << array_params("z" + std::to_string(a), true) << ", ";
     c << "const double* __restrict__ scal, double* __restrict__ part, int nx, int ny, int CH) {\n"
@@ -637,9 +686,16 @@ std::string stream_source(const hfav_plan_t* p, const Stream& S, const Part& P, 
     for (int r : p->an.order)
         if (in_part(P, r)) c << rule_fn(d.rules[r], "hfav_body" + std::to_string(r));
     c << "extern \"C\" __global__ void __launch_bounds__(" << NT << ") " << name << "(";
-    for (size_t a = 0; a < S.loads.size(); ++a) c << array_params("x" + std::to_string(a), false) << ", ";
+    // an in-place load shares its array with a goal: no __restrict__ on it
+    for (size_t a = 0; a < S.loads.size(); ++a)
+        c << (S.inplace[a] ? "const T* " + ("x" + std::to_string(a)) + array_params("x" + std::to_string(a), false).substr(
+                                 array_params("x" + std::to_string(a), false).find(','))
+                           : array_params("x" + std::to_string(a), false))
+          << ", ";
     for (size_t a = 0; a < S.goals.size(); ++a) c << array_params("y" + std::to_string(a), true) << ", ";
     for (size_t a = 0; a < S.crosses.size(); ++a) c << array_params("z" + std::to_string(a), true) << ", ";
+    for (size_t a = 0; a < S.loads.size(); ++a)
+        if (S.inplace[a]) c << "const T* __restrict__ cb" << a << ", const T* __restrict__ rb" << a << ", ";
     c << "const double* __restrict__ scal, double* __restrict__ part, int nx, int ny, int CH) {\n"
       << "    extern __shared__ __align__(16) unsigned char smem[];\n"
       << "    const int tid = threadIdx.x, i0 = blockIdx.x * " << TXc << ", j0 = blockIdx.y * CH;\n"
@@ -652,30 +708,58 @@ std::string stream_source(const hfav_plan_t* p, const Stream& S, const Part& P, 
         c << red_decl((int)k, d.rules[S.f[S.reds[k]].rule].op == HFAV_OP_REDUCE_MAX, f64);
     // fields read from memory: each thread's columns (fixed), a row fetch
     // issued kAhead steps ahead, indices wrapped (periodic axioms) or clamped
-    // into the field's footprint
+    // into the field's footprint.  A field whose array the part also writes
+    // (a declared in/out pair) reads only its own strip's interior rows live:
+    // the halo columns and the rows beyond its chunk come from bands saved
+    // before the launch, since neighbouring CTAs overwrite them.
+    const bool any_inplace = std::find(S.inplace.begin(), S.inplace.end(), 1) != S.inplace.end();
+    if (any_inplace) c << "    const int wint = min(" << TXc << ", nx - i0);\n";
     for (int f : S.loads) {
         const SField& F = S.f[f];
         const std::string a = std::to_string(F.load), x = "x" + a;
+        const bool inpl = S.inplace[F.load];
+        const int HXa = std::max(1, F.hxlo + F.hxhi), HYa = std::max(1, F.hylo + F.hyhi);
         for (int v = 0; v < V; ++v) {
             const std::string cv = a + "_" + std::to_string(v);
             if (inside(v, F.w) == "-") continue;
-            c << "    int col" << cv << " = i0 - " << F.hxlo << " + tid + " << v * NT << ";\n"
-              << "    if (" << x << "_w) col" << cv << " = hfav_wrap(col" << cv << ", nx);\n"
-              << "    else col" << cv << " = min(max(col" << cv << ", -" << F.hxlo << "), nx - 1 + " << F.hxhi << ");\n"
-              << "    const T* src" << cv << " = " << x << " + col" << cv << " + " << x << "_o0;\n";
+            if (!inpl) {
+                c << "    int col" << cv << " = i0 - " << F.hxlo << " + tid + " << v * NT << ";\n"
+                  << "    if (" << x << "_w) col" << cv << " = hfav_wrap(col" << cv << ", nx);\n"
+                  << "    else col" << cv << " = min(max(col" << cv << ", -" << F.hxlo << "), nx - 1 + " << F.hxhi << ");\n"
+                  << "    const T* src" << cv << " = " << x << " + col" << cv << " + " << x << "_o0;\n";
+            } else {
+                c << "    const int xv" << cv << " = tid + " << v * NT - F.hxlo << ";\n"
+                  << "    const bool live" << cv << " = xv" << cv << " >= 0 && xv" << cv << " < wint;\n"
+                  << "    const int kb" << cv << " = min(max(xv" << cv << " < 0 ? xv" << cv << " + " << F.hxlo << " : "
+                  << F.hxlo << " + xv" << cv << " - wint, 0), " << HXa - 1 << ");\n"
+                  << "    const T* src" << cv << " = live" << cv << " ? " << x << " + (long long)" << x << "_o1 * " << x
+                  << "_p1 + " << x << "_o0 + i0 + xv" << cv << " : cb" << a << " + ((long long)blockIdx.x * (ny + "
+                  << F.hylo + F.hyhi << ") + " << F.hylo << ") * " << HXa << " + kb" << cv << ";\n"
+                  << "    const long long sr" << cv << " = live" << cv << " ? " << x << "_p1 : " << HXa << ";\n"
+                  << "    const int rcol" << cv << " = min(max(i0 + xv" << cv << " + " << F.hxlo << ", 0), nx + "
+                  << F.hxlo + F.hxhi - 1 << ");\n";
+            }
         }
         c << "    auto fetch" << a << " = [&](int r) {\n"
-          << "        if (r >= -" << F.hylo << " && r < jn + " << F.hyhi << ") {\n"
-          << "            int gj = j0 + r;\n"
-          << "            if (" << x << "_w) gj = hfav_wrap(gj, ny);\n"
-          << "            else gj = min(max(gj, -" << F.hylo << "), ny - 1 + " << F.hyhi << ");\n"
-          << "            const long long ro = (long long)(gj + " << x << "_o1) * " << x << "_p1;\n"
-          << "            T* const dst = s" << f << " + " << slot("r", F.W) << " * " << F.w << " + tid;\n";
+          << "        if (r >= -" << F.hylo << " && r < jn + " << F.hyhi << ") {\n";
+        if (!inpl) {
+            c << "            int gj = j0 + r;\n"
+              << "            if (" << x << "_w) gj = hfav_wrap(gj, ny);\n"
+              << "            else gj = min(max(gj, -" << F.hylo << "), ny - 1 + " << F.hyhi << ");\n"
+              << "            const long long ro = (long long)(gj + " << x << "_o1) * " << x << "_p1;\n";
+        } else {
+            c << "            const bool band = r < 0 || r >= jn;\n"
+              << "            const T* const rrow = rb" << a << " + ((long long)blockIdx.y * " << HYa << " + min(max(r < 0 ? r + "
+              << F.hylo << " : " << F.hylo << " + r - jn, 0), " << HYa - 1 << ")) * (nx + " << F.hxlo + F.hxhi << ");\n";
+        }
+        c << "            T* const dst = s" << f << " + " << slot("r", F.W) << " * " << F.w << " + tid;\n";
         for (int v = 0; v < V; ++v) {
             const std::string in = inside(v, F.w), cv = a + "_" + std::to_string(v);
             if (in == "-") continue;
-            c << "            " << (in.empty() ? "" : "if (" + in + ") ") << "hfav_cp(dst + " << v * NT << ", src" << cv
-              << " + ro);\n";
+            c << "            " << (in.empty() ? "" : "if (" + in + ") ") << "hfav_cp(dst + " << v * NT << ", ";
+            if (!inpl) c << "src" << cv << " + ro);\n";
+            else
+                c << "band ? rrow + rcol" << cv << " : src" << cv << " + (long long)(j0 + r) * sr" << cv << ");\n";
         }
         c << "        }\n"
           << "    };\n";
@@ -951,7 +1035,24 @@ bool has_scalars(const hfav_plan_t* p) {
     return false;
 }
 
+// the loads of a single-part program whose arrays a declared in/out goal shares
+void mark_inplace(const hfav_plan_t* p, Stream* S, void* const* ax, void* const* go) {
+    const Dag& d = p->dag;
+    for (size_t l = 0; l < S->loads.size(); ++l)
+        for (size_t k = 0; k < d.goals.size(); ++k) {
+            const int a = d.inout[k];
+            if (a >= 0 && d.axioms[a] == S->loads[l] && (!ax || go[k] == ax[a])) S->inplace[l] = 1;
+        }
+}
+
 }  // namespace
+
+bool codegen_inplace(const hfav_plan_t* p, const Schedule& s) {
+    if (p->pipeline != PIPE_CODEGEN || s.fusion == FUSE_UNFUSED || p->dag.ndim != 2) return false;
+    Program G;
+    if (make_program(p, true, &G)) return false;
+    return G.parts.size() == 1;
+}
 
 int plan_source(const hfav_plan_t* p, std::string* out) {
     if (p->pipeline != PIPE_CODEGEN) return set_error(HFAV_EUNSUPPORTED, "the plan runs no generated kernels");
@@ -960,9 +1061,11 @@ int plan_source(const hfav_plan_t* p, std::string* out) {
         Program G;
         int rc = make_program(p, p->sched.fusion != FUSE_UNFUSED, &G);
         if (rc) return rc;
+        const bool inpl = codegen_inplace(p, p->sched);
         for (size_t k = 0; k < G.parts.size(); ++k) {
             Stream S;
             if ((rc = stream_geometry(p, p->sched, G.parts[k], &S))) return rc;
+            if (inpl) mark_inplace(p, &S, nullptr, nullptr);   // the declared pairs, as an aliased run compiles them
             o << "// ---- kernel " << k << "\n" << stream_source(p, S, G.parts[k], "hfav_cg_part");
             if (!G.fin_reds[k].empty() || !G.fin_rules[k].empty())
                 o << "// ---- kernel " << k << " finalize\n" << finalize_source(p, G.fin_reds[k], G.fin_rules[k]);
@@ -1040,9 +1143,11 @@ int launch_codegen(hfav_plan_t* p, const Schedule& s, void* const* ax, void* con
     struct Launch { Stream S; cudaKernel_t kern, fin = nullptr; int CH; int64_t strips, nblocks; };
     std::vector<Launch> L(G.parts.size());
     size_t part_bytes = 0;
+    const bool inpl = fused && G.parts.size() == 1;
     for (size_t k = 0; k < G.parts.size(); ++k) {
         Launch& X = L[k];
         if ((rc = stream_geometry(p, s, G.parts[k], &X.S))) return rc;
+        if (inpl && !X.S.pointwise) mark_inplace(p, &X.S, ax, go);
         const Stream& S = X.S;
         if ((rc = compile(stream_source(p, S, G.parts[k], "hfav_cg_part"), "hfav_cg_part", &X.kern))) return rc;
         // a library kernel takes its attributes per device
@@ -1086,6 +1191,30 @@ int launch_codegen(hfav_plan_t* p, const Schedule& s, void* const* ax, void* con
             add_array(A, y);
         }
         for (int f : S.crosses) add_array(A, cross[f]);
+        // in/out: save the halo bands of each aliased array before it is overwritten
+        for (size_t l = 0; l < S.loads.size(); ++l) {
+            if (!S.inplace[l]) continue;
+            const SField& F = S.f[S.loads[l]];
+            const int HXa = std::max(1, F.hxlo + F.hxhi), HYa = std::max(1, F.hylo + F.hyhi);
+            const int64_t chunks = (ny + X.CH - 1) / X.CH;
+            const int64_t ncb = X.strips * ((int64_t)ny + F.hylo + F.hyhi) * HXa;
+            const int64_t nrb = chunks * HYa * ((int64_t)nx + F.hxlo + F.hxhi);
+            void *cb, *rb;
+            if ((rc = scratch(p, "inout_cb_" + std::to_string(S.loads[l]), (size_t)ncb * es, &cb))) return rc;
+            if ((rc = scratch(p, "inout_rb_" + std::to_string(S.loads[l]), (size_t)nrb * es, &rb))) return rc;
+            const auto ai = std::find(d.axioms.begin(), d.axioms.end(), S.loads[l]);
+            const GArr src = caller_view_cg(p, ax[ai - d.axioms.begin()]);
+            const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((ncb + nrb + 255) / 256, 152 * 8));
+            if (es == 8)
+                inout_bands<double><<<blocks, 256, 0, st>>>(src, (double*)cb, (double*)rb, nx, ny, S.TXc, X.CH, F.hxlo,
+                                                            F.hxhi, F.hylo, F.hyhi, HXa, HYa, (int)X.strips, (int)chunks);
+            else
+                inout_bands<float><<<blocks, 256, 0, st>>>(src, (float*)cb, (float*)rb, nx, ny, S.TXc, X.CH, F.hxlo,
+                                                           F.hxhi, F.hylo, F.hyhi, HXa, HYa, (int)X.strips, (int)chunks);
+            HFAV_LAUNCHED(p->rt, "codegen_inout_bands", st);
+            A.add((const void*)cb);
+            A.add((const void*)rb);
+        }
         A.add((const void*)scal);
         A.add(part);
         A.add(nx);

@@ -27,6 +27,7 @@ struct Dag {
     int ndim = 2;
     int stream_axis = 1;
     int feedback = 0;
+    std::vector<int> inout;   // per goal: index of the axiom it may alias, -1 for none
 };
 
 // Schedule axes: fusion x placement x tile (the variant space of the cost model).
@@ -102,8 +103,10 @@ void features(const hfav_plan_t* p, const Schedule& s, float* f);
 // errors.cpp-style helpers (api.cpp)
 int set_error(int code, const std::string& msg);
 
-// codegen.cu: the CUDA source a plan of generated kernels compiles
+// codegen.cu: the CUDA source a plan of generated kernels compiles; whether
+// a schedule updates declared in/out pairs in place (no full snapshot)
 int plan_source(const hfav_plan_t* p, std::string* out);
+bool codegen_inplace(const hfav_plan_t* p, const Schedule& s);
 
 // runtime.cu
 int run(hfav_plan_t* p, void* const* ax, void* const* go, int n_steps, void* stream, bool graph);

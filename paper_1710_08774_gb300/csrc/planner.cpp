@@ -236,6 +236,21 @@ int copy_dag(const hfav_dag* in, Dag* d) {
     }
     if (d->feedback && d->axioms.size() != d->goals.size())
         return set_error(HFAV_EINVAL, "feedback needs as many goals as axioms");
+    d->inout.assign(d->goals.size(), -1);
+    if (in->inout) {
+        if (d->feedback) return set_error(HFAV_EINVAL, "in/out aliasing cannot be declared with feedback");
+        std::vector<char> used(d->axioms.size(), 0);
+        for (size_t g = 0; g < d->goals.size(); ++g) {
+            const int a = in->inout[g];
+            if (a == -1) continue;
+            if (a < 0 || a >= (int)d->axioms.size()) return set_error(HFAV_EINVAL, "inout: axiom index out of range");
+            if (used[a]) return set_error(HFAV_EINVAL, "inout: an axiom aliased by two goals");
+            if (d->rank[d->axioms[a]] != d->rank[d->goals[g]])
+                return set_error(HFAV_EINVAL, "inout: aliased fields of different rank");
+            used[a] = 1;
+            d->inout[g] = a;
+        }
+    }
     return HFAV_OK;
 }
 

@@ -28,7 +28,44 @@ int ensure_runtime(hfav_plan_t* p) {
     return HFAV_OK;
 }
 
+// elements of a caller array of grid g, from its first (halo) element to its last
+int64_t array_elems(const hfav_plan_t* p, int g) {
+    const hfav_grid& G = p->grids[g];
+    int64_t last = 0;
+    for (int d = 0; d < 3; ++d) {
+        const int64_t h = d < p->dag.ndim ? G.halo : 0;
+        last += (G.extent[d] + 2 * h - 1) * G.pitch[d];
+    }
+    return last + 1;
+}
+
+int launch_pipeline(hfav_plan_t* p, const Schedule& s, void* const* ax, void* const* go, int n_steps, cudaStream_t st);
+
+// Declared in/out pairs that share an array in this run: unless the schedule
+// updates them in place, the axiom is first copied to a plan-owned snapshot,
+// which the run then reads (Sec. 3.5 "In/out chaining": the input values the
+// update still needs go to temporaries before the output is written)
 int launch_once(hfav_plan_t* p, const Schedule& s, void* const* ax, void* const* go, int n_steps, cudaStream_t st) {
+    const size_t na = p->dag.axioms.size(), nq = p->dag.goals.size(), ng = p->grids.size();
+    std::vector<void*> axs(ax, ax + ng * na);
+    bool copied = false;
+    if (!(p->pipeline == PIPE_CODEGEN && codegen_inplace(p, s)))
+        for (size_t g = 0; g < ng; ++g)
+            for (size_t k = 0; k < nq; ++k) {
+                const int a = p->dag.inout[k];
+                if (a < 0 || go[g * nq + k] != ax[g * na + a]) continue;
+                const size_t bytes = (size_t)array_elems(p, (int)g) * (p->dtype == HFAV_F64 ? 8 : 4);
+                void* snap;
+                int rc = scratch(p, "inout_snapshot_" + std::to_string(g * na + a), bytes, &snap);
+                if (rc) return rc;
+                HFAV_CUDA(cudaMemcpyAsync(snap, ax[g * na + a], bytes, cudaMemcpyDeviceToDevice, st));
+                axs[g * na + a] = snap;
+                copied = true;
+            }
+    return launch_pipeline(p, s, copied ? axs.data() : ax, go, n_steps, st);
+}
+
+int launch_pipeline(hfav_plan_t* p, const Schedule& s, void* const* ax, void* const* go, int n_steps, cudaStream_t st) {
     switch (p->pipeline) {
         case PIPE_CHAIN2D: return launch_chain2d(p, s, ax, go, st);
         case PIPE_CHAIN3D: return launch_chain3d(p, s, ax, go, st);
@@ -49,8 +86,10 @@ int check_ptrs(hfav_plan_t* p, void* const* ax, void* const* go) {
     for (size_t k = 0; k < ng * p->dag.goals.size(); ++k) {
         if (!go[k]) return set_error(HFAV_EINVAL, "null goal pointer");
         if ((uintptr_t)go[k] % 16) return set_error(HFAV_EALIGN, "goal pointer not 16-byte aligned");
-        for (size_t a = 0; a < ng * p->dag.axioms.size(); ++a)
-            if (go[k] == ax[a]) return set_error(HFAV_EINVAL, "a goal aliases an axiom (in/out chaining is not supported)");
+        const size_t na = p->dag.axioms.size(), nq = p->dag.goals.size();
+        for (size_t a = 0; a < ng * na; ++a)
+            if (go[k] == ax[a] && !(a / na == k / nq && p->dag.inout[k % nq] == (int)(a % na)))
+                return set_error(HFAV_EINVAL, "a goal aliases an axiom it is not declared to alias (dag.inout)");
     }
     return HFAV_OK;
 }

@@ -56,7 +56,7 @@ class Dag(ctypes.Structure):
     _fields_ = [("n_fields", ctypes.c_int), ("field_rank", ctypes.POINTER(ctypes.c_int)), ("n_rules", ctypes.c_int),
                 ("rules", ctypes.POINTER(Rule)), ("n_axioms", ctypes.c_int), ("axioms", ctypes.POINTER(ctypes.c_int)),
                 ("n_goals", ctypes.c_int), ("goals", ctypes.POINTER(ctypes.c_int)), ("ndim", ctypes.c_int),
-                ("stream_axis", ctypes.c_int), ("feedback", ctypes.c_int)]
+                ("stream_axis", ctypes.c_int), ("feedback", ctypes.c_int), ("inout", ctypes.POINTER(ctypes.c_int))]
 
 
 class Grid(ctypes.Structure):
@@ -204,6 +204,11 @@ class DagSpec:
     def goal(self, *names):
         self.goals += [self.field(n) for n in names]
 
+    def inout(self, goal, axiom):
+        """Declare that `goal`'s array may be `axiom`'s array (an in-place update)."""
+        self.aliases = getattr(self, "aliases", {})
+        self.aliases[self.field(goal)] = self.field(axiom)
+
     def c(self):
         """The hfav_dag struct (kept alive by this object)."""
         keep = []
@@ -236,6 +241,12 @@ class DagSpec:
         d.n_axioms, d.axioms = len(self.axioms), ax
         d.n_goals, d.goals = len(self.goals), go
         d.ndim, d.stream_axis, d.feedback = self.ndim, self.stream_axis, self.feedback
+        aliases = getattr(self, "aliases", {})
+        if aliases:
+            io = (ctypes.c_int * len(self.goals))(*[self.axioms.index(aliases[g]) if g in aliases else -1
+                                                   for g in self.goals])
+            keep.append(io)
+            d.inout = io
         self._keep = keep
         self._c = d
         return d

@@ -161,3 +161,30 @@ def test_reduction_sources_compile_with_nvrtc(dtype, schedule):
     for u in _units(src):
         rc, log = _compile(L, u)
         assert rc == 0, log
+
+
+def test_inout_declarations_validated():
+    D = H.DagSpec(2)
+    D.rule("EXPR", [("u", (1, 0)), ("u", (-1, 0))], ["o"], expr="in0 - in1")
+    D.axiom("u"); D.goal("o"); D.inout("o", "u")
+    H.analyze(D)
+    bad = H.DagSpec(2, feedback=True)
+    bad.rule("EXPR", [("u", (1, 0))], ["o"], expr="in0")
+    bad.axiom("u"); bad.goal("o"); bad.inout("o", "u")
+    with pytest.raises(H.HfavError):
+        H.analyze(bad)
+
+
+@pytest.mark.parametrize("dtype", [H.HFAV_F64, H.HFAV_F32])
+def test_inplace_sources_compile_with_nvrtc(dtype):
+    """A declared in/out pair makes the fused 2D kernel read its halo bands
+    from saved copies; the source compiles."""
+    L = _nvrtc()
+    D = H.chain2d_expr_dag()
+    D.inout("out", "u")
+    P = H.Plan(D, [_grid((64, 64), 2)], dtype, H.HFAV_BC_PERIODIC, "full:smem:32x4")
+    src = P.source()
+    assert "cb0" in src and "rb0" in src and "wint" in src
+    for u in _units(src):
+        rc, log = _compile(L, u)
+        assert rc == 0, log
