@@ -318,7 +318,9 @@ int hfav_run(hfav_plan_t* plan, void* const* axiom_ptrs, void* const* goal_ptrs,
              void* stream);
 
 /* Same as hfav_run, but the whole n_steps sequence is captured once into a
- * CUDA graph (per plan, keyed on the pointers and n_steps) and replayed. */
+ * CUDA graph (per plan, keyed on the pointers and n_steps) and replayed.  The
+ * uncaptured preparation run before a capture works on plan-owned copies of
+ * in-place (dag.inout) arrays, so each call updates them exactly once. */
 int hfav_run_graph(hfav_plan_t* plan, void* const* axiom_ptrs, void* const* goal_ptrs, int n_steps,
                    void* stream);
 
@@ -330,7 +332,8 @@ int hfav_status(hfav_plan_t* plan, hfav_run_stats* stats);
  * hfav_autotune: time every valid schedule of the plan (fusion x placement x
  * tile) on the given arrays with CUDA events (median of `reps` after one warm
  * run), keep the fastest as the plan's schedule.  times_ms receives one time
- * per variant in the order of hfav_plan_variants (may be NULL).
+ * per variant in the order of hfav_plan_variants (may be NULL).  In-place
+ * (dag.inout) arrays are timed on plan-owned copies and left unchanged.
  */
 int hfav_autotune(hfav_plan_t* plan, void* const* axiom_ptrs, void* const* goal_ptrs, int n_steps,
                   int reps, void* stream, float* times_ms, int n_times);

@@ -41,6 +41,29 @@ int64_t array_elems(const hfav_plan_t* p, int g) {
 
 int launch_pipeline(hfav_plan_t* p, const Schedule& s, void* const* ax, void* const* go, int n_steps, cudaStream_t st);
 
+// Pointer tables in which every in-place pair of this run is redirected to a
+// plan-owned copy of its array (`tag` names the copies): runs that only
+// prepare or time a plan then leave the caller's arrays as they were.
+int redirect_inplace(hfav_plan_t* p, void* const* ax, void* const* go, cudaStream_t st, const std::string& tag,
+                     std::vector<void*>* axw, std::vector<void*>* gow) {
+    const size_t na = p->dag.axioms.size(), nq = p->dag.goals.size(), ng = p->grids.size();
+    axw->assign(ax, ax + ng * na);
+    gow->assign(go, go + ng * nq);
+    for (size_t g = 0; g < ng; ++g)
+        for (size_t k = 0; k < nq; ++k) {
+            const int a = p->dag.inout[k];
+            if (a < 0 || go[g * nq + k] != ax[g * na + a]) continue;
+            const size_t bytes = (size_t)array_elems(p, (int)g) * (p->dtype == HFAV_F64 ? 8 : 4);
+            void* w;
+            int rc = scratch(p, tag + std::to_string(g * na + a), bytes, &w);
+            if (rc) return rc;
+            HFAV_CUDA(cudaMemcpyAsync(w, ax[g * na + a], bytes, cudaMemcpyDeviceToDevice, st));
+            (*axw)[g * na + a] = w;
+            (*gow)[g * nq + k] = w;
+        }
+    return HFAV_OK;
+}
+
 // Declared in/out pairs that share an array in this run: unless the schedule
 // updates them in place, the axiom is first copied to a plan-owned snapshot,
 // which the run then reads (Sec. 3.5 "In/out chaining": the input values the
@@ -187,9 +210,13 @@ int run(hfav_plan_t* p, void* const* ax, void* const* go, int n_steps, void* str
               rt->gstream == st)) {
             drop_graph(p);
             // one uncaptured run allocates the scratch and uploads the tables;
-            // the captured run then only queues kernels and async memsets
+            // the captured run then only queues kernels and async memsets.  An
+            // in-place pair runs that warm-up on a copy, so the caller's array
+            // is updated once, by the graph
             rt->launches = 0;
-            if ((rc = launch_once(p, p->sched, ax, go, n_steps, st))) return rc;
+            std::vector<void*> axw, gow;
+            if ((rc = redirect_inplace(p, ax, go, st, "inout_copy_", &axw, &gow))) return rc;
+            if ((rc = launch_once(p, p->sched, axw.data(), gow.data(), n_steps, st))) return rc;
             HFAV_CUDA(cudaStreamSynchronize(st));
             cudaGraph_t gr;
             HFAV_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
@@ -281,6 +308,11 @@ int autotune(hfav_plan_t* p, void* const* ax, void* const* go, int n_steps, int 
     HFAV_CUDA(cudaEventCreate(&e1));
     Schedule keep = p->sched, best = p->sched;
     float best_t = 1e30f;
+    // in-place pairs are timed on a copy: the caller's arrays stay as they were
+    std::vector<void*> axw, gow;
+    if ((rc = redirect_inplace(p, ax, go, st, "inout_copy_", &axw, &gow))) return rc;
+    ax = axw.data();
+    go = gow.data();
     for (size_t v = 0; v < vars.size(); ++v) {
         std::vector<float> ts;
         rc = launch_once(p, vars[v], ax, go, n_steps, st);   // warm: allocations, uploads

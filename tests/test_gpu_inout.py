@@ -122,3 +122,15 @@ def test_undeclared_alias_refused_and_graph_replay():
     D.inout("out", "u")
     ref, got, _ = _twice(D, [I.chain2d_input(1100, seed=2, ny=600)], 2, "full:smem:32x4", graph=True)
     assert np.array_equal(ref, got)
+
+
+def test_autotune_leaves_in_place_arrays_unchanged():
+    import torch
+    D = H.chain2d_expr_dag()
+    D.inout("out", "u")
+    u = to_dev(I.chain2d_input(600, seed=4, ny=300))
+    keep = u.clone()
+    P = H.Plan(D, [H.Grid.of(u, 2)], H.HFAV_F64, H.HFAV_BC_PERIODIC)
+    P.autotune([u], [u], reps=1)
+    torch.cuda.synchronize()
+    assert torch.equal(u[2:-2, 2:-2], keep[2:-2, 2:-2])
