@@ -342,6 +342,21 @@ class Chain(Workload):
         return None, None, None
 
 
+class InPlace(Chain):
+    """The 2D chain as rule bodies with its goal declared to alias its axiom
+    (Sec. 3.5 "In/out chaining"): each step overwrites u with out.  The
+    generated fused kernel saves the halo bands at its CTA boundaries and
+    updates in place, so one array (plus the bands) is resident instead of
+    two; the unfused form runs from a snapshot of u."""
+
+    def __init__(self, H, I, torch, dev, n, dtype, seed=0):
+        super().__init__(H, I, torch, dev, 2, n, dtype, seed, expr=True)
+        self.name = self.name.replace("codegen_", "inplace_")
+        self.dag.inout("out", "u")
+        self.plan = H.Plan(self.dag, self.grids, self.hdt, H.HFAV_BC_PERIODIC, "full:smem:32x8")
+        self.out = self.u
+
+
 class Norm(Workload):
     """The normalization example (Sec. 5.2) on an n x n grid: flux, second
     difference, norm accumulation (a reduction) and root, division (a
@@ -384,7 +399,7 @@ class Norm(Workload):
 
 
 WORKLOADS = ["godunov1024_f64", "godunov4096_f32", "batch64_f32", "chain2d256_f64", "chain2d16384_f32", "chain3d512_f32",
-             "cosmo1024_f32", "codegen2d16384_f32", "norm2d16384_f32"]
+             "cosmo1024_f32", "codegen2d16384_f32", "norm2d16384_f32", "inplace2d16384_f32"]
 
 
 def make(name, H, I, torch, dev):
@@ -413,6 +428,9 @@ def make(name, H, I, torch, dev):
     m = re.fullmatch(r"norm2d(\d+)_(f32|f64)", name)
     if m:
         return Norm(H, I, torch, dev, int(m.group(1)), m.group(2))
+    m = re.fullmatch(r"inplace2d(\d+)_(f32|f64)", name)
+    if m:
+        return InPlace(H, I, torch, dev, int(m.group(1)), m.group(2))
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -448,7 +466,7 @@ def oracle_sample(workload, n=None):
         E.evaluate(E.normalization_rules(), {"u": u})
         dt = time.perf_counter() - t0
         return n * n / dt / 1e9, dt, 0.0, f"{n}x{n} u~U[0,1), expression oracle (numpy), single thread"
-    if workload.startswith("codegen"):
+    if workload.startswith(("codegen", "inplace")):
         from oracle import expr as E
         n = n or 8192
         u = I.chain2d_input(n, seed=0)[2:-2, 2:-2]
@@ -493,6 +511,9 @@ def workload_name(key):
     m = re.fullmatch(r"norm2d(\d+)_(f32|f64)", key)
     if m:
         return f"normalization2d_{'fp64' if m.group(2) == 'f64' else 'fp32'}_{m.group(1)}x{m.group(1)}"
+    m = re.fullmatch(r"inplace2d(\d+)_(f32|f64)", key)
+    if m:
+        return f"inplace_chain2d_{'fp64' if m.group(2) == 'f64' else 'fp32'}_{m.group(1)}x{m.group(1)}"
     raise SystemExit(f"unknown workload {key}")
 
 
@@ -700,7 +721,7 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default=WORKLOADS[0], help="one of " + ", ".join(WORKLOADS + ["all"]) + ", or chain2d<N>_f32|f64 / chain3d<N>_f32|f64 / cosmo<N>_f32|f64 / codegen2d<N>_f32|f64 / norm2d<N>_f32|f64 (other sizes)")
+    ap.add_argument("--workload", default=WORKLOADS[0], help="one of " + ", ".join(WORKLOADS + ["all"]) + ", or chain2d<N>_f32|f64 / chain3d<N>_f32|f64 / cosmo<N>_f32|f64 / codegen2d<N>_f32|f64 / norm2d<N>_f32|f64 / inplace2d<N>_f32|f64 (other sizes)")
     ap.add_argument("--schedule", default=None, help="fixed schedule (default: autotuned among fused ones)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--once", action="store_true", help="profiling case: build the plan and run it once")
