@@ -47,37 +47,40 @@ namespace hfav {
 // the row band holds the hylo rows above and the hyhi below, over all columns
 // [-hxlo, nx + hxhi).  Indices wrap (periodic) or clamp into the caller's halo
 // exactly as the kernel's own fetches do.  HXa, HYa: band widths, at least 1.
+// Two kernels, one per band, with no division per element.
 template <typename T>
-__global__ void __launch_bounds__(256) inout_bands(const GArr src, T* __restrict__ cb, T* __restrict__ rb, int nx,
-                                                   int ny, int TXc, int CH, int hxlo, int hxhi, int hylo, int hyhi,
-                                                   int HXa, int HYa, int strips, int chunks) {
-    const int64_t rows = (int64_t)ny + hylo + hyhi, cols = (int64_t)nx + hxlo + hxhi;
-    const int64_t ncb = (int64_t)strips * rows * HXa, total = ncb + (int64_t)chunks * HYa * cols;
-    auto load = [&](int gi, int gj) -> T {
-        if (!src.wrap) {
-            gi = min(max(gi, -src.org[0]), nx - 1 + src.org[0]);
-            gj = min(max(gj, -src.org[1]), ny - 1 + src.org[1]);
-        }
-        return garr_ld<T>(src, gi, gj, 0);
-    };
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x) {
-        if (q < ncb) {
-            const int k = (int)(q % HXa);
-            const int64_t t = q / HXa;
-            const int g = (int)(t % rows) - hylo, b = (int)(t / rows);
-            const int i0 = b * TXc, wint = min(TXc, nx - i0);
-            const int x = k < hxlo ? k - hxlo : wint + (k - hxlo);
-            cb[q] = load(i0 + x, g);
-        } else {
-            const int64_t u = q - ncb;
-            const int col = (int)(u % cols);
-            const int64_t t = u / cols;
-            const int k = (int)(t % HYa), c = (int)(t / HYa);
-            const int j0 = c * CH, jn = min(CH, ny - j0);
-            const int r = k < hylo ? k - hylo : jn + (k - hylo);
-            rb[u] = load(col - hxlo, j0 + r);
-        }
+__device__ __forceinline__ T band_load(const GArr& src, int gi, int gj, int nx, int ny) {
+    if (!src.wrap) {
+        gi = min(max(gi, -src.org[0]), nx - 1 + src.org[0]);
+        gj = min(max(gj, -src.org[1]), ny - 1 + src.org[1]);
     }
+    return garr_ld<T>(src, gi, gj, 0);
+}
+
+// column bands: one thread per (strip, row), its HXa columns
+template <typename T>
+__global__ void __launch_bounds__(256) inout_colband(const GArr src, T* __restrict__ cb, int nx, int ny, int TXc,
+                                                     int hxlo, int hylo, int rows, int HXa, int pairs) {
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= pairs) return;
+    const int b = q / rows, g = q - b * rows - hylo;
+    const int i0 = b * TXc, wint = min(TXc, nx - i0);
+    for (int k = 0; k < HXa; ++k) {
+        const int x = k < hxlo ? k - hxlo : wint + (k - hxlo);
+        cb[(int64_t)q * HXa + k] = band_load<T>(src, i0 + x, g, nx, ny);
+    }
+}
+
+// row bands: blockIdx.y = (chunk, band row), threads along the columns
+template <typename T>
+__global__ void __launch_bounds__(256) inout_rowband(const GArr src, T* __restrict__ rb, int nx, int ny, int CH,
+                                                     int hxlo, int hylo, int cols, int HYa) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= cols) return;
+    const int c = blockIdx.y / HYa, k = blockIdx.y - c * HYa;
+    const int j0 = c * CH, jn = min(CH, ny - j0);
+    const int r = k < hylo ? k - hylo : jn + (k - hylo);
+    rb[(int64_t)blockIdx.y * cols + col] = band_load<T>(src, col - hxlo, j0 + r, nx, ny);
 }
 
 namespace {
@@ -736,6 +739,7 @@ std::string stream_source(const hfav_plan_t* p, const Stream& S, const Part& P, 
                   << "_p1 + " << x << "_o0 + i0 + xv" << cv << " : cb" << a << " + ((long long)blockIdx.x * (ny + "
                   << F.hylo + F.hyhi << ") + " << F.hylo << ") * " << HXa << " + kb" << cv << ";\n"
                   << "    const long long sr" << cv << " = live" << cv << " ? " << x << "_p1 : " << HXa << ";\n"
+                  << "    const T* pl" << cv << " = src" << cv << " + (long long)(j0 + " << S.ylo << ") * sr" << cv << ";\n"
                   << "    const int rcol" << cv << " = min(max(i0 + xv" << cv << " + " << F.hxlo << ", 0), nx + "
                   << F.hxlo + F.hxhi - 1 << ");\n";
             }
@@ -758,11 +762,14 @@ std::string stream_source(const hfav_plan_t* p, const Stream& S, const Part& P, 
             if (in == "-") continue;
             c << "            " << (in.empty() ? "" : "if (" + in + ") ") << "hfav_cp(dst + " << v * NT << ", ";
             if (!inpl) c << "src" << cv << " + ro);\n";
-            else
-                c << "band ? rrow + rcol" << cv << " : src" << cv << " + (long long)(j0 + r) * sr" << cv << ");\n";
+            else c << "band ? rrow + rcol" << cv << " : pl" << cv << ");\n";
         }
-        c << "        }\n"
-          << "    };\n";
+        c << "        }\n";
+        // the fetches run for consecutive rows: each thread's live row pointers step by one row
+        if (inpl)
+            for (int v = 0; v < V; ++v)
+                if (inside(v, F.w) != "-") c << "        pl" << a << "_" << v << " += sr" << a << "_" << v << ";\n";
+        c << "    };\n";
     }
     // written fields: each thread's column pointers (fixed); caller goals take
     // the interior, crossing arrays the cells of their footprint this CTA owns
@@ -1204,13 +1211,17 @@ int launch_codegen(hfav_plan_t* p, const Schedule& s, void* const* ax, void* con
             if ((rc = scratch(p, "inout_rb_" + std::to_string(S.loads[l]), (size_t)nrb * es, &rb))) return rc;
             const auto ai = std::find(d.axioms.begin(), d.axioms.end(), S.loads[l]);
             const GArr src = caller_view_cg(p, ax[ai - d.axioms.begin()]);
-            const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((ncb + nrb + 255) / 256, 152 * 8));
-            if (es == 8)
-                inout_bands<double><<<blocks, 256, 0, st>>>(src, (double*)cb, (double*)rb, nx, ny, S.TXc, X.CH, F.hxlo,
-                                                            F.hxhi, F.hylo, F.hyhi, HXa, HYa, (int)X.strips, (int)chunks);
-            else
-                inout_bands<float><<<blocks, 256, 0, st>>>(src, (float*)cb, (float*)rb, nx, ny, S.TXc, X.CH, F.hxlo,
-                                                           F.hxhi, F.hylo, F.hyhi, HXa, HYa, (int)X.strips, (int)chunks);
+            const int rows = ny + F.hylo + F.hyhi, cols = nx + F.hxlo + F.hxhi;
+            const int pairs = (int)(X.strips * rows);
+            const dim3 gc((pairs + 255) / 256), gr((cols + 255) / 256, (unsigned)(chunks * HYa));
+            if (es == 8) {
+                inout_colband<double><<<gc, 256, 0, st>>>(src, (double*)cb, nx, ny, S.TXc, F.hxlo, F.hylo, rows, HXa, pairs);
+                inout_rowband<double><<<gr, 256, 0, st>>>(src, (double*)rb, nx, ny, X.CH, F.hxlo, F.hylo, cols, HYa);
+            } else {
+                inout_colband<float><<<gc, 256, 0, st>>>(src, (float*)cb, nx, ny, S.TXc, F.hxlo, F.hylo, rows, HXa, pairs);
+                inout_rowband<float><<<gr, 256, 0, st>>>(src, (float*)rb, nx, ny, X.CH, F.hxlo, F.hylo, cols, HYa);
+            }
+            HFAV_LAUNCHED(p->rt, "codegen_inout_bands", st);
             HFAV_LAUNCHED(p->rt, "codegen_inout_bands", st);
             A.add((const void*)cb);
             A.add((const void*)rb);

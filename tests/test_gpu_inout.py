@@ -50,8 +50,8 @@ def test_chain_as_rule_bodies_in_place(schedule, shape):
     u = I.chain2d_input(shape[0], seed=1, ny=shape[1])
     ref, got, P = _twice(D, [u], 2, schedule)
     assert np.array_equal(ref, got)
-    if schedule.startswith("full"):   # the bands kernel and the update, no snapshot copy
-        assert P.status()["last_launches"] == 2
+    if schedule.startswith("full"):   # the two band kernels and the update, no snapshot copy
+        assert P.status()["last_launches"] == 3
 
 
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
