@@ -8,10 +8,13 @@ project's autotuner picks among the fused variants) vs the unfused form
 
 Other workloads (``--workload``): the FP32-bulk Godunov at 4096^2, the batch
 of 64 uneven FP32 grids for 100 steps through a captured CUDA graph, the 2D
-three-stage chain at 256^2 FP64 and the 3D four-stage chain at 512^3 FP32.
+three-stage chain at 256^2 FP64 and 16384^2 FP32, the 3D four-stage chain at
+512^3 FP32, the COSMO diffusion at 1024 x 1024 x 64 FP32, and, on kernels
+generated at run time, the 2D chain written as rule bodies (out of place and
+in place) and the normalization example at 16384^2 FP32.
 
 Prints one JSON line per workload (rank 0).  Under torchrun each rank runs
-its own replica (one grid is not sharded by this build: "replicas only");
+its own replica (a grid is not sharded across GPUs: "replicas only");
 value = all ranks' cell updates / max time.  ``--impl reference`` times the
 CPU oracle on a bounded sample of the same workload.
 """
