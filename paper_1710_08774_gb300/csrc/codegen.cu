@@ -1170,16 +1170,10 @@ int launch_codegen(hfav_plan_t* p, const Schedule& s, void* const* ax, void* con
         const int64_t resident = (int64_t)std::max(1, sms) * std::max(1, per_sm);
         X.strips = (nx + S.TXc - 1) / S.TXc;
         const int fill = S.yhi - S.ylo;
-        // an in-place launch also copies its chunks' boundary rows first: chunks
-        // of at least 32 band heights keep that copy within 1/32 of the array
-        int min_ch = 1;
-        for (size_t l = 0; l < S.loads.size(); ++l)
-            if (S.inplace[l]) min_ch = std::max(min_ch, 32 * (S.f[S.loads[l]].hylo + S.f[S.loads[l]].hyhi));
         X.CH = ny;
         double best = 1e300;
         for (int64_t chunks = 1; chunks <= ny; chunks = chunks < 8 ? chunks + 1 : chunks * 5 / 4) {
             const int ch = (int)((ny + chunks - 1) / chunks);
-            if (ch < min_ch && chunks > 1) break;
             const int64_t ctas = X.strips * ((ny + ch - 1) / ch);
             const double cost = (double)(ch + fill) * (double)((ctas + resident - 1) / resident);
             if (cost < best) { best = cost; X.CH = ch; }
