@@ -26,6 +26,7 @@
 #include <nvrtc.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <functional>
@@ -172,11 +173,19 @@ int compile(const std::string& src, const char* name, cudaKernel_t* out) {
 }
 
 // ---- source pieces -------------------------------------------------------------
+// a parameter as a literal of the plan's type: 17 significant digits restore
+// any finite double exactly; infinities and NaNs (no C spelling) by their bits
 std::string lit(double v) {
     char b[64];
+    if (!std::isfinite(v)) {
+        unsigned long long bits;
+        std::memcpy(&bits, &v, sizeof bits);
+        std::snprintf(b, sizeof b, "__longlong_as_double(0x%016llxULL)", bits);
+        return "((T)" + std::string(b) + ")";
+    }
     std::snprintf(b, sizeof b, "%.17g", v);
     std::string s = b;
-    if (s.find_first_of(".eEn") == std::string::npos) s += ".0";
+    if (s.find_first_of(".eE") == std::string::npos) s += ".0";
     return "((T)" + s + ")";
 }
 

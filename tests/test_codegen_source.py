@@ -188,3 +188,19 @@ def test_inplace_sources_compile_with_nvrtc(dtype):
     for u in _units(src):
         rc, log = _compile(L, u)
         assert rc == 0, log
+
+
+def test_non_finite_and_extreme_parameters_compile():
+    """Parameters are baked in as literals: infinities, NaN, subnormals and
+    integers all give a valid, exact literal."""
+    L = _nvrtc()
+    D = H.DagSpec(2)
+    D.rule("EXPR", [("u", (0, 0))], ["o"], params=[float("inf"), float("nan"), 5e-324, 3.0, -float("inf")],
+           expr="fmin(in0, p0) + (p1 != p1 ? p2 : 0) + p3 * in0 + fmax(p4, in0)")
+    D.axiom("u"); D.goal("o")
+    for dt in (H.HFAV_F64, H.HFAV_F32):
+        src = H.Plan(D, [_grid((40, 30), 1)], dt, H.HFAV_BC_PERIODIC, "full:smem:32x4").source()
+        assert "__longlong_as_double(0x7ff0000000000000ULL)" in src and "4.9406564584124654e-324" in src
+        for u in _units(src):
+            rc, log = _compile(L, u)
+            assert rc == 0, log
