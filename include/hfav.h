@@ -132,8 +132,8 @@ typedef enum {
      * field = the sum / the maximum of the input over the interior cells,
      * accumulated in FP64.  Rule bodies (HFAV_OP_EXPR) over rank-0 inputs
      * finalize such results (e.g. a root); a rule body over the grid reads a
-     * rank-0 field at offset 0 as one value (a broadcast).  A rank-0 field is
-     * neither an axiom nor a goal.  Such DAGs run on generated kernels, 2D
+     * rank-0 field at offset 0 as one value (a broadcast), next to at least one
+     * grid field.  A rank-0 field is neither an axiom nor a goal.  Such DAGs run on generated kernels, 2D
      * only: the fused form is one kernel per fusion group (the reduction
      * splits the DAG), the unfused form one kernel per rule; the partials of
      * each reduction are combined in a fixed order (bitwise repeatable). */

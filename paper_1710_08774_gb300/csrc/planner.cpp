@@ -867,10 +867,13 @@ int recognise(hfav_plan_t* p) {
         const int o = r.out[0];
         if (r.op == HFAV_OP_EXPR) {
             expr = true;
+            bool reads_grid = false;
             for (auto& x : r.in) {
                 if (grid(x.field) && !grid(o)) return HFAV_EUNSUPPORTED;   // grid -> scalar only by a reduction
                 if (!grid(x.field) && (x.off[0] || x.off[1] || x.off[2])) return HFAV_EUNSUPPORTED;
+                reads_grid = reads_grid || grid(x.field);
             }
+            if (grid(o) && !reads_grid) return HFAV_EUNSUPPORTED;   // a grid field from scalars alone
             continue;
         }
         if (r.op == HFAV_OP_REDUCE_SUM || r.op == HFAV_OP_REDUCE_MAX) {

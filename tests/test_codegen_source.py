@@ -204,3 +204,28 @@ def test_non_finite_and_extreme_parameters_compile():
         for u in _units(src):
             rc, log = _compile(L, u)
             assert rc == 0, log
+
+
+def test_unsupported_scalar_forms_refused():
+    """A grid field from scalars alone, a scalar read at an offset, a scalar
+    goal, and a reduction in 3D have no generated kernels (EUNSUPPORTED)."""
+    def dag(build, ndim=2):
+        D = H.DagSpec(ndim)
+        D.field("s", rank=0)
+        build(D)
+        return D
+    cases = [
+        lambda D: (D.rule("REDUCE_SUM", ["u"], ["s"]), D.rule("EXPR", ["s"], ["o"], expr="in0"), D.axiom("u"), D.goal("o")),
+        lambda D: (D.rule("REDUCE_SUM", ["u"], ["s"]), D.rule("EXPR", ["u", ("s", (1, 0))], ["o"], expr="in0 + in1"),
+                   D.axiom("u"), D.goal("o")),
+        lambda D: (D.rule("REDUCE_SUM", ["u"], ["s"]), D.axiom("u"), D.goal("s")),
+    ]
+    for build in cases:
+        with pytest.raises(H.HfavError):
+            H.Plan(dag(build), [_grid((32, 32), 1)])
+    D3 = H.DagSpec(3)
+    D3.field("s", rank=0)
+    D3.rule("REDUCE_SUM", ["u"], ["s"]); D3.rule("EXPR", ["u", "s"], ["o"], expr="in0 - in1")
+    D3.axiom("u"); D3.goal("o")
+    with pytest.raises(H.HfavError):
+        H.Plan(D3, [H.Grid.of(np.zeros((10, 10, 10)), 1)])
