@@ -393,7 +393,6 @@ std::string red_final(int k, bool mx, bool f64) {
 struct SField {
     int hxlo = 0, hxhi = 0, hylo = 0, hyhi = 0;
     int w = 0;          // ring row width: TXc + hxlo + hxhi
-    int wp = 0;         // ring row stride: w rounded up to a multiple of V
     int lead = 0;       // computed at step s: row s - lead
     int W = 0;          // ring rows (0: not stored)
     bool scalar = false, inl = false;
@@ -489,7 +488,6 @@ int stream_geometry_v(const hfav_plan_t* p, const Schedule& s, const Part& P, in
     for (int f = 0; f < nf; ++f) {
         SField& F = S->f[f];
         F.w = S->TXc + F.hxlo + F.hxhi;
-        F.wp = (F.w + S->V - 1) / S->V * S->V;
         if (F.rule >= 0 && !F.scalar && F.goal < 0 && F.cross < 0 && readers[f] > 0 && off0[f]) {
             bool ok = true;
             for (int r : P.rules)
@@ -537,9 +535,9 @@ int stream_geometry_v(const hfav_plan_t* p, const Schedule& s, const Part& P, in
     for (int f = 0; f < nf; ++f) {
         SField& F = S->f[f];
         if (F.inl || !involved[f] || (F.scalar && F.red < 0)) continue;
-        if (F.W > 0) {   // W rows of wp, then 2 V elements that the last row's vector reads may touch
+        if (F.W > 0) {
             F.off = S->smem;
-            S->smem += ((size_t)(F.W * F.wp + 2 * S->V) * es + 15) / 16 * 16;
+            S->smem += ((size_t)F.W * F.w * es + 15) / 16 * 16;
         }
         S->ylo = std::min(S->ylo, -F.hylo + F.lead);
         S->yhi = std::max(S->yhi, F.hyhi + F.lead);
@@ -680,14 +678,13 @@ std::string stream_source(const hfav_plan_t* p, const Stream& S, const Part& P, 
     auto slot = [](const std::string& row, int W) {   // ring row of a (possibly negative) row index
         return "((unsigned)(" + row + " + " + std::to_string(1024 * W) + ") % " + std::to_string(W) + "u)";
     };
-    // Thread t owns the V consecutive ring columns V t .. V t + V - 1 of every
-    // ring row.  Ring rows are padded to a multiple of V, so a thread's columns
-    // of any row are one aligned vector: each rule reads every (input, row) it
-    // needs with a few vector loads and shares them between its V cells.
-    const char* lanes[4] = {"x", "y", "z", "w"};
-    const std::string VT = V == 1 ? std::string(f64 ? "double" : "float")
-                                  : std::string(f64 ? "double" : "float") + std::to_string(V);
-    auto lane = [&](int v) { return V == 1 ? std::string("") : std::string(".") + lanes[v]; };
+    // a thread's columns tid + v NT, v < V, of a ring row of width w: the
+    // condition that column set v is inside ("" when always, "-" never)
+    auto inside = [&](int v, int w) -> std::string {
+        if (w - v * NT >= NT) return "";
+        if (w - v * NT <= 0) return "-";
+        return "tid < " + std::to_string(w - v * NT);
+    };
     std::ostringstream c;
     c << prelude(f64)
       << "__device__ __forceinline__ void hfav_cp(void* dst, const void* src) {\n"
@@ -702,10 +699,11 @@ std::string stream_source(const hfav_plan_t* p, const Stream& S, const Part& P, 
         if (in_part(P, r)) c << rule_fn(d.rules[r], "hfav_body" + std::to_string(r));
     c << "extern \"C\" __global__ void __launch_bounds__(" << NT << ") " << name << "(";
     // an in-place load shares its array with a goal: no __restrict__ on it
-    for (size_t a = 0; a < S.loads.size(); ++a) {
-        const std::string x = "x" + std::to_string(a), ap = array_params(x, false);
-        c << (S.inplace[a] ? "const T* " + x + ap.substr(ap.find(',')) : ap) << ", ";
-    }
+    for (size_t a = 0; a < S.loads.size(); ++a)
+        c << (S.inplace[a] ? "const T* " + ("x" + std::to_string(a)) + array_params("x" + std::to_string(a), false).substr(
+                                 array_params("x" + std::to_string(a), false).find(','))
+                           : array_params("x" + std::to_string(a), false))
+          << ", ";
     for (size_t a = 0; a < S.goals.size(); ++a) c << array_params("y" + std::to_string(a), true) << ", ";
     for (size_t a = 0; a < S.crosses.size(); ++a) c << array_params("z" + std::to_string(a), true) << ", ";
     for (size_t a = 0; a < S.loads.size(); ++a)
@@ -713,7 +711,6 @@ std::string stream_source(const hfav_plan_t* p, const Stream& S, const Part& P, 
     c << "const double* __restrict__ scal, double* __restrict__ part, int nx, int ny, int CH) {\n"
       << "    extern __shared__ __align__(16) unsigned char smem[];\n"
       << "    const int tid = threadIdx.x, i0 = blockIdx.x * " << TXc << ", j0 = blockIdx.y * CH;\n"
-      << "    const int c0 = " << V << " * tid;   // this thread's first ring column\n"
       << "    const int jn = min(CH, ny - j0);\n"
       << "    const bool last_x = i0 + " << TXc << " >= nx, last_y = j0 + jn >= ny;\n";
     for (int f = 0; f < d.n_fields; ++f)
@@ -736,13 +733,14 @@ std::string stream_source(const hfav_plan_t* p, const Stream& S, const Part& P, 
         const int HXa = std::max(1, F.hxlo + F.hxhi), HYa = std::max(1, F.hylo + F.hyhi);
         for (int v = 0; v < V; ++v) {
             const std::string cv = a + "_" + std::to_string(v);
+            if (inside(v, F.w) == "-") continue;
             if (!inpl) {
-                c << "    int col" << cv << " = i0 - " << F.hxlo << " + c0 + " << v << ";\n"
+                c << "    int col" << cv << " = i0 - " << F.hxlo << " + tid + " << v * NT << ";\n"
                   << "    if (" << x << "_w) col" << cv << " = hfav_wrap(col" << cv << ", nx);\n"
                   << "    else col" << cv << " = min(max(col" << cv << ", -" << F.hxlo << "), nx - 1 + " << F.hxhi << ");\n"
                   << "    const T* src" << cv << " = " << x << " + col" << cv << " + " << x << "_o0;\n";
             } else {
-                c << "    const int xv" << cv << " = c0 + " << v - F.hxlo << ";\n"
+                c << "    const int xv" << cv << " = tid + " << v * NT - F.hxlo << ";\n"
                   << "    const bool live" << cv << " = xv" << cv << " >= 0 && xv" << cv << " < wint;\n"
                   << "    const int kb" << cv << " = min(max(xv" << cv << " < 0 ? xv" << cv << " + " << F.hxlo << " : "
                   << F.hxlo << " + xv" << cv << " - wint, 0), " << HXa - 1 << ");\n"
@@ -767,17 +765,19 @@ std::string stream_source(const hfav_plan_t* p, const Stream& S, const Part& P, 
               << "            const T* const rrow = rb" << a << " + ((long long)blockIdx.y * " << HYa << " + min(max(r < 0 ? r + "
               << F.hylo << " : " << F.hylo << " + r - jn, 0), " << HYa - 1 << ")) * (nx + " << F.hxlo + F.hxhi << ");\n";
         }
-        c << "            T* const dst = s" << f << " + " << slot("r", F.W) << " * " << F.wp << " + c0;\n";
+        c << "            T* const dst = s" << f << " + " << slot("r", F.W) << " * " << F.w << " + tid;\n";
         for (int v = 0; v < V; ++v) {
-            const std::string cv = a + "_" + std::to_string(v);
-            c << "            if (c0 + " << v << " < " << F.w << ") hfav_cp(dst + " << v << ", ";
+            const std::string in = inside(v, F.w), cv = a + "_" + std::to_string(v);
+            if (in == "-") continue;
+            c << "            " << (in.empty() ? "" : "if (" + in + ") ") << "hfav_cp(dst + " << v * NT << ", ";
             if (!inpl) c << "src" << cv << " + ro);\n";
             else c << "band ? rrow + rcol" << cv << " : pl" << cv << ");\n";
         }
         c << "        }\n";
         // the fetches run for consecutive rows: each thread's live row pointers step by one row
         if (inpl)
-            for (int v = 0; v < V; ++v) c << "        pl" << a << "_" << v << " += sr" << a << "_" << v << ";\n";
+            for (int v = 0; v < V; ++v)
+                if (inside(v, F.w) != "-") c << "        pl" << a << "_" << v << " += sr" << a << "_" << v << ";\n";
         c << "    };\n";
     }
     // written fields: each thread's column pointers (fixed); caller goals take
@@ -792,7 +792,8 @@ std::string stream_source(const hfav_plan_t* p, const Stream& S, const Part& P, 
             const std::string y = (kind == 0 ? "y" : "z") + std::to_string(idx);
             for (int v = 0; v < V; ++v) {
                 const std::string g = y + "_" + std::to_string(v);
-                c << "    const int gx" << g << " = c0 + " << v - F.hxlo << ";\n";
+                if (inside(v, F.w) == "-") continue;
+                c << "    const int gx" << g << " = tid + " << v * NT - F.hxlo << ";\n";
                 if (kind == 0)
                     c << "    const bool gok" << g << " = gx" << g << " >= 0 && gx" << g << " < " << TXc << " && i0 + gx" << g
                       << " < nx;\n";
@@ -826,74 +827,41 @@ std::string stream_source(const hfav_plan_t* p, const Stream& S, const Part& P, 
             const int f = R.out[0];
             const SField& F = S.f[f];
             if (F.inl) continue;
-            // the (ring field, row) groups the rule reads, inlined stages
-            // expanded, each with its column offsets relative to the cell
-            std::map<std::pair<int, int>, std::set<int>> groups;
-            std::function<void(int, int, int)> collect = [&](int g, int dx, int dy) {
-                const SField& G = S.f[g];
-                if (G.scalar) return;
-                if (G.inl) {
-                    for (const hfav_ref& x : d.rules[G.rule].in) collect(x.field, dx + x.off[0], dy + x.off[1]);
-                    return;
-                }
-                groups[{g, dy}].insert(dx + G.hxlo - F.hxlo);
-            };
-            for (const hfav_ref& x : R.in) collect(x.field, x.off[0], x.off[1]);
             c << "        {\n"
               << "            const int r = s - " << F.lead << ";\n"
-              << "            if (r >= -" << F.hylo << " && r < jn + " << F.hyhi << " && c0 < " << F.w << ") {\n";
-            // each group's columns c0 + lo .. c0 + hi + V - 1 as aligned vectors
-            std::map<std::pair<int, int>, int> a0_of;
-            int gi = 0;
-            std::map<std::pair<int, int>, int> name_of;
-            for (auto& kv : groups) {
-                const int g = kv.first.first, dy = kv.first.second;
-                const SField& G = S.f[g];
-                const int lo = *kv.second.begin(), hi = *kv.second.rbegin() + V - 1;   // lo >= 0: footprints nest
-                const int a0 = lo / V * V, a1 = hi / V * V, nvec = (a1 - a0) / V + 1;
-                a0_of[kv.first] = a0;
-                name_of[kv.first] = gi;
-                const int base = cslot(k, F.lead, dy, G.W) * G.wp + a0;
-                c << "                T e" << gi << "[" << nvec * V << "];\n";
-                for (int q = 0; q < nvec; ++q) {
-                    c << "                { const " << VT << " t = *(const " << VT << "*)(s" << g << " + " << base + q * V
-                      << " + c0);";
-                    for (int v = 0; v < V; ++v) c << " e" << gi << "[" << q * V + v << "] = t" << lane(v) << ";";
-                    c << " }\n";
-                }
-                ++gi;
-            }
-            // the value of field g at cell v of this thread shifted by (dx, dy)
-            std::function<std::string(int, int, int, int)> read = [&](int g, int dx, int dy, int v) -> std::string {
-                const SField& G = S.f[g];
-                if (G.scalar) return "sv" + std::to_string(g);
-                if (G.inl) {
-                    const Rule& Q = d.rules[G.rule];
-                    std::string val = "hfav_body" + std::to_string(G.rule) + "(";
-                    for (size_t q = 0; q < Q.in.size(); ++q)
-                        val += (q ? ", " : "") + read(Q.in[q].field, dx + Q.in[q].off[0], dy + Q.in[q].off[1], v);
-                    return val + ")";
-                }
-                const std::pair<int, int> key{g, dy};
-                return "e" + std::to_string(name_of[key]) + "[" + std::to_string(v + dx + G.hxlo - F.hxlo - a0_of[key]) +
-                       "]";
-            };
-            if (F.W > 0 && F.red < 0) c << "                " << VT << " o;\n";
+              << "            if (r >= -" << F.hylo << " && r < jn + " << F.hyhi << ") {\n";
             for (int v = 0; v < V; ++v) {
-                c << "                {\n";
+                const std::string in = inside(v, F.w);
+                if (in == "-") continue;
+                // the value of field g at this thread's cell (column set v) shifted by (dx, dy)
+                std::function<std::string(int, int, int)> read = [&](int g, int dx, int dy) -> std::string {
+                    const SField& G = S.f[g];
+                    if (G.scalar) return "sv" + std::to_string(g);
+                    if (G.inl) {
+                        const Rule& Q = d.rules[G.rule];
+                        std::string val = "hfav_body" + std::to_string(G.rule) + "(";
+                        for (size_t q = 0; q < Q.in.size(); ++q)
+                            val += (q ? ", " : "") + read(Q.in[q].field, dx + Q.in[q].off[0], dy + Q.in[q].off[1]);
+                        return val + ")";
+                    }
+                    return "s" + std::to_string(g) + "[" +
+                           std::to_string(cslot(k, F.lead, dy, G.W) * G.w + dx + G.hxlo - F.hxlo + v * NT) + " + tid]";
+                };
+                c << "            " << (in.empty() ? "{" : "if (" + in + ") {") << "\n";
                 for (size_t q = 0; q < R.in.size(); ++q)
-                    c << "                const T in" << q << " = " << read(R.in[q].field, R.in[q].off[0], R.in[q].off[1], v)
+                    c << "                const T in" << q << " = " << read(R.in[q].field, R.in[q].off[0], R.in[q].off[1])
                       << ";\n";
                 if (F.red >= 0) {
                     // a reduction: the input's value over this CTA's interior cells
-                    const std::string x = "(c0 + " + std::to_string(v - F.hxlo) + ")";
+                    const std::string x = "(tid + " + std::to_string(v * NT - F.hxlo) + ")";
                     c << "                if (" << x << " < " << TXc << " && i0 + " << x << " < nx)\n"
-                      << "                    " << red_add(F.red, R.op == HFAV_OP_REDUCE_MAX, f64, "in0") << "\n"
-                      << "                }\n";
+                      << "                    " << red_add(F.red, R.op == HFAV_OP_REDUCE_MAX, f64, "in0") << "\n";
+                    c << "            }\n";
                     continue;
                 }
                 c << "                const T v = " << rule_call(R, "hfav_body" + std::to_string(r)) << ";\n";
-                if (F.W > 0) c << "                o" << lane(v) << " = v;\n";
+                if (F.W > 0)
+                    c << "                s" << f << "[" << cslot(k, F.lead, 0, F.W) * F.w + v * NT << " + tid] = v;\n";
                 if (F.goal >= 0) {
                     const std::string g = "y" + std::to_string(F.goal) + "_" + std::to_string(v);
                     c << "                if (r >= 0 && r < jn && gok" << g << ")\n"
@@ -904,10 +872,8 @@ std::string stream_source(const hfav_plan_t* p, const Stream& S, const Part& P, 
                     c << "                if (gok" << g << " && ((r >= 0 && r < jn) || j0 + r < 0 || (last_y && j0 + r >= ny)))\n"
                       << "                    gcol" << g << "[(long long)(j0 + r) * z" << F.cross << "_p1] = v;\n";
                 }
-                c << "                }\n";
+                c << "            }\n";
             }
-            if (F.W > 0 && F.red < 0)
-                c << "                *(" << VT << "*)(s" << f << " + " << cslot(k, F.lead, 0, F.W) * F.wp << " + c0) = o;\n";
             c << "            }\n        }\n";
         }
         c << "        hfav_wait();\n"
