@@ -275,11 +275,14 @@ int hfav_plan_schedule(const hfav_plan_t* plan, char* buf, size_t n);
 int hfav_plan_dump(const hfav_plan_t* plan, char* buf, size_t n);
 
 /* The CUDA C++ source of the kernels a plan of generated kernels (a DAG
- * with HFAV_OP_EXPR rules) compiles under its current schedule: the fused
- * kernel, or one kernel per EXPR rule for 'unfused' -- the emitted code of
- * the method (Sec. 3.6).  Copies up to n - 1 characters and a NUL into buf;
- * HFAV_EINVAL (message: the size needed) when buf is too small,
- * HFAV_EUNSUPPORTED for plans of the builtin kernels.  Needs no device. */
+ * with HFAV_OP_EXPR rules or reductions) compiles under its current
+ * schedule -- the emitted code of the method (Sec. 3.6): one streaming or
+ * pointwise kernel per fusion group (fused) or per rule (unfused), and a
+ * finalization kernel after each part with reductions.  Each separately
+ * compiled unit follows a line starting with "// ---- kernel".  Copies up to
+ * n - 1 characters and a NUL into buf; HFAV_EINVAL (message: the size
+ * needed) when buf is too small, HFAV_EUNSUPPORTED for plans of the builtin
+ * kernels.  Needs no device. */
 int hfav_plan_source(const hfav_plan_t* plan, char* buf, size_t n);
 
 /* Features of the plan under a schedule for the learned cost model: writes
