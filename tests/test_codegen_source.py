@@ -229,3 +229,28 @@ def test_unsupported_scalar_forms_refused():
     D3.axiom("u"); D3.goal("o")
     with pytest.raises(H.HfavError):
         H.Plan(D3, [H.Grid.of(np.zeros((10, 10, 10)), 1)])
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("schedule", ["full:smem:32x4", "unfused:hbm:32x4"])
+def test_generated_units_run_in_dependency_order(seed, schedule):
+    """In the emitted program every scalar a kernel reads (sv<f>) is written by
+    an earlier finalization (scal[f] = ...), and every finalization follows the
+    kernel whose partials it combines."""
+    import re
+    rules, axioms, goals = X.random_reduce_dag(seed)
+    P = H.Plan(X.to_spec_reduce(rules, axioms, goals), [_grid((64, 48), 6)], H.HFAV_F64, H.HFAV_BC_PERIODIC, schedule)
+    src = P.source()
+    units = src.split("// ---- kernel ")[1:]
+    known = set()
+    for k, u in enumerate(units):
+        head = u.split("\n", 1)[0]
+        body = u.split("\n", 1)[1]
+        if head.endswith("finalize"):
+            assert k > 0 and not units[k - 1].split("\n", 1)[0].endswith("finalize")
+            assert "part[" in units[k - 1]          # the preceding kernel writes partials
+            known |= {int(f) for f in re.findall(r"scal\[(\d+)\] = ", body)}
+        else:
+            for f in re.findall(r"\(T\)scal\[(\d+)\]", body):
+                assert int(f) in known, (k, f)
+    assert len(known) == sum(1 for r in rules if r["out"].startswith(("acc", "sc")))
