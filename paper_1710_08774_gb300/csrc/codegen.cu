@@ -1,22 +1,20 @@
-// codegen.cu -- runtime code generation for rule DAGs that carry user rule
-// bodies (HFAV_OP_EXPR): the code generation step of the method (Sec. 3.6:
-// with the fusion and storage analysis done, the fused nests are emitted by a
-// walk of the nest DAG, each kernel invocation in its phase; Sec. 4.1 leaves
-// the emitted scalar loops to a vectorizing compiler), here as CUDA source
-// compiled by NVRTC for the device the plan runs on and launched through the
-// runtime's library API.
+// codegen.cu -- runtime code generation for rule DAGs with user rule bodies
+// (HFAV_OP_EXPR), reductions to scalars, or declared in/out aliasing: the code
+// generation step of the method (Sec. 3.6: with the fusion and storage
+// analysis done, the fused nests are emitted by a walk of the nest DAG, each
+// kernel invocation in its phase; Sec. 4.1 leaves the emitted scalar loops to
+// a vectorizing compiler), here as CUDA source compiled by NVRTC for the
+// device the plan runs on and launched through the runtime's library API.
 //
-// Two forms are generated:
-//   * fused (schedule full:smem:TXxTY, 2D DAGs): one kernel per launch; a CTA
-//     of TX x TY threads owns a TX-wide tile of the goals, up to 8 TY rows
-//     tall; every field gets a shared-memory tile over its footprint (the
-//     tile widened by the field's halo from the planner's analysis, Sec.
-//     3.5), the axioms are loaded once, and the rules are evaluated in
-//     topological order over their footprints, a barrier between rules -- the
-//     contraction of every intermediate to a tile, its halo recomputed by the
-//     neighbouring tiles;
-//   * unfused: one kernel per rule over full arrays (the generic executor's
-//     storage) for the EXPR rules of an unfused plan.
+// What is generated (details at each generator below):
+//   * fused 2D plans: one kernel per fusion group of the analysis -- a
+//     streaming kernel whose fields live in rolling row rings in shared memory
+//     (Sec. 3.5 "Contraction"), or, for a group without offsets, a pointwise
+//     kernel in registers; reductions accumulate inside the group that
+//     produces their input and a one-CTA finalization combines them (Sec. 3.4);
+//   * unfused plans: one kernel per rule;
+//   * in-place runs of declared in/out pairs: two small kernels that save the
+//     halo bands the streaming kernel cannot read live.
 // Rule bodies are C expressions over in0 .. in{n-1} (the rule's inputs at
 // their offsets) and p0 .. p{m-1} (its parameters, baked in as constants),
 // evaluated in the plan's precision inside a device function that sees
