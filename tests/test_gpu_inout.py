@@ -134,3 +134,32 @@ def test_autotune_leaves_in_place_arrays_unchanged():
     P.autotune([u], [u], reps=1)
     torch.cuda.synchronize()
     assert torch.equal(u[2:-2, 2:-2], keep[2:-2, 2:-2])
+
+
+def test_split_dag_with_reduction_in_place():
+    """Rule bodies, a maximum broadcast back, and an in-place update (the
+    README example): the split makes two parts, so the run reads a snapshot."""
+    import torch
+    from oracle import expr as E
+    D = H.DagSpec(2)
+    D.rule("EXPR", [("u", (1, 0)), ("u", (-1, 0)), ("u", (0, 1)), ("u", (0, -1)), ("u", (0, 0))], ["lap"],
+           params=[4.0], expr="in0 + in1 + in2 + in3 - p0 * in4")
+    D.field("m", rank=0)
+    D.rule("REDUCE_MAX", ["lap"], ["m"])
+    D.rule("EXPR", ["u", "lap", "m"], ["out"], params=[0.1], expr="in0 + p0 * in1 / fmax(in2, (T)1)")
+    D.axiom("u"); D.goal("out"); D.inout("out", "u")
+    rng = np.random.default_rng(12)
+    core = rng.uniform(0, 1, (300, 500))
+    u = np.full((304, 504), np.nan)
+    u[2:-2, 2:-2] = core
+    ut = to_dev(u)
+    P = H.Plan(D, [H.Grid.of(ut, 2)], H.HFAV_F64, H.HFAV_BC_PERIODIC, "full:smem:32x8")
+    P.run([ut], [ut])
+    torch.cuda.synchronize()
+    rules = [("lap", [("u", (1, 0)), ("u", (-1, 0)), ("u", (0, 1)), ("u", (0, -1)), ("u", (0, 0))],
+              lambda a, b, c, d, e: a + b + c + d - 4.0 * e, []),
+             ("m", [("lap", (0, 0))], "max", []),
+             ("out", [("u", (0, 0)), ("lap", (0, 0)), ("m", (0, 0))], lambda a, b, c: a + 0.1 * b / np.maximum(c, 1.0), [])]
+    ref = E.evaluate(rules, {"u": core})["out"]
+    got = ut[2:-2, 2:-2].cpu().numpy()
+    assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) <= 1e-12
