@@ -7,8 +7,10 @@ HFAV_OP_EXPR) against the oracle, through the C ABI.
 - Seeded random DAGs (several axioms and goals, offsets in every direction,
   chains of up to 6 rules) against oracle/expr.py: fused and unfused, 2D and
   3D, periodic and halo-given, FP64 and FP32.
-- Rule bodies mixed with builtin ops in one fused kernel; CUDA-graph replay;
-  a body that does not compile fails the run cleanly.
+- Rule bodies mixed with builtin ops in one fused kernel; nested pointwise
+  stages evaluated inside their readers; rings above the default 48 KB of
+  shared memory; CUDA-graph replay; a body that does not compile fails the run
+  cleanly.
 FP32 bar: 2e-5 normwise -- a chain of up to 6 bodies of a few FP32 roundings
 (relative 6e-8) each, on O(1) values whose bodies are Lipschitz with small
 constants.
