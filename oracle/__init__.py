@@ -49,6 +49,7 @@ def lib():
                                    ctypes.c_int, ctypes.c_double, dp, dp, dp, dp]
         L.oracle_riemann.argtypes = [dp, dp, ctypes.c_double, dp, ctypes.POINTER(ctypes.c_int),
                                      ctypes.POINTER(ctypes.c_long)]
+        L.oracle_trace.argtypes = [dp, ctypes.c_double, dp, ctypes.c_double, dp, dp]
         L.oracle_godunov.argtypes = [dp, ctypes.c_long, ctypes.c_long, ctypes.c_int, ctypes.c_double,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_int, dp,
                                      ctypes.POINTER(GodunovStats)]
@@ -114,6 +115,16 @@ def riemann(qL, qR, gamma=1.4):
     g = np.empty(4); nc = ctypes.c_int(0); fh = ctypes.c_long(0)
     it = lib().oracle_riemann(_p(a), _p(b), gamma, _p(g), ctypes.byref(nc), ctypes.byref(fh))
     return g, it, bool(nc.value), fh.value
+
+
+def trace(W, c, dW, dtdx):
+    """Characteristic tracing of one cell: primitive state W = (rho, u_n, u_t, p),
+    sound speed c, limited slopes dW, dt/dx.  Returns (qm, qp): the states at
+    the cell's left and right faces."""
+    a = np.ascontiguousarray(W, dtype=np.float64); d = np.ascontiguousarray(dW, dtype=np.float64)
+    qm = np.empty(4); qp = np.empty(4)
+    lib().oracle_trace(_p(a), float(c), _p(d), float(dtdx), _p(qm), _p(qp))
+    return qm, qp
 
 
 def godunov(U, nsteps, cfl=0.5, gamma=1.4, dt_fixed=0.0, sweeps=3):

@@ -262,6 +262,40 @@ int oracle_riemann(const double* qL, const double* qR, double g, double* gdnv,
     return it;
 }
 
+/*
+ * trace: characteristic tracing of one cell, MUSCL-Hancock form (the Hydro2D
+ * kernel "trace", Sec. 5.4; the paper names it only).  W = (rho, u_n, u_t, p),
+ * c its sound speed, dW its limited slopes, dtdx = dt/dx.  Wave strengths
+ * alpha = L dW, eigenvalues (u-c, u, u, u+c), right eigenvectors r_k;
+ *   face-right state (at a+1/2): qp = W + 1/2 sum (1 - nu_k) alpha_k r_k,
+ *   face-left state (at a-1/2):  qm = W - 1/2 sum (1 + nu_k) alpha_k r_k,
+ * with nu_k = lambda_k dt/dx.
+ */
+void oracle_trace(const double* W, double c, const double* dW, double dtdx, double* qm, double* qp) {
+    const double r = W[0], u = W[1];
+    const double dr = dW[0], du = dW[1], dv = dW[2], dp = dW[3];
+    double alpha[4], lam[4], rv[4][4];
+    alpha[0] = (dp / c - r * du) / (2.0 * c);
+    alpha[1] = dr - dp / (c * c);
+    alpha[2] = dv;
+    alpha[3] = (dp / c + r * du) / (2.0 * c);
+    lam[0] = u - c; lam[1] = u; lam[2] = u; lam[3] = u + c;
+    rv[0][0] = 1.0; rv[0][1] = -c / r; rv[0][2] = 0.0; rv[0][3] = c * c;
+    rv[1][0] = 1.0; rv[1][1] = 0.0;    rv[1][2] = 0.0; rv[1][3] = 0.0;
+    rv[2][0] = 0.0; rv[2][1] = 0.0;    rv[2][2] = 1.0; rv[2][3] = 0.0;
+    rv[3][0] = 1.0; rv[3][1] = c / r;  rv[3][2] = 0.0; rv[3][3] = c * c;
+    for (int f = 0; f < 4; ++f) {
+        double sp = 0.0, sm = 0.0;
+        for (int m = 0; m < 4; ++m) {
+            double nu = lam[m] * dtdx;
+            sp += (1.0 - nu) * alpha[m] * rv[m][f];
+            sm += (1.0 + nu) * alpha[m] * rv[m][f];
+        }
+        qp[f] = W[f] + 0.5 * sp;
+        qm[f] = W[f] - 0.5 * sm;
+    }
+}
+
 /* Godunov work arrays: every intermediate of one sweep, fully materialised
  * over the padded (ny+4) x (nx+4) grid.  4 (U) + 4 (W) + 1 (c) + 4 (dW)
  * + 8 (face-left/right traces) + 8 (qL/qR) + 4 (Riemann state) + 4 (flux)
@@ -356,38 +390,14 @@ static void godunov_sweep(gwork* w, int dir, double dt, double dx, double g,
                 w->dW[f][gidx(w, dir, a, b)] = minmod(q0 - qm1, qp1 - q0);
             }
 
-    /* trace: characteristic tracing, MUSCL-Hancock form.  Wave strengths
-     * alpha = L dW, eigenvalues (u-c, u, u, u+c), right eigenvectors r_k;
-     * face-right state (at a+1/2) = W + 1/2 sum (1 - nu_k) alpha_k r_k,
-     * face-left state (at a-1/2)  = W - 1/2 sum (1 + nu_k) alpha_k r_k,
-     * with nu_k = lambda_k dt/dx. */
+    /* trace: characteristic tracing (oracle_trace), cell by cell */
     for (long b = 0; b < nb; ++b)
         for (long a = -1; a < na + 1; ++a) {
             long k = gidx(w, dir, a, b);
-            double r = w->W[0][k], u = w->W[1][k], v = w->W[2][k], p = w->W[3][k];
-            double c = w->c[k];
-            double dr = w->dW[0][k], du = w->dW[1][k], dv = w->dW[2][k], dp = w->dW[3][k];
-            double alpha[4], lam[4], rv[4][4];
-            alpha[0] = (dp / c - r * du) / (2.0 * c);
-            alpha[1] = dr - dp / (c * c);
-            alpha[2] = dv;
-            alpha[3] = (dp / c + r * du) / (2.0 * c);
-            lam[0] = u - c; lam[1] = u; lam[2] = u; lam[3] = u + c;
-            rv[0][0] = 1.0; rv[0][1] = -c / r; rv[0][2] = 0.0; rv[0][3] = c * c;
-            rv[1][0] = 1.0; rv[1][1] = 0.0;    rv[1][2] = 0.0; rv[1][3] = 0.0;
-            rv[2][0] = 0.0; rv[2][1] = 0.0;    rv[2][2] = 1.0; rv[2][3] = 0.0;
-            rv[3][0] = 1.0; rv[3][1] = c / r;  rv[3][2] = 0.0; rv[3][3] = c * c;
-            double Wc[4] = {r, u, v, p};
-            for (int f = 0; f < 4; ++f) {
-                double sp = 0.0, sm = 0.0;
-                for (int m = 0; m < 4; ++m) {
-                    double nu = lam[m] * dtdx;
-                    sp += (1.0 - nu) * alpha[m] * rv[m][f];
-                    sm += (1.0 + nu) * alpha[m] * rv[m][f];
-                }
-                w->qp[f][k] = Wc[f] + 0.5 * sp;
-                w->qm[f][k] = Wc[f] - 0.5 * sm;
-            }
+            double Wc[4], dWc[4], qm[4], qp[4];
+            for (int f = 0; f < 4; ++f) { Wc[f] = w->W[f][k]; dWc[f] = w->dW[f][k]; }
+            oracle_trace(Wc, w->c[k], dWc, dtdx, qm, qp);
+            for (int f = 0; f < 4; ++f) { w->qm[f][k] = qm[f]; w->qp[f][k] = qp[f]; }
         }
 
     /* qleftright: the face a+1/2 is stored at index a, for a in [-1, na) */

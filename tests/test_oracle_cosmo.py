@@ -9,6 +9,8 @@
 * u = i^4 (halo given) makes every flux_x counter-gradient (flux and du have
   the same sign), so the limiter zeroes all of them and out = u exactly; the
   unlimited value would be u - 24 c.
+* u = j^4 does the same to every flux_y, the limiter along j; the
+  unlimited value would again be u - 24 c.
 * Quadratics have a constant Laplacian, hence zero fluxes and out = u exactly.
 * Periodic data: the update is in flux form, so the sum over a plane is
   conserved (to rounding).
@@ -49,6 +51,16 @@ def test_limiter_zeroes_counter_gradient_fluxes():
     u = (i.astype(np.float64)) ** 4
     lap, flx, fly, out = oracle.cosmo(u, c, periodic=False)
     assert np.all(lap[:, 1:-1, 1:-1] == 12.0 * (np.arange(nx) ** 2) + 2.0)
+    assert np.all(flx == 0.0) and np.all(fly == 0.0)
+    assert np.all(out == u[2:-2, 2:-2, 2:-2])
+
+
+def test_limiter_zeroes_counter_gradient_fluxes_in_j():
+    nx, ny, nz, c = 7, 18, 2, 0.1
+    k, j, i = np.meshgrid(np.arange(-2, nz + 2), np.arange(-2, ny + 2), np.arange(-2, nx + 2), indexing="ij")
+    u = (j.astype(np.float64)) ** 4
+    lap, flx, fly, out = oracle.cosmo(u, c, periodic=False)
+    assert np.all(lap[:, 1:-1, 1:-1] == (12.0 * (np.arange(ny) ** 2) + 2.0)[None, :, None])
     assert np.all(flx == 0.0) and np.all(fly == 0.0)
     assert np.all(out == u[2:-2, 2:-2, 2:-2])
 

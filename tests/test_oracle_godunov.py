@@ -11,6 +11,25 @@
   the exact solution (L1 error falls with N, star-region pressure within 1e-3
   of the exact p* = 0.30313); no floors and no Newton non-convergence on the
   Sod-like workloads.
+- Trace (the half-step predictor of the characteristic tracing): a smooth
+  entropy wave (rho = 1 + 0.2 sin 2 pi x, u = 1, p = 1) is advected exactly by
+  the Euler equations, and a MUSCL-Hancock scheme converges to it at second
+  order in L1; without the dt/dx terms of the trace the update is forward Euler
+  in time and the order drops to about one.
+- Trace, one cell: the two face states differ by exactly the slope
+  (qp - qm = dW) and their mean is the half-step predictor
+  (qp + qm = 2 W - dt/dx A(W) dW), where A is the Jacobian of the primitive
+  1D Euler system (rows: rho_t + u rho_x + rho u_x, u_t + u u_x + p_x / rho,
+  v_t + u v_x, p_t + rho c^2 u_x + u p_x) written out as a matrix, not
+  through its eigenvectors.  A wrong wave strength, eigenvector or eigenvalue
+  breaks one of the two identities.
+- Rarefaction fans sampled at x/t = 0: where the sonic point lies inside a
+  weak fan the face state equals the linear interpolation between the outer
+  state and the star state with the weight fixed by the fan's head and tail
+  speeds, here computed from the exact Riemann solution (the two-shock star
+  state differs from the exact one at third order in the wave strength); and
+  the face state is continuous in the data as the fan's head or tail crosses
+  x/t = 0 (the Godunov flux is a continuous function of its two states).
 """
 import math
 
@@ -144,3 +163,103 @@ def test_sod_converges_to_exact():
 def test_exact_star_pressure_sod():
     ps, us = ER.star(1.0, 0.0, 1.0, 0.125, 0.0, 0.1)
     assert abs(ps - 0.30313) < 1e-5 and abs(us - 0.92745) < 1e-5
+
+
+def _entropy_wave_l1(N, T=0.25, ny=4):
+    """L1 density error after advecting rho = 1 + 0.2 sin(2 pi x), u = 1, p = 1
+    to time T (exact solution: the profile shifted by T)."""
+    x = (np.arange(N) + 0.5) / N
+    rho = 1.0 + 0.2 * np.sin(2 * np.pi * x)
+    U = np.empty((4, ny, N))
+    U[0] = rho; U[1] = rho; U[2] = 0.0; U[3] = 1.0 / (G - 1) + 0.5 * rho
+    cmax = 1.0 + math.sqrt(G / 0.8)
+    nsteps = int(math.ceil(T / (0.5 / (cmax * N))))
+    W, _, st = oracle.godunov(U, nsteps, dt_fixed=T / nsteps)
+    assert st.floor_hits == 0 and st.newton_nonconv == 0
+    exact = 1.0 + 0.2 * np.sin(2 * np.pi * (x - T))
+    # the wave is one-dimensional: every row agrees, and v stays zero
+    assert all(np.array_equal(W[:, 0], W[:, j]) for j in range(1, ny))
+    return np.mean(np.abs(W[0, 0] - exact))
+
+
+def test_entropy_wave_second_order():
+    errs = [_entropy_wave_l1(N) for N in (64, 128, 256)]
+    order = math.log2(errs[0] / errs[2]) / 2
+    assert order >= 1.8, (errs, order)
+    assert errs[2] < 1e-4, errs
+
+
+def _primitive_jacobian(W, c):
+    r, u, _, _ = W
+    return np.array([[u, r, 0.0, 0.0],
+                     [0.0, u, 0.0, 1.0 / r],
+                     [0.0, 0.0, u, 0.0],
+                     [0.0, r * c * c, 0.0, u]])
+
+
+def test_trace_identities():
+    rng = np.random.default_rng(11)
+    for _ in range(200):
+        W = np.array([rng.uniform(0.1, 2.0), rng.uniform(-2, 2), rng.uniform(-2, 2), rng.uniform(0.1, 2.0)])
+        c = math.sqrt(G * W[3] / W[0])
+        dW = rng.uniform(-0.3, 0.3, 4)
+        dtdx = rng.uniform(0.0, 0.5) / (abs(W[1]) + c)
+        qm, qp = oracle.trace(W, c, dW, dtdx)
+        scale = np.abs(W) + np.abs(dW) + 1.0
+        assert np.all(np.abs((qp - qm) - dW) <= 1e-13 * scale)
+        pred = 2.0 * W - dtdx * (_primitive_jacobian(W, c) @ dW)
+        assert np.all(np.abs((qp + qm) - pred) <= 1e-13 * scale)
+
+
+def _fan_weight_state(rl, ul, pl, rr, ur, pr):
+    """Face state of a left rarefaction fan that contains x/t = 0, by linear
+    interpolation with the exact solution's star state and fan speeds."""
+    ps, us = ER.star(rl, ul, pl, rr, ur, pr)
+    cl = math.sqrt(G * pl / rl)
+    rs = rl * (ps / pl) ** (1.0 / G)        # isentropic star density
+    cs = math.sqrt(G * ps / rs)
+    head, tail = ul - cl, us - cs
+    assert head < 0.0 < tail and ps < pl    # the sonic point is inside the fan
+    f = (0.0 - tail) / (head - tail)
+    return np.array([f * rl + (1 - f) * rs, f * ul + (1 - f) * us, f * pl + (1 - f) * ps]), f
+
+
+@pytest.mark.parametrize("L,R", [((1.0, 1.0, 1.0), (0.9, 1.2, 0.85)),
+                                 ((1.0, 1.1, 1.0), (0.95, 1.2, 0.9)),
+                                 ((1.0, 1.15, 1.0), (0.9, 1.3, 0.8))])
+def test_transonic_fan_weights(L, R):
+    rl, ul, pl = L; rr, ur, pr = R
+    want, f = _fan_weight_state(rl, ul, pl, rr, ur, pr)
+    assert abs(1 - 2 * f) > 0.4     # reversed weights would move the state by far more than the bar
+    s, _, nc, fh = oracle.riemann([rl, ul, 0.3, pl], [rr, ur, -0.1, pr])
+    assert not nc and fh == 0
+    got = np.array([s[0], s[1], s[3]])
+    assert np.max(np.abs(got - want) / np.abs(want)) <= 2e-3, (got, want)
+    assert s[2] == 0.3              # u* > 0: the transverse velocity of the left side
+    # the mirrored problem (x -> -x: states swapped, normal velocities negated)
+    # puts the same fan on the right side of the contact
+    m, _, _, _ = oracle.riemann([rr, -ur, -0.1, pr], [rl, -ul, 0.3, pl])
+    assert np.allclose([m[0], -m[1], m[3]], got, rtol=1e-13, atol=0) and m[2] == 0.3
+
+
+def test_face_state_continuous_across_fan_edges():
+    """Sweep the left normal velocity so that first the fan's tail and then its
+    head cross x/t = 0; consecutive face states differ by O(step)."""
+    dul = 1e-4
+    prev = None
+    worst = 0.0
+    branches = set()
+    for ul in np.arange(0.7, 1.45, dul):
+        ql = [1.0, ul, 0.0, 1.0]; qr = [0.9, ul + 0.2, 0.0, 0.85]
+        s, _, nc, _ = oracle.riemann(ql, qr)
+        assert not nc
+        ps, us = ER.star(1.0, ul, 1.0, 0.9, ul + 0.2, 0.85)
+        cl = math.sqrt(G)
+        rs = (ps / 1.0) ** (1.0 / G); cs = math.sqrt(G * ps / rs)
+        head, tail = ul - cl, us - cs
+        branches.add("left" if head >= 0.0 else "fan" if tail > 0.0 else "star")
+        if prev is not None:
+            worst = max(worst, np.max(np.abs(s - prev)))
+        prev = s
+    assert branches == {"star", "fan", "left"}, branches
+    assert worst <= 50 * dul, worst
