@@ -241,9 +241,14 @@ typedef struct hfav_plan_s hfav_plan_t;
  *   grids     : n_grids grid descriptions (copied).  Every axiom/goal array of
  *               grid g uses grids[g]'s extents, pitches and halo.
  *   dtype     : hfav_dtype.  bc: hfav_bc.
- *   schedule  : NULL or "auto" (default schedule), or an explicit variant
+ *   schedule  : NULL or "auto" (default schedule), "tuned" (hfav_autotune on
+ *               the arrays of the first hfav_run / hfav_run_graph, which then
+ *               runs the fastest variant), or an explicit variant
  *               "<fusion>[:<placement>][:<TX>x<TY>]" with fusion in
  *               {full, sweep, unfused}, placement in {reg, smem, hbm}.
+ *               When schedule is NULL or "auto" and the environment variable
+ *               HFAV_SCHEDULE is set, its value ("auto", "tuned" or a variant)
+ *               is used instead.
  *   out       : receives the plan; release with hfav_free.
  * Host only: no device memory is touched until the first hfav_run.
  * Errors: EINVAL, ECYCLE, EPRODUCER, EMISSING, EHALO, EUNSUPPORTED, ENOMEM.
@@ -313,7 +318,14 @@ int hfav_plan_features(const hfav_plan_t* plan, const char* schedule, float* fea
  * (plan-owned).  The halo cells of goal arrays are left unspecified.
  * Plan-owned scratch (ping-pong state, HBM intermediates of split or unfused
  * schedules, per-grid time-step slots, counters) is allocated on first use and
- * kept until hfav_free.  Asynchronous: returns after queueing the kernels.
+ * kept until hfav_free.  Asynchrony: a run that allocates (the plan's first
+ * run, or one that needs a larger scratch buffer) synchronises the device
+ * through cudaMalloc; otherwise the call queues its table uploads (ordered
+ * copies from host memory that may be reused once the call returns) and its
+ * kernels on `stream` and returns without waiting for the GPU, so runs queued
+ * back to back on one stream, each reading the previous one's goals, are
+ * ordered correctly.  The runs of one plan share its scratch: queue them on
+ * one stream, or order the streams yourself.
  * Errors: EINVAL, EALIGN, ENOMEM, ECUDA.  Newton / non-physical results are
  * reported by hfav_status, which synchronises.
  */
@@ -321,9 +333,14 @@ int hfav_run(hfav_plan_t* plan, void* const* axiom_ptrs, void* const* goal_ptrs,
              void* stream);
 
 /* Same as hfav_run, but the whole n_steps sequence is captured once into a
- * CUDA graph (per plan, keyed on the pointers and n_steps) and replayed.  The
- * uncaptured preparation run before a capture works on plan-owned copies of
- * in-place (dag.inout) arrays, so each call updates them exactly once. */
+ * CUDA graph (per plan, keyed on the pointers, n_steps, schedule and stream)
+ * and replayed.  The uncaptured preparation run before a capture works on
+ * plan-owned copies of in-place (dag.inout) arrays, so each call updates them
+ * exactly once.  The graph uploads its own pointer tables from pinned host
+ * memory that nothing else writes, so plain hfav_run calls between replays
+ * (on other arrays) leave it intact; a plain run that has to grow a scratch
+ * buffer drops the graph (after its last replay finishes) and the next
+ * hfav_run_graph captures a new one.  Building a graph synchronises `stream`. */
 int hfav_run_graph(hfav_plan_t* plan, void* const* axiom_ptrs, void* const* goal_ptrs, int n_steps,
                    void* stream);
 
@@ -371,12 +388,17 @@ int hfav_kernel_times(hfav_plan_t* plan, char* names, size_t n_names, double* ms
  *              u(i, j), or NULL for (1, 1, 1, 1, -4).
  *   stream   : cudaStream_t (NULL = legacy stream); asynchronous.
  * Limits and behaviour: (nx + 2) * (ny + 2) * 8 bytes must fit the 16 MiB
- * array, else HFAV_EINVAL and no device work.  The array is held by every GPU
- * that loads the library until the process exits.  The first call on a device
- * looks up the array's address on that device (make it before any stream
- * capture).  All calls share the array and each overwrites all of L it reads;
- * calls whose device work overlaps race.  Allocates nothing (no cudaMalloc,
- * cudaFree or allocating library call).
+ * array, else HFAV_EINVAL and no device work; u and out must not overlap
+ * (HFAV_EINVAL).  With CUDA's default lazy module loading the array is
+ * reserved on a device by the first call made there, which also looks up its
+ * address on that device: make that first call at start-up, before any stream
+ * capture and before a memory pool takes the device's remaining memory (if
+ * 16 MiB are no longer free it fails with HFAV_ENOMEM).  From then on the
+ * device holds the array until the process exits.  The address is cached per
+ * device for the life of the process, so the call must not be used across a
+ * cudaDeviceReset.  All calls share the array and each overwrites all of L it
+ * reads; calls whose device work overlaps race.  Allocates nothing (no
+ * cudaMalloc, cudaFree or allocating library call).
  */
 int hfav_chain2d_static(const double* u, int64_t nx, int64_t ny, int64_t pitch, int halo, int bc,
                         const double* weights, double* out, void* stream);
@@ -394,6 +416,26 @@ int hfav_selftest_arith(const double* x, int64_t n, double* rcp_out, double* quo
  * 1/sqrt(x[k]) (device array).  Tests hold it to within 2^-38 relative of
  * CUDA's rsqrt. */
 int hfav_selftest_rsqrt(const double* x, int64_t n, double* out, void* stream);
+
+/* Diagnostic: measured arithmetic peaks of the current device, the
+ * denominators of the ALU rooflines.  Writes rates[0] = FP64 fused
+ * multiply-adds per second (one per thread per instruction, the FP64 pipe's
+ * issue rate), rates[1..3] = FP64 IEEE divides, square roots and CUDA
+ * reciprocal square roots per second, rates[4] = FP32 fused multiply-adds per
+ * second, each from eight independent dependency chains per thread on 8 CTAs
+ * of 256 threads per SM, timed with CUDA events on `stream` after a warm-up
+ * launch (about 0.1 s of device time; synchronises).  The ratio
+ * rates[0] / rates[k] is the cost of operation k in FP64 pipe slots.  n must
+ * be >= 5.  The paper has no counterpart. */
+int hfav_probe_peaks(double* rates, int n, void* stream);
+
+/* Fault injection for tests of the failure paths: after `after` more device
+ * allocations by the library (plan scratch, counters, model buffers), the
+ * next one fails once as if the device were out of memory, and the call that
+ * made it returns HFAV_ENOMEM with the plan left usable; after < 0 turns the
+ * injection off.  Process-wide, host only; returns HFAV_OK.  The paper has no
+ * counterpart. */
+int hfav_inject_alloc_failure(int after);
 
 void hfav_free(hfav_plan_t* plan);
 

@@ -107,6 +107,14 @@ int hfav_plan(const hfav_dag* dag, const hfav_grid* grids, int n_grids, int dtyp
         rc = set_error(HFAV_EUNSUPPORTED, "the Godunov pipeline runs on periodic grids only");
     if (rc == HFAV_OK && p->pipeline != PIPE_GODUNOV && n_grids != 1)
         rc = set_error(HFAV_EUNSUPPORTED, "batches of grids are supported for the Godunov pipeline only");
+    // HFAV_SCHEDULE overrides a NULL / "auto" schedule argument: "auto", an
+    // explicit variant, or "tuned" (autotune on the arrays of the first run)
+    const char* env = getenv("HFAV_SCHEDULE");
+    if (rc == HFAV_OK && (!schedule || !strcmp(schedule, "auto")) && env && *env) {
+        if (!strcmp(env, "tuned")) p->tune_first_run = true;
+        else schedule = env;
+    }
+    if (rc == HFAV_OK && schedule && !strcmp(schedule, "tuned")) { p->tune_first_run = true; schedule = nullptr; }
     if (rc == HFAV_OK) {
         Schedule s;
         std::string err;

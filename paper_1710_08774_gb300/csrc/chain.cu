@@ -188,7 +188,7 @@ int launch_generic(hfav_plan_t* p, void* const* ax, void* const* go, cudaStream_
             continue;
         }
         int64_t total = (int64_t)a.n[0] * a.n[1] * a.n[2];
-        int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 16);
+        int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)device_sms() * 16);
         for (int k = 0; k < 27; ++k) a.wf[k] = (float)a.w[k];
         if (p->dtype == HFAV_F64) generic_rule_kernel<double><<<blocks, 256, 0, st>>>(a);
         else generic_rule_kernel<float><<<blocks, 256, 0, st>>>(a);
@@ -481,8 +481,8 @@ __global__ void __launch_bounds__(256) chain2d_tail(const GArr L, const GArr out
 
 namespace {
 int rows_per_thread(int64_t cells, int lo, int hi) {
-    // enough threads for ~8 warps per SM on 152 SMs, at least `lo` rows
-    int64_t want = 152LL * 256;
+    // enough threads for ~8 warps per SM, at least `lo` rows
+    int64_t want = (int64_t)device_sms() * 256;
     int64_t r = cells / want;
     int R = lo;
     while (R < hi && R < r) R *= 2;
@@ -492,7 +492,6 @@ int rows_per_thread(int64_t cells, int lo, int hi) {
 
 namespace {
 int chunk_planes(int64_t tiles, int nz, int64_t cap, int lead);
-int device_sms();
 }  // namespace
 
 // 2D warp-strip kernel: 16-byte lane vectors for the 32x4 and 64x4 tiles
@@ -767,7 +766,7 @@ int launch_chain2d(hfav_plan_t* p, const Schedule& s, void* const* ax, void* con
         ga.out = L;
         ga.lo[0] = -fi.halo_lo[0]; ga.lo[1] = -fi.halo_lo[1]; ga.lo[2] = 0;
         ga.n[0] = (int)ex; ga.n[1] = (int)ey; ga.n[2] = 1;
-        int blocks = (int)std::min<int64_t>((ex * ey + 255) / 256, 152 * 16);
+        int blocks = (int)std::min<int64_t>((ex * ey + 255) / 256, (int64_t)device_sms() * 16);
         for (int k = 0; k < 27; ++k) ga.wf[k] = (float)ga.w[k];
         if (f64) generic_rule_kernel<double><<<blocks, 256, 0, st>>>(ga);
         else generic_rule_kernel<float><<<blocks, 256, 0, st>>>(ga);
@@ -1145,18 +1144,6 @@ __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a) {
 }
 
 namespace {
-int device_sms() {
-    static int sms[64] = {0};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
-    if (!sms[dev]) {
-        int n = 0;
-        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
-        sms[dev] = n;
-    }
-    return sms[dev];
-}
-
 // planes per CTA for the streaming 3D kernel: with `cap` CTAs resident at a
 // time, a launch takes (waves) x (K + lead) iterations; take the K that
 // minimises it (ties to the larger K: fewer re-read halo planes)
@@ -1276,7 +1263,7 @@ int launch_chain3d(hfav_plan_t* p, const Schedule& s, void* const* ax, void* con
         ga.out = S;
         for (int x = 0; x < 3; ++x) { ga.lo[x] = -fi.halo_lo[x]; ga.n[x] = (int)e[x]; }
         int64_t tot = e[0] * e[1] * e[2];
-        int blocks = (int)std::min<int64_t>((tot + 255) / 256, 152 * 16);
+        int blocks = (int)std::min<int64_t>((tot + 255) / 256, (int64_t)device_sms() * 16);
         for (int k = 0; k < 27; ++k) ga.wf[k] = (float)ga.w[k];
         if (f64) generic_rule_kernel<double><<<blocks, 256, 0, st>>>(ga);
         else generic_rule_kernel<float><<<blocks, 256, 0, st>>>(ga);
@@ -1292,7 +1279,7 @@ int launch_chain3d(hfav_plan_t* p, const Schedule& s, void* const* ax, void* con
     // chunk of planes per CTA: enough CTAs to fill the machine
     int64_t tiles = (int64_t)((a.nx + TX - 1) / TX) * ((a.ny + TY - 1) / TY);
     int K = 8;
-    while (K < 64 && tiles * ((a.nz + 2 * K - 1) / (2 * K)) >= 152 * 8) K *= 2;
+    while (K < 64 && tiles * ((a.nz + 2 * K - 1) / (2 * K)) >= (int64_t)device_sms() * 8) K *= 2;
     a.K = K;
     dim3 blk(TX, TY), grd((a.nx + TX - 1) / TX, (a.ny + TY - 1) / TY, (a.nz + K - 1) / K);
     size_t per = (size_t)3 * ((TX + 6) * (TY + 6) + (TX + 4) * (TY + 4) + (TX + 2) * (TY + 2)) * es;

@@ -1111,7 +1111,7 @@ int launch_cg_rule(hfav_plan_t* p, const Rule& R, const std::vector<int>& ref_sl
     for (int x = 0; x < 3; ++x) A.add(n[x]);
     auto args = A.ptrs();
     const int64_t total = (int64_t)n[0] * n[1] * n[2];
-    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, 152 * 16));
+    const unsigned blocks = (unsigned)std::max<int64_t>(1, std::min<int64_t>((total + 255) / 256, (int64_t)device_sms() * 16));
     HFAV_CUDA(cudaLaunchKernel((const void*)k, dim3(blocks), dim3(256), args.data(), 0, st));
     HFAV_LAUNCHED(p->rt, "codegen_rule", st);
     return HFAV_OK;

@@ -2,6 +2,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <map>
 #include <string>
@@ -120,6 +121,12 @@ struct Runtime {
     int last_launches = 0;
     int last_steps = 0;
     bool capturing = false;   // inside stream capture: no synchronous uploads
+    // device tables written from the host (upload()): runs that build a graph
+    // keep theirs under this prefix, apart from the plain runs' tables, and
+    // copy them from pinned staging that stays fixed after the capture, so a
+    // replay re-uploads exactly what was captured
+    std::string upload_tag;
+    std::map<std::string, std::pair<void*, size_t>> pinned;
     // per-kernel timing (events recorded after each launch of a plain run)
     bool timing = false;
     std::vector<cudaEvent_t> kpool;
@@ -131,6 +138,7 @@ struct Runtime {
     int gsteps = -1;
     std::string gsched;
     cudaStream_t gstream = nullptr;
+    cudaEvent_t gdone = nullptr;         // recorded after every graph launch
     cudaStream_t own = nullptr;          // capture stream when the caller passes the legacy stream
     cudaEvent_t join0 = nullptr, join1 = nullptr;
 };
@@ -138,8 +146,20 @@ struct Runtime {
 // record the next timing event (event 0 is recorded at the start of a run)
 void kt_mark(Runtime* rt, const char* name, cudaStream_t st);
 
-// allocate (or reuse) a named scratch buffer of at least `bytes`
+// cudaMalloc behind the library's fault injection (hfav_inject_alloc_failure)
+cudaError_t dev_malloc(void** ptr, size_t bytes);
+extern std::atomic<int> g_fail_alloc;
+
+// streaming multiprocessors of the current device (queried once per device)
+int device_sms();
+
+// allocate (or reuse) a named scratch buffer of at least `bytes`; growing a
+// buffer drops the plan's captured graph, which holds the old address
 int scratch(hfav_plan_t* p, const std::string& name, size_t bytes, void** out);
+
+// copy `bytes` of host data into the named device table, ordered on `st`
+// after the work queued before it (the host data may be reused on return)
+int upload(hfav_plan_t* p, const std::string& name, const void* host, size_t bytes, cudaStream_t st, void** dev);
 
 // launchers (chain.cu / godunov.cu)
 int launch_chain2d(hfav_plan_t* p, const Schedule& s, void* const* ax, void* const* go, cudaStream_t st);

@@ -596,9 +596,10 @@ __global__ void __launch_bounds__(256) gcfl_reduce(const GGrid<T>* __restrict__ 
         smax = fmax(smax, wave_speed(u[0], u[1], u[2], u[3], (T)gamma, &bad));
     }
     smax = warp_max(smax);
+    const unsigned any_bad = __ballot_sync(0xffffffffu, bad);
     if ((threadIdx.x & 31) == 0) {
         atomic_max_pos(G.wave + slot, smax);
-        (void)counters;
+        if (any_bad) atomicAdd(&counters[1], (unsigned long long)__popc(any_bad));
     }
 }
 
@@ -739,8 +740,6 @@ __global__ void u_update(UArrays<T> A, int dir, const GGrid<T>* G, int step, dou
 // ---------------------------------------------------------------------------
 namespace {
 
-constexpr int kSMs = 152;
-
 struct GodState {
     // per grid device pointers of the plan-owned state buffers
     std::vector<std::array<void*, 4>> P, X;   // ping-pong state, x-swept state
@@ -822,7 +821,7 @@ int choose_yR(const hfav_plan_t* p, const Schedule& s) {
         int64_t warps = 0;
         for (auto& g : p->grids)
             warps += (int64_t)((g.extent[0] + W - 1) / W) * ((g.extent[1] + R - 1) / R) * wpi;
-        const int64_t slots = (int64_t)kSMs * 4;
+        const int64_t slots = (int64_t)device_sms() * 4;
         const int64_t q = (warps + slots - 1) / slots;
         const double cost = q * (R + 1.5) / (q >= 2 ? 1.0 : 0.6);
         if (cost < best - 1e-9) { best = cost; bestR = R; }
@@ -918,18 +917,13 @@ static int run_godunov_t(hfav_plan_t* p, const Schedule& s, void* const* ax, voi
         std::stable_sort(xit.begin(), xit.end(), [&](int2 a, int2 b) { return G0[a.x].nx > G0[b.x].nx; });
         std::stable_sort(yit.begin(), yit.end(), [&](int2 a, int2 b) { return G0[a.x].yR > G0[b.x].yR; });
     }
+    // the tables hold this run's pointers: uploaded in stream order, so a
+    // run queued behind an earlier one never changes the tables under it
     void *dtab, *dxit, *dyit;
     int rc;
-    if ((rc = scratch(p, "gtables", host.size() * sizeof(GGrid<T>), &dtab))) return rc;
-    if ((rc = scratch(p, "gxitems", xit.size() * sizeof(int2), &dxit))) return rc;
-    if ((rc = scratch(p, "gyitems", yit.size() * sizeof(int2), &dyit))) return rc;
-    // synchronous uploads (tables are tied to the pointers of this run; a
-    // captured graph keeps using them, so they must not change under it)
-    if (!rt->capturing) {
-        HFAV_CUDA(cudaMemcpy(dtab, host.data(), host.size() * sizeof(GGrid<T>), cudaMemcpyHostToDevice));
-        HFAV_CUDA(cudaMemcpy(dxit, xit.data(), xit.size() * sizeof(int2), cudaMemcpyHostToDevice));
-        HFAV_CUDA(cudaMemcpy(dyit, yit.data(), yit.size() * sizeof(int2), cudaMemcpyHostToDevice));
-    }
+    if ((rc = upload(p, "gtables", host.data(), host.size() * sizeof(GGrid<T>), st, &dtab))) return rc;
+    if ((rc = upload(p, "gxitems", xit.data(), xit.size() * sizeof(int2), st, &dxit))) return rc;
+    if ((rc = upload(p, "gyitems", yit.data(), yit.size() * sizeof(int2), st, &dyit))) return rc;
     const GGrid<T>* tabs = (const GGrid<T>*)dtab;
 
     GCommon C;
@@ -969,7 +963,7 @@ static int run_godunov_t(hfav_plan_t* p, const Schedule& s, void* const* ax, voi
             *sl = (T*)ptr;
         }
         const int64_t cells = (int64_t)(A.nx + 4) * (A.ny + 4);
-        const int blocks = (int)std::min<int64_t>((cells + 255) / 256, kSMs * 16);
+        const int blocks = (int)std::min<int64_t>((cells + 255) / 256, (int64_t)device_sms() * 16);
         const T g = (T)gm.gamma, ig1 = (T)(1.0 / (gm.gamma - 1.0));
         for (int step = 0; step < n_steps; ++step) {
             const GGrid<T>* tx_ = tabs + steps[step].x;   // state(step) -> x-swept
@@ -999,8 +993,7 @@ static int run_godunov_t(hfav_plan_t* p, const Schedule& s, void* const* ax, voi
         return HFAV_OK;
     }
     // persistent grids: the SMs times the resident CTAs of each kernel
-    int dev;
-    HFAV_CUDA(cudaGetDevice(&dev));
+    const int kSMs = device_sms();
     if (s.fusion == FUSE_SWEEP) {
         const int NT = TX * TY;
         const size_t xsm = xstage_elems<T>(Smax) * es;
@@ -1036,9 +1029,7 @@ static int run_godunov_t(hfav_plan_t* p, const Schedule& s, void* const* ax, voi
             }
         }
         if (s.placement == PLACE_REG) {
-            if ((rc = scratch(p, "gxrows", xrows.size() * sizeof(int2), &dxrows))) return rc;
-            if (!rt->capturing)
-                HFAV_CUDA(cudaMemcpy(dxrows, xrows.data(), xrows.size() * sizeof(int2), cudaMemcpyHostToDevice));
+            if ((rc = upload(p, "gxrows", xrows.data(), xrows.size() * sizeof(int2), st, &dxrows))) return rc;
             HFAV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occx, gsweep_xw<T>, 32 * xarcs, 0));
         } else if (s.placement == PLACE_HBM) {
             HFAV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occx, gsweep_x<T, true>, NT, 0));

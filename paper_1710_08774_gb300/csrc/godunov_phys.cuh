@@ -49,6 +49,12 @@ __device__ __forceinline__ bool dabslt(float x, float y) { return fabsf(x) < fab
 __device__ __forceinline__ bool dpos(double x) { return __double_as_longlong(x) > 0; }
 __device__ __forceinline__ bool dneg(double x) { return __double_as_longlong(x) < 0 && (__double_as_longlong(x) & 0x7fffffffffffffffLL) != 0; }
 __device__ __forceinline__ bool dpos(float x) { return x > 0.f; }
+// 0 < x < inf (false for NaN): the bit pattern minus one lies below that of the
+// largest finite double only for positive finite x
+__device__ __forceinline__ bool dposfin(double x) {
+    return (unsigned long long)(__double_as_longlong(x) - 1) < 0x7fefffffffffffffULL;
+}
+__device__ __forceinline__ bool dposfin(float x) { return x > 0.f && x <= 3.402823466e38f; }
 __device__ __forceinline__ bool dneg(float x) { return x < 0.f; }
 
 
@@ -242,7 +248,7 @@ __device__ __forceinline__ double wave_speed(double U0, double U1, double U2, do
     const double u = U1 * ir, v = U2 * ir;
     const double e = fma(U3, ir, -0.5 * fma(u, u, v * v));
     double p = (g - 1.0) * U0 * e;
-    if (!dpos(U0) || !dpos(p)) *bad = 1;
+    if (!dposfin(U0) || !dposfin(p)) *bad = 1;   // also NaN and infinite states
     p = dfloor(p, G_P_FLOOR);
     const double c = g * p * rsqrt(g * p * U0);
     return (dabslt(u, v) ? fabs(v) : fabs(u)) + c;
@@ -254,7 +260,7 @@ __device__ __forceinline__ double wave_speed(float U0, float U1, float U2, float
     const float u = U1 * ir, v = U2 * ir;
     const float e = fmaf(U3, ir, -0.5f * fmaf(u, u, v * v));
     float p = (g - 1.0f) * U0 * e;
-    if (!(U0 > 0.0f) || !(p > 0.0f)) *bad = 1;
+    if (!dposfin(U0) || !dposfin(p)) *bad = 1;
     p = fmaxf(p, (float)G_P_FLOOR);
     const float c = g * p * rsqrtf(g * p * U0);
     return (double)(fmaxf(fabsf(u), fabsf(v)) + c);

@@ -216,8 +216,9 @@ int hfav_model_choose(hfav_plan_t* p, const float* params, int n_models, int hid
         }
     }
     float *dX, *dy;
-    HFAV_CUDA(cudaMalloc(&dX, X.size() * sizeof(float)));
-    cudaError_t e = cudaMalloc(&dy, nv * sizeof(float));
+    cudaError_t e = dev_malloc((void**)&dX, X.size() * sizeof(float));
+    if (e != cudaSuccess) { cudaGetLastError(); return set_error(HFAV_ENOMEM, "cudaMalloc"); }
+    e = dev_malloc((void**)&dy, nv * sizeof(float));
     if (e != cudaSuccess) { cudaFree(dX); return set_error(HFAV_ENOMEM, "cudaMalloc"); }
     std::vector<float> y(nv, 0.f), ym(nv);
     int rc = HFAV_OK;

@@ -9,10 +9,17 @@
 // file-scope device array that the library carries instead:
 //   - capacity HFAV_STATIC_SCRATCH_BYTES (16 MiB), i.e. (nx+2)*(ny+2) doubles;
 //     larger grids are rejected with HFAV_EINVAL before any device work;
-//   - every GPU that loads libhfav.so holds the array until the process exits;
-//   - the first call on a device looks the array's device address up with
-//     cudaGetSymbolAddress while that device is current (once per device);
-//     make that first call before any stream capture;
+//   - the array belongs to this file's device module.  With lazy module
+//     loading (the CUDA default) the module, and with it the 16 MiB, is loaded
+//     on a device by the first call there, which looks the array's device
+//     address up with cudaGetSymbolAddress while that device is current (once
+//     per device); from then on the device holds the array until the process
+//     exits.  Make that first call at start-up, before any stream capture and
+//     before a memory pool takes the rest of the device: if the device has no
+//     16 MiB left then, the call fails with HFAV_ENOMEM;
+//   - the address is cached per device for the life of the process: after a
+//     cudaDeviceReset the module is loaded again, possibly elsewhere, so this
+//     entry point must not be used across a device reset;
 //   - the array is shared by every call: each call overwrites all of L it
 //     reads, so nothing has to start at zero, and calls whose device work
 //     overlaps (different streams, no ordering) race on it.
@@ -21,7 +28,7 @@
 #include <mutex>
 #include <string>
 
-#include "plan.hpp"
+#include "common.cuh"
 
 #define HFAV_STATIC_SCRATCH_BYTES (16u << 20)
 #define HFAV_STATIC_MAX_DEVICES 64
@@ -34,10 +41,11 @@ namespace {
 
 std::mutex g_static_mu;
 double* g_static_addr[HFAV_STATIC_MAX_DEVICES] = {};
+int g_static_blocks[HFAV_STATIC_MAX_DEVICES] = {};   // grid cap: 16 CTAs per SM
 
 // device address of the scratch array for the current device (host code may
-// not use the symbol's name as an address)
-int static_scratch(double** out) {
+// not use the symbol's name as an address) and the grid-size cap there
+int static_scratch(double** out, int* blocks) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return set_error(HFAV_ECUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
@@ -46,11 +54,18 @@ int static_scratch(double** out) {
     if (!g_static_addr[dev]) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_chain2d_scratch);
+        if (e == cudaErrorMemoryAllocation) {
+            cudaGetLastError();
+            return set_error(HFAV_ENOMEM, "loading the static scratch array (16 MiB) on this device: out of memory");
+        }
         if (e != cudaSuccess || !p)
             return set_error(HFAV_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        int n = device_sms();
         g_static_addr[dev] = (double*)p;
+        g_static_blocks[dev] = 16 * (n > 0 ? n : 1);
     }
     *out = g_static_addr[dev];
+    *blocks = g_static_blocks[dev];
     return HFAV_OK;
 }
 
@@ -111,13 +126,18 @@ extern "C" int hfav_chain2d_static(const double* u, int64_t nx, int64_t ny, int6
     if (bc != HFAV_BC_PERIODIC && bc != HFAV_BC_HALO_GIVEN) return set_error(HFAV_EINVAL, "bad bc");
     if (halo < 0 || (bc == HFAV_BC_HALO_GIVEN && halo < 2)) return set_error(HFAV_EHALO, "halo-given mode needs halo >= 2");
     if (pitch < nx + 2 * halo) return set_error(HFAV_EHALO, "pitch smaller than the padded row");
-    if (u == out) return set_error(HFAV_EINVAL, "out aliases u");
+    {   // u and out span the same padded layout; they must not overlap at all
+        const uint64_t span = ((uint64_t)(ny + 2 * halo - 1) * (uint64_t)pitch + (uint64_t)(nx + 2 * halo)) * sizeof(double);
+        const uintptr_t a0 = (uintptr_t)u, b0 = (uintptr_t)out;
+        if (a0 < b0 + span && b0 < a0 + span) return set_error(HFAV_EINVAL, "out overlaps u");
+    }
     const uint64_t need = (uint64_t)(nx + 2) * (uint64_t)(ny + 2) * sizeof(double);
     if (need > HFAV_STATIC_SCRATCH_BYTES)
         return set_error(HFAV_EINVAL, "grid needs " + std::to_string(need) + " bytes of scratch; the static buffer holds " +
                                           std::to_string(HFAV_STATIC_SCRATCH_BYTES) + " ((nx+2)*(ny+2) doubles)");
     double* L = nullptr;
-    int rc = static_scratch(&L);
+    int cap = 1;
+    int rc = static_scratch(&L, &cap);
     if (rc) return rc;
     StaticArgs a;
     a.u = u; a.pu = pitch; a.hu = halo;
@@ -128,12 +148,12 @@ extern "C" int hfav_chain2d_static(const double* u, int64_t nx, int64_t ny, int6
     a.out = out;
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t n1 = (nx + 2) * (ny + 2);
-    const int b1 = (int)((n1 + 255) / 256 < 152 * 16 ? (n1 + 255) / 256 : 152 * 16);
+    const int b1 = (int)((n1 + 255) / 256 < cap ? (n1 + 255) / 256 : cap);
     static_lap<<<b1, 256, 0, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(HFAV_ECUDA, std::string("static_lap: ") + cudaGetErrorString(e));
     const int64_t n2 = nx * ny;
-    const int b2 = (int)((n2 + 255) / 256 < 152 * 16 ? (n2 + 255) / 256 : 152 * 16);
+    const int b2 = (int)((n2 + 255) / 256 < cap ? (n2 + 255) / 256 : cap);
     static_tail<<<b2, 256, 0, st>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return set_error(HFAV_ECUDA, std::string("static_tail: ") + cudaGetErrorString(e));

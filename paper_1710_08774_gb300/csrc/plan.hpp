@@ -87,6 +87,7 @@ struct hfav_plan_s {
     hfav::GodunovMap gmap;
     hfav::ChainMap cmap;
     hfav::Schedule sched;
+    bool tune_first_run = false;   // schedule "tuned": autotune on the first run's arrays
     hfav::Runtime* rt = nullptr;
 };
 

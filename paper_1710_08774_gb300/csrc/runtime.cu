@@ -2,6 +2,7 @@
 // plan's schedule onto the pipeline launchers, CUDA-graph capture and replay,
 // run statistics and the exhaustive autotuner.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -10,16 +11,33 @@
 
 namespace hfav {
 
+// fault injection: the allocation after this many more device allocations
+// fails once with cudaErrorMemoryAllocation (-1: off)
+std::atomic<int> g_fail_alloc{-1};
+
+cudaError_t dev_malloc(void** ptr, size_t bytes) {
+    int n = g_fail_alloc.load();
+    while (n >= 0 && !g_fail_alloc.compare_exchange_weak(n, n - 1)) {}
+    if (n == 0) return cudaErrorMemoryAllocation;
+    return cudaMalloc(ptr, bytes);
+}
+
 namespace {
 
 int ensure_runtime(hfav_plan_t* p) {
     if (p->rt) return HFAV_OK;
+    int dev = -1;
+    HFAV_CUDA(cudaGetDevice(&dev));
+    void* c = nullptr;
+    cudaError_t e = dev_malloc(&c, 4 * sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(HFAV_ENOMEM, std::string("cudaMalloc of the plan's counters: ") + cudaGetErrorString(e));
+    }
     Runtime* rt = new (std::nothrow) Runtime();
-    if (!rt) return set_error(HFAV_ENOMEM, "host allocation failed");
+    if (!rt) { cudaFree(c); return set_error(HFAV_ENOMEM, "host allocation failed"); }
     p->rt = rt;
-    HFAV_CUDA(cudaGetDevice(&rt->device));
-    void* c;
-    HFAV_CUDA(cudaMalloc(&c, 4 * sizeof(unsigned long long)));
+    rt->device = dev;
     rt->allocs.push_back(c);
     rt->counters = (unsigned long long*)c;
     HFAV_CUDA(cudaMemset(c, 0, 4 * sizeof(unsigned long long)));
@@ -131,17 +149,34 @@ void kt_mark(Runtime* rt, const char* name, cudaStream_t st) {
     rt->kused++;
 }
 
+int device_sms() {
+    static std::atomic<int> sms[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) { cudaGetLastError(); return 1; }
+    int n = sms[dev].load(std::memory_order_relaxed);
+    if (n <= 0) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) {
+            cudaGetLastError();
+            return 1;
+        }
+        sms[dev].store(n, std::memory_order_relaxed);
+    }
+    return n;
+}
+
 int scratch(hfav_plan_t* p, const std::string& name, size_t bytes, void** out) {
     Runtime* rt = p->rt;
     auto it = rt->named.find(name);
     if (it != rt->named.end() && rt->named_bytes[name] >= bytes) { *out = it->second; return HFAV_OK; }
     if (it != rt->named.end()) {
+        if (rt->capturing) return set_error(HFAV_EINVAL, "scratch " + name + " grew during a graph capture");
+        drop_graph(p);   // a captured graph holds the old address
         cudaFree(it->second);
         rt->allocs.erase(std::find(rt->allocs.begin(), rt->allocs.end(), it->second));
         rt->named.erase(it);
     }
     void* ptr = nullptr;
-    cudaError_t e = cudaMalloc(&ptr, std::max<size_t>(bytes, 256));
+    cudaError_t e = dev_malloc(&ptr, std::max<size_t>(bytes, 256));
     if (e != cudaSuccess) {
         cudaGetLastError();
         return set_error(HFAV_ENOMEM, "cudaMalloc(" + std::to_string(bytes) + ") for " + name + ": " + cudaGetErrorString(e));
@@ -153,9 +188,44 @@ int scratch(hfav_plan_t* p, const std::string& name, size_t bytes, void** out) {
     return HFAV_OK;
 }
 
+int upload(hfav_plan_t* p, const std::string& name, const void* host, size_t bytes, cudaStream_t st, void** dev) {
+    Runtime* rt = p->rt;
+    const std::string nm = rt->upload_tag + name;
+    int rc = scratch(p, nm, bytes, dev);
+    if (rc || bytes == 0) return rc;
+    if (rt->upload_tag.empty()) {
+        // plain run: an asynchronous copy from pageable memory is staged by the
+        // driver before the call returns and runs in stream order, after the
+        // kernels of earlier runs that may still read this table
+        HFAV_CUDA(cudaMemcpyAsync(*dev, host, bytes, cudaMemcpyHostToDevice, st));
+        return HFAV_OK;
+    }
+    // graph run: the copy is captured as a node reading pinned staging that no
+    // later call writes (the uncaptured preparation run allocates it)
+    auto it = rt->pinned.find(nm);
+    if (it == rt->pinned.end() || it->second.second < bytes) {
+        if (rt->capturing) return set_error(HFAV_EINVAL, "pinned staging of " + nm + " missing during a capture");
+        if (it != rt->pinned.end()) { cudaFreeHost(it->second.first); rt->pinned.erase(it); }
+        void* h = nullptr;
+        cudaError_t e = cudaMallocHost(&h, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(HFAV_ENOMEM, "cudaMallocHost(" + std::to_string(bytes) + ") for " + nm);
+        }
+        it = rt->pinned.emplace(nm, std::make_pair(h, bytes)).first;
+    }
+    memcpy(it->second.first, host, bytes);
+    HFAV_CUDA(cudaMemcpyAsync(*dev, it->second.first, bytes, cudaMemcpyHostToDevice, st));
+    return HFAV_OK;
+}
+
 void drop_graph(hfav_plan_t* p) {
     if (!p->rt) return;
-    if (p->rt->gexec) cudaGraphExecDestroy(p->rt->gexec);
+    if (p->rt->gexec) {
+        // the last replay may still be reading the pinned tables and scratch
+        if (p->rt->gdone && cudaEventSynchronize(p->rt->gdone) != cudaSuccess) cudaGetLastError();
+        cudaGraphExecDestroy(p->rt->gexec);
+    }
     p->rt->gexec = nullptr;
     p->rt->gkey.clear();
     p->rt->gsteps = -1;
@@ -167,11 +237,13 @@ void destroy_runtime(hfav_plan_t* p) {
     if (rt->last_stream) cudaStreamSynchronize(rt->last_stream);
     drop_graph(p);
     for (void* a : rt->allocs) cudaFree(a);
+    for (auto& kv : rt->pinned) cudaFreeHost(kv.second.first);
     if (rt->ev0) cudaEventDestroy(rt->ev0);
     if (rt->ev1) cudaEventDestroy(rt->ev1);
     for (cudaEvent_t e : rt->kpool) cudaEventDestroy(e);
     if (rt->join0) cudaEventDestroy(rt->join0);
     if (rt->join1) cudaEventDestroy(rt->join1);
+    if (rt->gdone) cudaEventDestroy(rt->gdone);
     if (rt->own) cudaStreamDestroy(rt->own);
     delete rt;
     p->rt = nullptr;
@@ -183,6 +255,10 @@ int run(hfav_plan_t* p, void* const* ax, void* const* go, int n_steps, void* str
     int rc = check_ptrs(p, ax, go);
     if (rc) return rc;
     if ((rc = ensure_runtime(p))) return rc;
+    if (p->tune_first_run) {   // schedule "tuned": time every variant on these arrays first
+        p->tune_first_run = false;
+        if ((rc = autotune(p, ax, go, n_steps, 3, stream, nullptr, 0))) return rc;
+    }
     Runtime* rt = p->rt;
     cudaStream_t st = (cudaStream_t)stream;
     rt->last_stream = st;
@@ -215,6 +291,11 @@ int run(hfav_plan_t* p, void* const* ax, void* const* go, int n_steps, void* str
             // is updated once, by the graph
             rt->launches = 0;
             std::vector<void*> axw, gow;
+            struct TagGuard {   // the graph's tables live apart from the plain runs'
+                Runtime* rt;
+                explicit TagGuard(Runtime* r) : rt(r) { rt->upload_tag = "graph:"; }
+                ~TagGuard() { rt->upload_tag.clear(); rt->capturing = false; }
+            } guard(rt);
             if ((rc = redirect_inplace(p, ax, go, st, "inout_copy_", &axw, &gow))) return rc;
             if ((rc = launch_once(p, p->sched, axw.data(), gow.data(), n_steps, st))) return rc;
             HFAV_CUDA(cudaStreamSynchronize(st));
@@ -239,6 +320,8 @@ int run(hfav_plan_t* p, void* const* ax, void* const* go, int n_steps, void* str
         HFAV_CUDA(cudaEventRecord(rt->ev0, st));
         HFAV_CUDA(cudaGraphLaunch(rt->gexec, st));
         HFAV_CUDA(cudaEventRecord(rt->ev1, st));
+        if (!rt->gdone) HFAV_CUDA(cudaEventCreateWithFlags(&rt->gdone, cudaEventDisableTiming));
+        HFAV_CUDA(cudaEventRecord(rt->gdone, st));
         if (st != caller) {
             HFAV_CUDA(cudaEventRecord(rt->join1, st));
             HFAV_CUDA(cudaStreamWaitEvent(caller, rt->join1, 0));
@@ -373,3 +456,8 @@ int set_timing(hfav_plan_t* p, int on) {
 }
 
 }  // namespace hfav
+
+extern "C" int hfav_inject_alloc_failure(int after) {
+    hfav::g_fail_alloc.store(after < 0 ? -1 : after);
+    return HFAV_OK;
+}

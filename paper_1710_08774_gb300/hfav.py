@@ -33,7 +33,8 @@ SYMBOLS = ["hfav_plan", "hfav_analyze", "hfav_plan_groups", "hfav_plan_field", "
            "hfav_run_graph", "hfav_status", "hfav_autotune", "hfav_plan_variants", "hfav_free", "hfav_last_error",
            "hfav_version", "hfav_mlp_n_params", "hfav_mlp_forward", "hfav_mlp_work_floats", "hfav_mlp_loss_grad",
            "hfav_mlp_adam", "hfav_mlp_train", "hfav_model_choose", "hfav_plan_timing", "hfav_kernel_times",
-           "hfav_chain2d_static", "hfav_selftest_arith", "hfav_selftest_rsqrt"]
+           "hfav_chain2d_static", "hfav_selftest_arith", "hfav_selftest_rsqrt", "hfav_inject_alloc_failure",
+           "hfav_probe_peaks"]
 
 
 class HfavError(RuntimeError):
@@ -152,6 +153,8 @@ def load(path=None):
                                  ctypes.POINTER(ctypes.c_double), P, P], ctypes.c_int),
         "hfav_kernel_times": ([P, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double), ip,
                                ctypes.c_int], ctypes.c_int),
+        "hfav_inject_alloc_failure": ([ctypes.c_int], ctypes.c_int),
+        "hfav_probe_peaks": ([ctypes.POINTER(ctypes.c_double), ctypes.c_int, P], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)
@@ -535,6 +538,14 @@ def analyze(dag, extent=None):
 # ---------------------------------------------------------------------------
 # MLP kernels
 # ---------------------------------------------------------------------------
+def probe_peaks(stream=None):
+    """Measured peaks of the current device: FP64 FMA/s (the FP64 pipe's issue
+    rate), FP64 divide/s, sqrt/s, rsqrt/s and FP32 FMA/s (per second, whole GPU)."""
+    r = (ctypes.c_double * 5)()
+    check(load().hfav_probe_peaks(r, 5, _stream(stream)))
+    return dict(dfma=r[0], ddiv=r[1], dsqrt=r[2], drsqrt=r[3], ffma=r[4])
+
+
 def mlp_n_params(n_in, hidden):
     return int(load().hfav_mlp_n_params(n_in, hidden))
 

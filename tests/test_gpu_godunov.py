@@ -6,6 +6,10 @@ bulk (Newton + CFL in FP64): <= 1e-4 normwise per field after 10 steps.
 Also: conservation to 1e-12 on the GPU, the uniform state as a fixed point,
 dt history equal to the oracle's, a CUDA-graph replay bitwise equal to a
 plain run, and batches of uneven grids equal to per-grid oracle runs.
+Ordering: a plain run on other arrays between two replays of a captured graph
+leaves the graph's tables intact, and two runs queued back to back on a
+non-blocking stream (the second reading the first one's goals) equal the
+oracle's 20 steps.
 """
 import math
 
@@ -117,6 +121,51 @@ def test_graph_replay_bitwise():
     (b,), _, _ = gpu_godunov([U], 10, "sweep:reg:32x4", graph=True)
     (c,), _, _ = gpu_godunov([U], 10, "sweep:reg:32x4", graph=True)
     assert np.array_equal(a, b) and np.array_equal(a, c)
+
+
+def _host_state(ts):
+    return np.stack([t.double().cpu().numpy() for t in ts])
+
+
+@pytest.mark.parametrize("schedule", ["sweep:reg:32x4", "sweep:smem:64x4", "full:reg:32x4", "unfused"])
+def test_plain_run_between_graph_replays(schedule):
+    import torch
+    UA = I.sod_state(96, 64, seed=4)
+    UB = I.sod_state(96, 64, seed=5)
+    refA = oracle.godunov(UA, 6)[0]
+    refB = oracle.godunov(UB, 6)[0]
+    inA = state_tensors(UA, torch.float64); outA = empty_like_state(inA)
+    inB = state_tensors(UB, torch.float64); outB = empty_like_state(inB)
+    P = H.Plan(H.godunov_dag(), [H.Grid.of(inA[0], 0)], H.HFAV_F64, H.HFAV_BC_PERIODIC, schedule)
+    P.run(inA, outA, 6, graph=True)
+    torch.cuda.synchronize()
+    check_fields(_host_state(outA), refA, 1e-12)
+    for t in outA:
+        t.fill_(float("nan"))
+    P.run(inB, outB, 6)                 # rewrites the plain run's tables
+    P.run(inA, outA, 6, graph=True)     # replays the graph captured for A
+    torch.cuda.synchronize()
+    check_fields(_host_state(outA), refA, 1e-12)
+    check_fields(_host_state(outB), refB, 1e-12)
+
+
+@pytest.mark.parametrize("schedule", ["sweep:reg:32x4", "sweep:hbm:32x4", "full:reg:32x4"])
+def test_back_to_back_runs_on_a_side_stream(schedule):
+    import torch
+    U = I.sod_state(512, 256, seed=6)
+    ref = oracle.godunov(U, 20)[0]
+    side = torch.cuda.Stream()
+    A = state_tensors(U, torch.float64)
+    B = empty_like_state(A)
+    P = H.Plan(H.godunov_dag(), [H.Grid.of(A[0], 0)], H.HFAV_F64, H.HFAV_BC_PERIODIC, schedule)
+    W = empty_like_state(A)
+    P.run(A, W, 10, stream=side)        # allocates the plan's scratch (synchronising)
+    side.synchronize()
+    with torch.cuda.stream(side):
+        P.run(A, B, 10, stream=side)    # A -> B
+        P.run(B, A, 10, stream=side)    # B -> A, queued before the first run has finished
+    side.synchronize()
+    check_fields(_host_state(A), ref, 1e-12)
 
 
 @pytest.mark.parametrize("dtype,tol", [(H.HFAV_F64, 1e-12), (H.HFAV_F32, 1e-4)])
