@@ -17,7 +17,12 @@ namespace hfav {
 #define G_RHO_FLOOR 1e-10
 #define G_P_FLOOR 1e-10
 #define G_NEWTON_MAX 10
-#define G_NEWTON_TOL 1e-10
+// The iteration stops after an update |dp| <= 1e-8 p*.  Newton converges
+// quadratically here, so the error left after that update is of order
+// dp^2 / p*, about 1e-16 relative: the same root, to rounding, as a stop at
+// 1e-10 (one more iteration on a few faces, which would keep most warps
+// iterating for their slowest lane).
+#define G_NEWTON_TOL 1e-8
 
 // ---- arithmetic helpers that keep work off the FP64 pipe ------------------
 // On this part the FP64 pipe issues ~1/58 of the FP32 rate, so compares,
@@ -210,13 +215,24 @@ __device__ __forceinline__ Face4<T> riemann(const Face4<T>& L, const Face4<T>& R
         take_side = dneg(fma(sgn * S.u, S.r, ws));
         take_star = !take_side;
     } else {           // rarefaction fan
-        const T cs = g * S.p * rsqrt(g * S.p * S.r);
-        const T cst = g * pst * rsqrt(g * pst * rst);
-        const T head = fma(sgn, cs, S.u);
-        const T tail = fma(sgn, cst, ust);
-        take_side = left ? dpos(head) : dneg(head);
-        take_star = !take_side && ((left ? dneg(tail) : dpos(tail)) || head == tail);
-        if (!take_side && !take_star) f = div_nr(-tail, head - tail);
+        // The head u_s + sgn c_s has passed the face when the side's flow
+        // is supersonic away from the contact (sgn u_s < 0 and u_s^2 > c_s^2),
+        // and the tail u* + sgn c* has not reached it when the star flow is
+        // subsonic (u*^2 < c*^2; sgn u* <= 0 on the sampled side): squared
+        // speeds, so no sound speed is needed unless the face lies inside the
+        // fan.  At the fan's edges the state is continuous, so a decision
+        // that rounding flips there moves it by rounding only.
+        const T gps = g * S.p, gpst = g * pst;
+        take_side = (left ? dpos(S.u) : dneg(S.u)) && dlt(gps, S.r * S.u * S.u);
+        take_star = !take_side && dlt(rst * ust * ust, gpst);
+        if (!take_side && !take_star) {   // inside the fan: interpolate between its edges
+            const T cs = gps * rsqrt(gps * S.r);
+            const T cst = gpst * rsqrt(gpst * rst);
+            const T head = fma(sgn, cs, S.u);
+            const T tail = fma(sgn, cst, ust);
+            if (head == tail) take_star = true;   // degenerate fan
+            else f = div_nr(-tail, head - tail);
+        }
     }
     if (take_side) { o.r = S.r; o.u = S.u; o.p = S.p; }
     else if (take_star) { o.r = rst; o.u = ust; o.p = pst; }
