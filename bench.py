@@ -33,8 +33,34 @@ sys.path.insert(0, ROOT)
 METRIC = "Gcell-updates/s and % HBM roofline, fused vs unfused on 1 GB300 at stated tolerance"
 UNIT = "Gcell-updates/s"
 CFL = 0.5
-PEAK_FP64_GFLOPS = 1187.0      # DFMA rate measured on this GB300 pool by the repo's FP64 probe (nominal 1250)
-PEAK_FP32_GFLOPS = 68700.0     # FFMA rate measured by the same probe
+_PROBE = {}
+
+
+def probe():
+    """Arithmetic peaks measured on this device in this run (hfav_probe_peaks):
+    FP64 / FP32 FMA per second and the FP64 divide / sqrt / rsqrt rates."""
+    if not _PROBE:
+        from paper_1710_08774_gb300 import hfav as H
+        _PROBE.update(H.probe_peaks())
+    return _PROBE
+
+
+_CLK = {}
+# FP64 pipe issue slots per SM per clock cycle: one FP64 warp instruction keeps
+# the pipe busy 16 cycles on this part (sm__pipe_fp64_cycles_active over
+# sm__inst_executed_pipe_fp64 in every capture), i.e. 32 / 16 lanes per cycle;
+# with 152 SMs at 2070 MHz that is the nominal 1.26 TFLOP/s of FP64 FMA
+FP64_SLOTS_PER_SM_CLK = 2.0
+
+
+def fp64_peak_gflops():
+    """FP64 pipe peak in DFMA-equivalent GFLOP/s (2 flops per slot), derived
+    from the pipe's slots per SM per clock, the SM count and the median SM
+    clock sampled during the timed region (the maximum clock when none was)."""
+    import torch
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    mhz = _CLK.get("sm_mhz") or peaks().get("sm_max_mhz", 2070.0)
+    return 2.0 * FP64_SLOTS_PER_SM_CLK * props.multi_processor_count * mhz * 1e6 / 1e9
 
 
 # FP64 operations of the method, counted from its definition (each +, -, *,
@@ -80,6 +106,25 @@ def src_hash(files):
     for f in files:
         h.update(open(os.path.join(ROOT, "paper_1710_08774_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
+
+
+# FP64 pipe issue slots (ncu sm__inst_executed_pipe_fp64.sum x 32 lanes) of
+# one launch of a Godunov kernel on the bench's workload and schedule, from
+# one ncu capture (profiles/godunov_fp64_1024_pipe_ncu.md), with the hash of
+# the kernel sources at capture time: a changed source voids it.
+FP64_SLOTS = {
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg:32x4", "gsweep_x"): (296.20e6, "55662954019f9d94"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg:32x4", "gsweep_y"): (333.78e6, "55662954019f9d94"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg:64x4", "gsweep_x"): (296.20e6, "55662954019f9d94"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg:64x4", "gsweep_y"): (333.78e6, "55662954019f9d94"),
+}
+
+
+def fp64_slots_for(workload, schedule, kernel):
+    t = FP64_SLOTS.get((workload, schedule, kernel))
+    if not t:
+        return None
+    return t[0] if src_hash(["godunov.cu", "godunov_phys.cuh", "common.cuh"]) == t[1] else None
 
 
 def traffic_for(workload, kernel):
@@ -204,15 +249,29 @@ class Godunov(Workload):
         per = 8 * self.esize * (2 if sched.startswith("sweep") else 1)   # 4 fields read + written per pass
         return per * self.n * self.n * self.tsteps
 
-    def kernel_work(self, kernel, it):
-        """(bound, algorithmic work per launch, unit) of one launch of `kernel`."""
+    def kernel_work(self, kernel, it, schedule=None):
+        """(bound, work per launch, unit, peak, what) of one launch of `kernel`.
+
+        The Godunov kernels are bound by the FP64 pipe.  Their work is the
+        FP64 pipe issue slots of a launch (every DFMA, DMUL, DADD one slot; a
+        divide, square root or reciprocal square root the slots of its
+        instruction sequence), counted by ncu on this workload and schedule,
+        as DFMA-equivalent flops (2 per slot) against the FP64 FMA rate
+        measured in this run.  Without a count for the current sources the
+        conventional op count of the method stands in (each +, -, *, /, sqrt
+        one flop)."""
         cells = self.n * self.n
+        slots = fp64_slots_for(self.name, schedule, kernel)
+        if slots is not None:
+            return "alu", 2.0 * slots, "GFLOP/s", fp64_peak_gflops(), \
+                "FP64 pipe issue slots (ncu) x 2 against the pipe's slots per SM per clock x SMs x sampled SM clock"
         if self.dtype == "f64":
             per = {"gsweep_x": godunov_flops_sweep(it), "gsweep_y": godunov_flops_sweep(it) + GODUNOV_CFL_FLOPS,
                    "gfull": 2 * godunov_flops_sweep(it) + GODUNOV_CFL_FLOPS}.get(kernel, godunov_flops_sweep(it))
         else:   # FP64 work of the FP32-bulk form: the Newton iteration, ~36 flops per iteration and face
             per = {"gsweep_x": 36.0 * it, "gsweep_y": 36.0 * it, "gfull": 72.0 * it}.get(kernel, 36.0 * it)
-        return "alu", per * cells, "GFLOP/s", PEAK_FP64_GFLOPS, "FP64 DFMA rate measured by the repo's probe"
+        return "alu", per * cells, "GFLOP/s", fp64_peak_gflops(), \
+            "conventional FP64 op count of the method against the FP64 pipe peak (slots per SM per clock x SMs x clock)"
 
     def io(self):
         return self.host, self.ins, self.outs
@@ -246,9 +305,14 @@ class Batch(Godunov):
     def compulsory_bytes(self, sched):
         return 8 * 4 * (2 if sched.startswith("sweep") else 1) * self.cells * self.tsteps
 
-    def kernel_work(self, kernel, it):
+    def kernel_work(self, kernel, it, schedule=None):
+        slots = fp64_slots_for(self.name, schedule, kernel)
+        if slots is not None:
+            return "alu", 2.0 * slots, "GFLOP/s", fp64_peak_gflops(), \
+                "FP64 pipe issue slots (ncu) x 2 against the pipe's slots per SM per clock x SMs x sampled SM clock"
         per = {"gsweep_x": 36.0 * it, "gsweep_y": 36.0 * it, "gfull": 72.0 * it}.get(kernel, 36.0 * it)
-        return "alu", per * self.cells, "GFLOP/s", PEAK_FP64_GFLOPS, "FP64 DFMA rate measured by the repo's probe"
+        return "alu", per * self.cells, "GFLOP/s", fp64_peak_gflops(), \
+            "conventional FP64 op count of the Newton iteration against the FP64 pipe peak"
 
     def io(self):
         return None, None, None
@@ -285,12 +349,13 @@ class Cosmo(Workload):
         # ustage reads u and both fluxes, writes out
         return (12 if sched.startswith("unfused") else 2) * self.esize * self.cells_per_step()
 
-    def kernel_work(self, kernel, it):
+    def kernel_work(self, kernel, it, schedule=None):
         cells = self.cells_per_step()
         if self.dtype == "f32":
             return "hbm", 2 * self.esize * cells, "GB/s", peaks().get("hbm_gbs", 6787.6), \
                 "measured copy bandwidth (MEASURED_PEAKS.json)"
-        return "alu", COSMO_FLOPS * cells, "GFLOP/s", PEAK_FP64_GFLOPS, "FP64 DFMA rate measured by the repo's probe"
+        return "alu", COSMO_FLOPS * cells, "GFLOP/s", fp64_peak_gflops(), \
+            "FP64 op count against the FP64 pipe peak (slots per SM per clock x SMs x clock)"
 
     def io(self):
         return None, None, None
@@ -334,13 +399,14 @@ class Chain(Workload):
         per = (6 if self.dims == 2 else 8) if sched.startswith("unfused") else 2
         return per * self.esize * self.n ** self.dims
 
-    def kernel_work(self, kernel, it):
+    def kernel_work(self, kernel, it, schedule=None):
         cells = self.n ** self.dims
         if self.dtype == "f32":
             return "hbm", 2 * self.esize * cells / 1e0, "GB/s", peaks().get("hbm_gbs", 6787.6), \
                 "measured copy bandwidth (MEASURED_PEAKS.json)"
         fl = CHAIN2D_FLOPS if self.dims == 2 else CHAIN3D_FLOPS
-        return "alu", fl * cells, "GFLOP/s", PEAK_FP64_GFLOPS, "FP64 DFMA rate measured by the repo's probe"
+        return "alu", fl * cells, "GFLOP/s", fp64_peak_gflops(), \
+            "FP64 op count against the FP64 pipe peak (slots per SM per clock x SMs x clock)"
 
     def io(self):
         return None, None, None
@@ -393,7 +459,7 @@ class Norm(Workload):
         # flux (u -> flux), diff (flux -> diff), sq (diff -> sq), the sum (reads sq), out (diff -> out)
         return (9 if sched.startswith("unfused") else 4) * self.esize * self.cells_per_step()
 
-    def kernel_work(self, kernel, it):
+    def kernel_work(self, kernel, it, schedule=None):
         # each fused nest reads one array and writes one
         return "hbm", 2 * self.esize * self.cells_per_step(), "GB/s", peaks().get("hbm_gbs", 6787.6), \
             "measured copy bandwidth (MEASURED_PEAKS.json)"
@@ -491,6 +557,30 @@ def oracle_sample(workload, n=None):
     oracle.chain3d(u)
     dt = time.perf_counter() - t0
     return n ** 3 / dt / 1e9, dt, 0.0, f"{n}^3 u~N(0,1), single thread"
+
+
+def _oracle_worker(workload, barrier, q):
+    barrier.wait()
+    v, dt, _, _ = oracle_sample(workload)
+    q.put((v * 1e9 * dt, dt))
+
+
+def oracle_all_cores(workload, procs=None):
+    """The oracle's sample run as one process per host core at once (spawned,
+    released together by a barrier): (Gcell-updates/s of all of them, seconds
+    of the slowest, processes)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    P = procs or os.cpu_count() or 1
+    barrier, q = ctx.Barrier(P), ctx.Queue()
+    ps = [ctx.Process(target=_oracle_worker, args=(workload, barrier, q)) for _ in range(P)]
+    for p in ps:
+        p.start()
+    res = [q.get(timeout=900) for _ in range(P)]
+    for p in ps:
+        p.join()
+    wall = max(r[1] for r in res)
+    return sum(r[0] for r in res) / wall / 1e9, wall, P
 
 
 def workload_name(key):
@@ -605,6 +695,7 @@ def bench(args, name, torch, H, I, dev, ws, rank, local):
     clk.start()
     ms, ktimes, launches = timed(w.plan, args.steps, timing=True)
     clocks = clk.stop()
+    _CLK["sm_mhz"] = clocks.get("sm_mhz")
     st = w.plan.status()
     value, total_ms = replica_value(sum(ms), w.cells_per_step(), args.steps, ws, dev)
 
@@ -676,16 +767,28 @@ def bench(args, name, torch, H, I, dev, ws, rank, local):
         v, secs, it, sample = oracle_sample(name)
         it_avg = it or it_avg
         cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": f"{sample} ({secs:.1f} s)"}
+        try:
+            va, wall, P = oracle_all_cores(name)
+            cpu["all_cores"] = {"value": va, "unit": UNIT, "cores": P, "kind": "oracle",
+                                "sample": f"the same sample in {P} processes at once, one per host core "
+                                          f"({wall:.1f} s for the slowest)"}
+        except Exception as e:   # the single-thread figure stands on its own
+            cpu["all_cores"] = {"unavailable": str(e)[:200]}
 
     roof = None
     if ktimes:
         dom = max(ktimes, key=lambda k: ktimes[k][0])
         dom_ms = ktimes[dom][0] / ktimes[dom][1]
-        bound, work, unit, peak, src = w.kernel_work(dom, it_avg)
+        bound, work, unit, peak, src = w.kernel_work(dom, it_avg, best)
         achieved = work / (dom_ms * 1e-3) / 1e9
         roof = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
                 "frac": achieved / peak, "traffic": traffic_for(w.name, dom), "peak_source": src,
                 "launch_ms": dom_ms, "work_per_launch": work}
+        if bound == "alu":   # in-run probe: a pure FMA loop, and the slot cost of divide / sqrt / rsqrt
+            pr = probe()
+            roof["probe"] = {"dfma_loop_gflops": 2 * pr["dfma"] / 1e9, "ffma_loop_tflops": 2 * pr["ffma"] / 1e12,
+                             "slots": {"div": pr["dfma"] / pr["ddiv"], "sqrt": pr["dfma"] / pr["dsqrt"],
+                                       "rsqrt": pr["dfma"] / pr["drsqrt"]}}
     hbm = peaks().get("hbm_gbs", 6787.6)
     cb = w.compulsory_bytes(best)
     line = {

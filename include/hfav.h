@@ -114,6 +114,9 @@ typedef enum {
      * TRACE      in: rho un ut p c drho dun dut dp dt   -> qm[4] qp[4]
      * QLEFTRIGHT in: qp[4](0) qm[4](+1)                 -> qL[4] qR[4]
      * RIEMANN    in: qL[4] qR[4]                        -> g[4]
+     *            (params[1], optional: cap on the Newton iterations, 1..10,
+     *            default 10; faces that reach it are counted and reported
+     *            as HFAV_WARN_NEWTON)
      * CMPFLX     in: g[4]                               -> F[4]
      * UPDATE     in: U0..U3 F[4](0) F[4](-1) dt         -> U'0..U'3
      * The face a+1/2 is stored at index a. */

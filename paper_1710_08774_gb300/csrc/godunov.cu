@@ -50,6 +50,7 @@ struct GCommon {
     unsigned long long* counters;   // [0] Newton non-converged faces, [1] non-physical cells
     void* slab;                     // per-CTA-group scratch for placement hbm
     int reduce_cfl;                 // gsweep_y / gfull: fold the next step's CFL reduction in
+    int newton_max;                 // cap on the Riemann solver's Newton iterations
 };
 
 template <typename T>
@@ -194,7 +195,7 @@ __global__ void __launch_bounds__(256) gsweep_xw(const GGrid<T>* __restrict__ gr
                 Face4<T> q0n = (exact && s == nch + 1) ? qmNext : shfl_face(qmNew, 0);
                 if (lane == 31) qR = q0n;
                 int nc_local = 0;
-                Face4<T> F = flux(riemann(qpOld, qR, g, ashk, &nc_local), ig1);
+                Face4<T> F = flux(riemann(qpOld, qR, g, ashk, C.newton_max, &nc_local), ig1);
                 if (32 * v - 1 + lane <= nf - 2) nonconv |= nc_local;
                 if (v == 0) {
                     Fsave = shfl_face(F, 0);   // face of cell a0-1
@@ -304,7 +305,7 @@ __global__ void __launch_bounds__(256) gsweep_x(const GGrid<T>* __restrict__ gri
                 Face4<T> L, R;
                 L.r = QP[lm + 1]; L.u = QP[QS + lm + 1]; L.v = QP[2 * QS + lm + 1]; L.p = QP[3 * QS + lm + 1];
                 R.r = QM[l + 1]; R.u = QM[QS + l + 1]; R.v = QM[2 * QS + l + 1]; R.p = QM[3 * QS + l + 1];
-                Face4<T> fl = flux(riemann(L, R, g, ashk, &nonconv), ig1);
+                Face4<T> fl = flux(riemann(L, R, g, ashk, C.newton_max, &nonconv), ig1);
                 F[0 * (S + 1) + l] = fl.r; F[1 * (S + 1) + l] = fl.u; F[2 * (S + 1) + l] = fl.v; F[3 * (S + 1) + l] = fl.p;
             }
         }
@@ -371,14 +372,14 @@ __device__ __forceinline__ void ywin_load(const volatile T* p, int stride, YWin<
 // in the y frame (rho, rho v, rho u, E).  Emits the updated cell r-2 into out.
 template <typename T>
 __device__ __forceinline__ bool ystep(YWin<T>& w, const Face4<T>& U2, int r, int j0, T dtdx, T g, double ashk, T ig1,
-                                      int* nonconv, Face4<T>* out) {
+                                      int nmax, int* nonconv, Face4<T>* out) {
     Prim<T> W2 = cons_to_prim(U2.r, U2.u, U2.v, U2.p, g);
     bool emit = false;
     if (r >= j0) {
         Face4<T> qm, qp;
         slope_trace(w.W0, w.W1, W2, dtdx, qm, qp);   // cell r-1
         if (r >= j0 + 1) {
-            Face4<T> q = riemann(w.qpp, qm, g, ashk, nonconv);   // face between r-2 and r-1
+            Face4<T> q = riemann(w.qpp, qm, g, ashk, nmax, nonconv);   // face between r-2 and r-1
             Face4<T> F = flux(q, ig1);
             if (r >= j0 + 2) {   // update cell r-2 with its faces below (Fp) and above (F)
                 out->r = fma(-dtdx, F.r - w.Fp.r, w.U0.r);
@@ -434,7 +435,7 @@ __global__ void __launch_bounds__(256) gsweep_y(const GGrid<T>* __restrict__ gri
                     U2.v = ldg_src(G, 1, i, jr); U2.p = ldg_src(G, 3, i, jr);
                     if (PL != PLACE_REG && r > j0 - 2) ywin_load(ring, stride, w);
                     Face4<T> o;
-                    bool emit = ystep(w, U2, r, j0, dtdx, g, ashk, ig1, &nonconv, &o);
+                    bool emit = ystep(w, U2, r, j0, dtdx, g, ashk, ig1, C.newton_max, &nonconv, &o);
                     if (PL != PLACE_REG) ywin_store(ring, stride, w);
                     const int j = r - 2;
                     if (emit && j < G.ny) {
@@ -539,7 +540,7 @@ __global__ void __launch_bounds__(256) gfull(const GGrid<T>* __restrict__ grids,
                 Face4<T> L, Rr;
                 L.r = QP[l]; L.u = QP[TX + l]; L.v = QP[2 * TX + l]; L.p = QP[3 * TX + l];
                 Rr.r = QM[l + 1]; Rr.u = QM[TX + l + 1]; Rr.v = QM[2 * TX + l + 1]; Rr.p = QM[3 * TX + l + 1];
-                Face4<T> fl = flux(riemann(L, Rr, g, ashk, &nonconv), ig1);
+                Face4<T> fl = flux(riemann(L, Rr, g, ashk, C.newton_max, &nonconv), ig1);
                 F[l] = fl.r; F[TX + l] = fl.u; F[2 * TX + l] = fl.v; F[3 * TX + l] = fl.p;
             }
             __syncthreads();
@@ -558,7 +559,7 @@ __global__ void __launch_bounds__(256) gfull(const GGrid<T>* __restrict__ grids,
                 U2.r = UR[t]; U2.u = UR[2 * TX + t]; U2.v = UR[TX + t]; U2.p = UR[3 * TX + t];
                 if (PL != PLACE_REG && r > j0 - 2) ywin_load(ring, stride, w);
                 Face4<T> o;
-                bool emit = ystep(w, U2, r, j0, dtdx, g, ashk, ig1, &nonconv, &o);
+                bool emit = ystep(w, U2, r, j0, dtdx, g, ashk, ig1, C.newton_max, &nonconv, &o);
                 if (PL != PLACE_REG) ywin_store(ring, stride, w);
                 const int j = r - 2;
                 if (emit && j < G.ny) {
@@ -698,13 +699,13 @@ __global__ void u_qleftright(UArrays<T> A, int dir) {
 }
 
 template <typename T>
-__global__ void u_riemann(UArrays<T> A, int dir, T g, double ashk, unsigned long long* counters) {
+__global__ void u_riemann(UArrays<T> A, int dir, T g, double ashk, int nmax, unsigned long long* counters) {
     int nonconv = 0;
     U_LOOP(-1, na)
         const int64_t x = uidx(A, dir, a, b);
         Face4<T> L{A.qL[0][x], A.qL[1][x], A.qL[2][x], A.qL[3][x]};
         Face4<T> R{A.qR[0][x], A.qR[1][x], A.qR[2][x], A.qR[3][x]};
-        Face4<T> q = riemann(L, R, g, ashk, &nonconv);
+        Face4<T> q = riemann(L, R, g, ashk, nmax, &nonconv);
         A.gd[0][x] = q.r; A.gd[1][x] = q.u; A.gd[2][x] = q.v; A.gd[3][x] = q.p;
     }
     unsigned m = __ballot_sync(0xffffffffu, nonconv);
@@ -936,6 +937,7 @@ static int run_godunov_t(hfav_plan_t* p, const Schedule& s, void* const* ax, voi
     C.counters = rt->counters;
     C.slab = nullptr;
     C.reduce_cfl = 1;
+    C.newton_max = gm.newton_max;
 
     const int TX = s.tx, TY = s.ty;
     // step 0's wave speed
@@ -981,7 +983,7 @@ static int run_godunov_t(hfav_plan_t* p, const Schedule& s, void* const* ax, voi
                 u_slope<T><<<blocks, 256, 0, st>>>(A, dir); HFAV_LAUNCHED(rt, "u_slope", st);
                 u_trace<T><<<blocks, 256, 0, st>>>(A, dir, G, step, gm.cfl); HFAV_LAUNCHED(rt, "u_trace", st);
                 u_qleftright<T><<<blocks, 256, 0, st>>>(A, dir); HFAV_LAUNCHED(rt, "u_qleftright", st);
-                u_riemann<T><<<blocks, 256, 0, st>>>(A, dir, g, C.ashk, rt->counters); HFAV_LAUNCHED(rt, "u_riemann", st);
+                u_riemann<T><<<blocks, 256, 0, st>>>(A, dir, g, C.ashk, C.newton_max, rt->counters); HFAV_LAUNCHED(rt, "u_riemann", st);
                 u_cmpflx<T><<<blocks, 256, 0, st>>>(A, dir, ig1); HFAV_LAUNCHED(rt, "u_cmpflx", st);
                 u_update<T><<<blocks, 256, 0, st>>>(A, dir, G, step, gm.cfl); HFAV_LAUNCHED(rt, "u_update", st);
             }

@@ -157,9 +157,11 @@ __device__ __forceinline__ double newton_rsqrt(double x) {
     }
 }
 
-// ashk = (g + 1) / (2 g), the shock coefficient (computed once on the host)
+// ashk = (g + 1) / (2 g), the shock coefficient (computed once on the host);
+// nmax: the cap on Newton iterations (G_NEWTON_MAX unless the rule sets one)
 template <typename T>
-__device__ __forceinline__ Face4<T> riemann(const Face4<T>& L, const Face4<T>& R, T g, double ashk, int* nonconv) {
+__device__ __forceinline__ Face4<T> riemann(const Face4<T>& L, const Face4<T>& R, T g, double ashk, int nmax,
+                                             int* nonconv) {
     const double gd = (double)g;
     const double pl = (double)L.p, pr = (double)R.p, rl = (double)L.r, rr = (double)R.r;
     const double ul = (double)L.u, ur = (double)R.u;
@@ -172,7 +174,7 @@ __device__ __forceinline__ Face4<T> riemann(const Face4<T>& L, const Face4<T>& R
     double ps = div_nr(cr * pl + cl * pr - cl * cr * (ur - ul), cl + cr);
     ps = dfloor(ps, G_P_FLOOR);
     bool conv = false;
-    for (int it = 0; it < G_NEWTON_MAX; ++it) {
+    for (int it = 0; it < nmax; ++it) {
         const double ql = newton_rsqrt<T>(fma(al, ps - pl, 1.0));
         const double qr = newton_rsqrt<T>(fma(ar, ps - pr, 1.0));
         const double iwl = ql * sl, iwr = qr * sr;         // 1 / W_k

@@ -49,6 +49,7 @@ enum Pipeline { PIPE_GENERIC = 0, PIPE_CHAIN2D = 1, PIPE_CHAIN3D = 2, PIPE_GODUN
 // Field ids of a recognised Godunov DAG (x sweep then y sweep, optional CFL).
 struct GodunovMap {
     double gamma = 1.4, cfl = 0.5;
+    int newton_max = 10;          // RIEMANN params[1] when given: cap on Newton iterations (1..10)
     int cfl_rule = -1;
     int sweep_rules[2][8] = {};   // rule ids per axis in kernel order
 };

@@ -798,6 +798,14 @@ bool recognise_godunov(hfav_plan_t* p) {
         if (gamma < 0) gamma = R[0]->params[0];
         for (int k = 0; k < 8; ++k)
             if (R[k]->params.size() >= 1 && R[k]->params[0] != gamma) return false;
+        if (R[5]->params.size() >= 2) {   // riemann: optional cap on the Newton iterations
+            const double nm = R[5]->params[1];
+            if (!(nm >= 1 && nm <= 10) || nm != (double)(int)nm) return false;
+            if (ax == 1 && (int)nm != p->gmap.newton_max) return false;
+            p->gmap.newton_max = (int)nm;
+        } else if (ax == 1 && p->gmap.newton_max != 10) {
+            return false;
+        }
         const std::vector<int>& W = R[0]->out;   // rho un ut e
         // eos: rho e -> p c
         if (R[1]->in.size() != 2 || R[1]->out.size() != 2 || !ref0(R[1]->in[0], W[0], 0) || !ref0(R[1]->in[1], W[3], 0)) return false;

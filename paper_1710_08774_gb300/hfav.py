@@ -339,10 +339,11 @@ def cosmo_dag(c=0.05, ndim=3):
     return D
 
 
-def godunov_dag(gamma=1.4, cfl=0.5, axes=(0, 1)):
+def godunov_dag(gamma=1.4, cfl=0.5, axes=(0, 1), newton_max=None):
     """Directionally split Godunov step: the Hydro2D kernels once per pass
     (x then y), the CFL time step as a reduction of the state entering the
-    step, and the goals fed back as next step's axioms."""
+    step, and the goals fed back as next step's axioms.  newton_max (1..10)
+    caps the Riemann solver's Newton iterations (default 10)."""
     D = DagSpec(2, stream_axis=1, feedback=True)
     U = ["U0", "U1", "U2", "U3"]
     D.field("dt", rank=0)
@@ -364,7 +365,7 @@ def godunov_dag(gamma=1.4, cfl=0.5, axes=(0, 1)):
         D.rule("QLEFTRIGHT", [(q, (0, 0)) for q in qp] + [(q, _off(a, 1)) for q in qm], qL + qR, params=[gamma],
                axis=a)
         g = [f(f"g{k}") for k in range(4)]
-        D.rule("RIEMANN", qL + qR, g, params=[gamma], axis=a)
+        D.rule("RIEMANN", qL + qR, g, params=[gamma] if newton_max is None else [gamma, newton_max], axis=a)
         F = [f(f"F{k}") for k in range(4)]
         D.rule("CMPFLX", g, F, params=[gamma], axis=a)
         nxt = [f"U{k}_{s}" for k in range(4)]
@@ -540,7 +541,8 @@ def analyze(dag, extent=None):
 # ---------------------------------------------------------------------------
 def probe_peaks(stream=None):
     """Measured peaks of the current device: FP64 FMA/s (the FP64 pipe's issue
-    rate), FP64 divide/s, sqrt/s, rsqrt/s and FP32 FMA/s (per second, whole GPU)."""
+    rate), FP64 divide/s, sqrt/s, rsqrt/s and FP32 FMA/s (per second, whole
+    GPU)."""
     r = (ctypes.c_double * 5)()
     check(load().hfav_probe_peaks(r, 5, _stream(stream)))
     return dict(dfma=r[0], ddiv=r[1], dsqrt=r[2], drsqrt=r[3], ffma=r[4])

@@ -1,5 +1,8 @@
 """Declared in/out aliasing (Sec. 3.5 "In/out chaining") on the GPU: an
-in-place run gives bit for bit the result of the out-of-place run.
+in-place run gives bit for bit the result of the out-of-place run, and both
+equal the CPU oracle (oracle.chain2d for the chain, oracle/expr.py for rule
+bodies and random DAGs, oracle.cosmo) within the FP64 bar (1e-12 normwise;
+FP32 2e-5).
 
 - Generated fused 2D kernels update in place, reading the halo bands at CTA
   boundaries from copies saved before the launch: the 2D chain as rule
@@ -12,10 +15,12 @@ in-place run gives bit for bit the result of the out-of-place run.
 import numpy as np
 import pytest
 
+import oracle
+from oracle import expr as E
 from paper_1710_08774_gb300 import hfav as H
 from paper_1710_08774_gb300 import inputs as I
 from tests import expr_dags as X
-from tests.gpu_util import to_dev
+from tests.gpu_util import normwise, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -50,6 +55,7 @@ def test_chain_as_rule_bodies_in_place(schedule, shape):
     u = I.chain2d_input(shape[0], seed=1, ny=shape[1])
     ref, got, P = _twice(D, [u], 2, schedule)
     assert np.array_equal(ref, got)
+    assert normwise(got, oracle.chain2d(u)[2]) <= 1e-12
     if schedule.startswith("full"):   # the two band kernels and the update, no snapshot copy
         assert P.status()["last_launches"] == 3
 
@@ -63,6 +69,8 @@ def test_chain_in_place_f32_and_halo_given(dtype, bc):
     u = rng.uniform(0, 1, (904, 1203)).astype(dtype)
     ref, got, _ = _twice(D, [u], 2, "full:smem:32x4", dtype, bc)
     assert np.array_equal(ref, got)
+    want = oracle.chain2d(u.astype(np.float64), periodic=bc == H.HFAV_BC_PERIODIC)[2]
+    assert normwise(got, want) <= (1e-12 if dtype == np.float64 else 2e-5)
 
 
 @pytest.mark.parametrize("seed", range(5))
@@ -84,8 +92,12 @@ def test_random_dags_in_place(seed, schedule):
         arr[h:-h, h:-h] = core[a]
         arrs.append(arr)
     ref, got, P = _twice(D, arrs, h, schedule, n_goals=len(goals))
-    for r, g in zip(ref, got):
+    if len(goals) == 1:
+        ref, got = [ref], [got]
+    want = E.evaluate(X.to_oracle(rules), core)
+    for r, g, name in zip(ref, got, goals):
         assert np.array_equal(r, g)
+        assert normwise(g, want[name]) <= 1e-12, name
 
 
 def test_pointwise_in_place():
@@ -96,6 +108,7 @@ def test_pointwise_in_place():
     u, v = rng.normal(size=(302, 502)), rng.normal(size=(302, 502))
     ref, got, _ = _twice(D, [u, v], 1, "full:smem:32x4", alias=1)
     assert np.array_equal(ref, got)
+    assert normwise(got, u[1:-1, 1:-1] * 0.5 + np.sqrt(np.abs(v[1:-1, 1:-1]))) <= 1e-12
 
 
 @pytest.mark.parametrize("case", ["chain2d", "cosmo2d", "normalization"])
@@ -110,6 +123,13 @@ def test_snapshot_paths(case):
     D.inout(D.names[D.goals[0]], D.names[D.axioms[0]])
     ref, got, _ = _twice(D, [u], h, sched)
     assert np.array_equal(ref, got)
+    if case == "chain2d":
+        want = oracle.chain2d(u)[2]
+    elif case == "cosmo2d":
+        want = oracle.cosmo(np.stack([u] * 5), 0.05)[3][0]   # one plane; the k halo is never read
+    else:
+        want = E.evaluate(E.normalization_rules(), {"u": u[1:-1, 1:-1]})["out"]
+    assert normwise(got, want) <= 1e-12
 
 
 def test_undeclared_alias_refused_and_graph_replay():
@@ -120,8 +140,10 @@ def test_undeclared_alias_refused_and_graph_replay():
         P.run([u], [u])
     D = H.chain2d_expr_dag()
     D.inout("out", "u")
-    ref, got, _ = _twice(D, [I.chain2d_input(1100, seed=2, ny=600)], 2, "full:smem:32x4", graph=True)
+    u = I.chain2d_input(1100, seed=2, ny=600)
+    ref, got, _ = _twice(D, [u], 2, "full:smem:32x4", graph=True)
     assert np.array_equal(ref, got)
+    assert normwise(got, oracle.chain2d(u)[2]) <= 1e-12
 
 
 def test_autotune_leaves_in_place_arrays_unchanged():

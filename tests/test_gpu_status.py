@@ -7,6 +7,13 @@
 - Checkpoint / resume: 5 steps, the state copied to the host and back, then 5
   more steps equal 10 steps in one run bit for bit, and the oracle's 10 steps
   to 1e-12.
+- The two-shock Newton iteration converges within its cap of 10 on every
+  state tried (random states over 16 decades of density and 19 of pressure,
+  collisions up to Mach 1e8; see the oracle pins), so physical data do not
+  reach the cap; with the cap set to one iteration through the RIEMANN
+  rule's parameter,
+  hfav_status returns HFAV_WARN_NEWTON with the count of faces, and the
+  default cap reports none.
 - An injected allocation failure (hfav_inject_alloc_failure) makes the run
   that meets it return HFAV_ENOMEM, on the plan's first allocation and on a
   later one; the same plan then runs and matches the oracle.
@@ -21,7 +28,7 @@ from tests.gpu_util import empty_like_state, normwise, state_tensors
 
 pytestmark = pytest.mark.gpu
 
-ENOMEM, ENONPHYSICAL = -7, -10
+ENOMEM, ENONPHYSICAL, WARN_NEWTON = -7, -10, 1
 
 
 def _host(ts):
@@ -103,3 +110,20 @@ def test_injected_allocation_failure(after):
     s = P.status()
     assert s["nonphysical"] == 0
     assert max(_errs(_host(outs), ref)) <= 1e-12
+
+
+@pytest.mark.parametrize("schedule", ["sweep:reg:32x4", "full:reg:32x4", "unfused"])
+def test_newton_cap_reports_warning(schedule):
+    import torch
+    U = I.sod_state(64, 48, seed=3)
+    ins = state_tensors(U, torch.float64)
+    outs = empty_like_state(ins)
+    P = H.Plan(H.godunov_dag(newton_max=1), [H.Grid.of(ins[0], 0)], H.HFAV_F64, H.HFAV_BC_PERIODIC, schedule)
+    P.run(ins, outs, 2)
+    s = P.status()
+    assert s["rc"] == WARN_NEWTON and s["newton_nonconverged"] > 0 and s["nonphysical"] == 0
+    Q = H.Plan(H.godunov_dag(newton_max=10), [H.Grid.of(ins[0], 0)], H.HFAV_F64, H.HFAV_BC_PERIODIC, schedule)
+    Q.run(ins, outs, 2)
+    s = Q.status()
+    assert s["rc"] == 0 and s["newton_nonconverged"] == 0
+    assert max(_errs(_host(outs), oracle.godunov(U, 2)[0])) <= 1e-12

@@ -74,3 +74,9 @@ def test_schedule_environment_override(monkeypatch):
     with pytest.raises(H.HfavError) as e:
         H.Plan(H.chain2d_dag(), g, H.HFAV_F64)
     assert e.value.code == EINVAL
+
+
+@pytest.mark.parametrize("cap", [0, 11, 2.5])
+def test_newton_cap_out_of_range_refused(cap):
+    with pytest.raises(H.HfavError):
+        H.Plan(H.godunov_dag(newton_max=cap), [H.Grid.make((64, 48), (1, 64), 0)], H.HFAV_F64, H.HFAV_BC_PERIODIC)
