@@ -373,10 +373,10 @@ class Chain(Workload):
         if dims == 2:
             u = I.chain2d_input(n, seed=seed)
             dag, halo = (H.chain2d_expr_dag() if expr else H.chain2d_dag()), 2
-        else:
+        else:   # a periodic grid stored without halo (its halo would never be read)
             import numpy as np
-            u = I.chain3d_input(n, seed=seed, dtype=np.float32 if dtype == "f32" else np.float64)
-            dag, halo = H.chain3d_dag(), 3
+            u = I.chain3d_input(n, seed=seed, dtype=np.float32 if dtype == "f32" else np.float64, halo=0)
+            dag, halo = H.chain3d_dag(), 0
         self.u = torch.from_numpy(u).to(dev).to(td)
         self.out = torch.empty_like(self.u)
         self.dag = dag

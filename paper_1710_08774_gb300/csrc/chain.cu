@@ -17,6 +17,7 @@
 #include <type_traits>
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace hfav {
 
@@ -817,6 +818,7 @@ struct C3Args {
     double a1[7], a2[7];   // weights: centre, +i, -i, +j, -j, +k, -k
     float f1[7], f2[7];    // the same, rounded to FP32
     void* slab;
+    unsigned* err;         // set when a bounded wait on a copy gave up (the plan's timeout word)
 };
 
 template <typename T>
@@ -934,7 +936,16 @@ struct C3Tile {
     // u planes are fetched ND planes ahead with asynchronous copies into a
     // ring of ND + 2 plane buffers (the s1 stage reads planes kk-1 and kk)
     static constexpr int ND = 2, NB = ND + 2;
+    // TMA form: cells of a periodic edge tile patched per thread (one i band
+    // of 4 columns and one j band of 3 rows at most)
+    static constexpr int NF = (3 * W + 4 * RU + NT - 1) / NT;
     static constexpr size_t smem(size_t es) { return (size_t)(NB * PU + 3 * P1 + 3 * P2) * es; }
+    // TMA form: u plane slots padded to 128 bytes (copy destinations), the
+    // NB completion barriers after the rings, 128 bytes to align the base
+    static constexpr int pua(size_t es) { return (int)(((size_t)PU * es + 127) / 128 * 128 / es); }
+    static constexpr size_t smem_tma(size_t es) {
+        return (size_t)(NB * pua(es) + 3 * P1 + 3 * P2) * es + NB * 8 + 128;
+    }
 };
 
 template <typename T>
@@ -984,22 +995,73 @@ __device__ __forceinline__ T chain3_out(T gx, T gy, T gz) {
     }
 }
 
-template <typename T, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a) {
+// LOAD selects how u planes reach shared memory: 0, one cp.async per element
+// (any layout); 1, the tensor memory accelerator -- one tiled tensor copy of
+// the whole W x RU plane tile per plane, completed on one mbarrier per ring
+// slot, with the cells a periodic edge tile wraps to patched from registers
+// after the copy lands.  The host takes LOAD 1 only where the copy is
+// 16-byte aligned and a tile touches at most one edge per axis (see
+// launch_c3regw).
+template <typename T, int TX, int TY, int LOAD>
+__global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a, const __grid_constant__ CUtensorMap tmap) {
     using G = C3Tile<TX, TY>;
     using V = typename Pair<T>::type;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T* U = (T*)smem_raw;          // [NB][PU] ring of u planes
-    T* S1 = U + G::NB * G::PU;    // [3][P1] ring of s1 planes
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* sbase = smem_raw;
+    if constexpr (LOAD == 1) sbase += (128u - (smem_u32(smem_raw) & 127u)) & 127u;
+    constexpr int PUS = LOAD == 1 ? G::pua(sizeof(T)) : G::PU;   // stride of the u plane slots
+    T* U = (T*)sbase;             // [NB][PUS] ring of u planes
+    T* S1 = U + G::NB * PUS;      // [3][P1] ring of s1 planes
     T* S2 = S1 + 3 * G::P1;       // [3][P2] ring of s2 planes
+    unsigned long long* bars = (unsigned long long*)(S2 + 3 * G::P2);   // LOAD 1: one per u slot
     const int tid = threadIdx.y * TX + threadIdx.x;
     const int i0 = blockIdx.x * TX, j0 = blockIdx.y * G::TYO, k0 = blockIdx.z * a.K;
     const T* u = (const T*)a.u.p;
     // loaded u elements: in-plane global offset (wrapped / halo-given;
     // 32-bit, a padded plane is far below 2^31 elements) and shared offset
-    int gu[G::NU], su[G::NU];
+    constexpr int NUL = LOAD == 0 ? G::NU : 1;
+    int gu[NUL], su[NUL];
+    // LOAD 1 on a periodic grid: a tile on the i or j edge gets from its
+    // box the out-of-range cells of the plane tile as zeros (or as the
+    // array's unread halo); those cells -- three rows of the j edge, four
+    // columns of the i edge -- are patched with their wrapped values, which
+    // each thread (up to G::NF cells) loads two planes ahead into registers
+    // and stores once the plane's copy has landed
+    const bool iedge = a.u.wrap && (i0 == 0 || i0 + TX >= a.nx);
+    const bool jedge = a.u.wrap && (j0 == 0 || j0 + G::TYO >= a.ny);
+    const bool patch = LOAD == 1 && (iedge || jedge);
+    int pso[G::NF];       // patched cell: shared offset in the plane slot (-1: none)
+    int pgo[G::NF];       // its wrapped in-plane global offset
+    T pv0[G::NF], pv1[G::NF], pv2[G::NF];   // its values for planes it, it + 1, it + 2
+    bool timed_out = false;
+    if constexpr (LOAD == 1) {
+        const int nj = jedge ? 3 : 0, ni = iedge ? 4 : 0;
+        const int rj0 = j0 == 0 ? 0 : G::RU - 3;         // rows of the j band
+        const int ci0 = i0 == 0 ? 0 : G::W - 4;          // columns of the i band
+        const int ro0 = (jedge && j0 == 0) ? 3 : 0;      // first row outside the j band
+        const int ncell = nj * G::W + ni * (G::RU - nj);
 #pragma unroll
-    for (int r = 0; r < G::NU; ++r) {
+        for (int f = 0; f < G::NF; ++f) {
+            const int e = tid + f * G::NT;
+            pso[f] = -1;
+            pgo[f] = 0;
+            pv0[f] = pv1[f] = pv2[f] = (T)0;
+            if (!patch || e >= ncell) continue;
+            int r, c;
+            if (e < nj * G::W) { r = rj0 + e / G::W; c = e % G::W; }
+            else { const int q = e - nj * G::W; r = ro0 + q / 4; c = ci0 + q % 4; }
+            const int gi = wrap_idx(i0 - 4 + c, a.nx), gj = wrap_idx(j0 - 3 + r, a.ny);
+            pso[f] = r * G::W + c;
+            pgo[f] = (int)((int64_t)(gj + a.u.org[1]) * a.u.pitch[1] + (gi + a.u.org[0]));
+        }
+        if (tid == 0) {
+            for (int b = 0; b < G::NB; ++b) mbar_init(bars + b, 1);
+            mbar_init_fence();
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < (LOAD == 0 ? G::NU : 0); ++r) {
         const int e = min(tid + r * G::NT, G::LU - 1);
         const int row = e / G::WL, col = e - row * G::WL;
         int gi = i0 - 3 + col, gj = j0 - 3 + row;
@@ -1050,29 +1112,70 @@ __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a) {
     const int nu = a.K + 6, nit = a.K + 8;
     const int64_t kstep = a.out.pitch[2];
     auto fetch = [&](int it) {
-        if (it < nu) {
+        if constexpr (LOAD == 0) {
+            if (it < nu) {
+                const int kk = k0 - 3 + it;
+                const int kw = a.u.wrap ? wrap_idx(kk, a.nz) : min(max(kk, -3), a.nz + 2);
+                const T* ub = u + (int64_t)(kw + a.u.org[2]) * a.u.pitch[2];
+                T* Ub = U + (it % G::NB) * PUS;
+#pragma unroll
+                for (int r = 0; r < G::NU; ++r)
+                    if (r < G::NU - 1 || tid + r * G::NT < G::LU) cp_async_el<sizeof(T)>(Ub + su[r], ub + gu[r]);
+            }
+            cp_async_commit();   // one group per plane, empty past the chunk's end
+        } else {
+            if (it >= nu) return;
             const int kk = k0 - 3 + it;
             const int kw = a.u.wrap ? wrap_idx(kk, a.nz) : min(max(kk, -3), a.nz + 2);
-            const T* ub = u + (int64_t)(kw + a.u.org[2]) * a.u.pitch[2];
-            T* Ub = U + (it % G::NB) * G::PU;
+            if (tid == 0) {
+                T* Ub = U + (it % G::NB) * PUS;
+                unsigned long long* bar = bars + it % G::NB;
+                // the slot's previous plane was read before the barrier this
+                // thread just passed; order those reads before the copy's writes
+                fence_proxy_async_smem();
+                mbar_arrive_expect_tx(bar, (unsigned)(G::PU * sizeof(T)));
+                // column i0 - 4 + c at c, row j0 - 3 + r at r: the W x RU plane tile
+                tma_load_3d(Ub, &tmap, i0 - 4 + a.u.org[0], j0 - 3 + a.u.org[1], kw + a.u.org[2], bar);
+            }
+            if (patch) {   // wrapped cells of plane it, two planes ahead of their use
+                const T* pl = u + (int64_t)(kw + a.u.org[2]) * a.u.pitch[2];
 #pragma unroll
-            for (int r = 0; r < G::NU; ++r)
-                if (r < G::NU - 1 || tid + r * G::NT < G::LU) cp_async_el<sizeof(T)>(Ub + su[r], ub + gu[r]);
+                for (int f = 0; f < G::NF; ++f)
+                    if (pso[f] >= 0) pv2[f] = pl[pgo[f]];
+            }
         }
-        cp_async_commit();   // one group per plane, empty past the chunk's end
     };
+    static_assert(G::ND == 2, "the patch registers hold two planes ahead");
+    fetch(0);
+    if constexpr (LOAD == 1) {
 #pragma unroll
-    for (int it = 0; it < G::ND; ++it) fetch(it);
+        for (int f = 0; f < G::NF; ++f) pv0[f] = pv2[f];
+    }
+    fetch(1);
+    if constexpr (LOAD == 1) {
+#pragma unroll
+        for (int f = 0; f < G::NF; ++f) pv1[f] = pv2[f];
+    }
     int c0 = 0, c1 = 1, c2 = 2;   // it % 3, (it + 1) % 3, (it + 2) % 3
     for (int it = 0; it < nit; ++it) {
-        cp_async_wait<G::ND - 1>();   // this thread's copies of plane it are done
+        if constexpr (LOAD == 0) {
+            cp_async_wait<G::ND - 1>();   // this thread's copies of plane it are done
+        } else if (it < nu) {
+            if (!mbar_wait_bounded(bars + it % G::NB, (unsigned)(it / G::NB) & 1u, a.err)) timed_out = true;
+            if (patch) {   // the copy has landed: overwrite its out-of-range cells
+                T* Ub = U + (it % G::NB) * PUS;
+#pragma unroll
+                for (int f = 0; f < G::NF; ++f)
+                    if (pso[f] >= 0) Ub[pso[f]] = pv0[f];
+            }
+        }
         __syncthreads();
         // the slot of plane it + ND held plane it - 2, last read at it - 1
         fetch(it + G::ND);
         // s1 at plane kk-1: window u(kk-2 .. kk), in-plane neighbours from u(kk-1)
         if (it < nu) {
-            const T* Ub = U + (it % G::NB) * G::PU;
-            const T* Up = U + ((it + G::NB - 1) % G::NB) * G::PU;
+            const T* Ub = U + (it % G::NB) * PUS;
+            const T* Up = U + ((it + G::NB - 1) % G::NB) * PUS;
             T* S1b = S1 + c0 * G::P1;
             const bool comp = it >= 2;
 #pragma unroll
@@ -1140,6 +1243,17 @@ __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a) {
             }
         }
         const int t = c0; c0 = c1; c1 = c2; c2 = t;
+        if constexpr (LOAD == 1) {
+#pragma unroll
+            for (int f = 0; f < G::NF; ++f) { pv0[f] = pv1[f]; pv1[f] = pv2[f]; }
+        }
+    }
+    if constexpr (LOAD == 1) {
+        // after a timed-out wait, give the copies still in flight (the last
+        // plane of each slot) a bounded time to land before the CTA exits
+        if (timed_out)
+            for (int it = max(0, nu - G::NB); it < nu; ++it)
+                mbar_wait_bounded(bars + it % G::NB, (unsigned)(it / G::NB) & 1u, nullptr);
     }
 }
 
@@ -1161,14 +1275,31 @@ int chunk_planes(int64_t tiles, int nz, int64_t cap, int lead) {
 }
 }  // namespace
 
-template <typename T, int TX, int TY>
-static int launch_c3regw(hfav_plan_t* p, C3Args& a, cudaStream_t st) {
+// The TMA load form needs the copy 16-byte aligned: the row and plane
+// pitches and the column i0 - 4 of a tile (i0 a multiple of TX) after the
+// array's halo offset.  On a periodic grid whole tiles (nx a multiple of TX,
+// ny of TYO) and at least two per axis, so that a tile patches at most one
+// i band and one j band.  Halo-given grids read their halo through the box,
+// which starts 4 columns and 3 rows / planes before the interior.
+template <typename T, int TX, int TYO>
+static bool c3_tma_ok(const C3Args& a) {
+    const int A = 16 / (int)sizeof(T);
+    const int64_t es = sizeof(T);
+    if ((a.u.pitch[1] * es) % 16 || (a.u.pitch[2] * es) % 16 || ((uintptr_t)a.u.p & 15)) return false;
+    if (((a.u.org[0] - 4) % A + A) % A) return false;
+    if (a.u.wrap) return a.nx % TX == 0 && a.nx >= 2 * TX && a.ny % TYO == 0 && a.ny >= 2 * TYO;
+    return a.u.org[0] >= 4 && a.u.org[1] >= 3 && a.u.org[2] >= 3;
+}
+
+template <typename T, int TX, int TY, int LOAD>
+static int launch_c3regw_load(hfav_plan_t* p, C3Args& a, const CUtensorMap& map, cudaStream_t st) {
     using G = C3Tile<TX, TY>;
-    const size_t sm = G::smem(sizeof(T));
-    cudaFuncSetAttribute(chain3d_regw<T, TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    const size_t sm = LOAD == 1 ? G::smem_tma(sizeof(T)) : G::smem(sizeof(T));
+    cudaFuncSetAttribute(chain3d_regw<T, TX, TY, LOAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     static int occ = 0;   // resident CTAs per SM (same on every device of the one target)
     if (!occ) {
-        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, chain3d_regw<T, TX, TY>, G::NT, sm) != cudaSuccess ||
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, chain3d_regw<T, TX, TY, LOAD>, G::NT, sm) !=
+                cudaSuccess ||
             occ <= 0) {
             cudaGetLastError();
             occ = 1;
@@ -1177,9 +1308,26 @@ static int launch_c3regw(hfav_plan_t* p, C3Args& a, cudaStream_t st) {
     const int64_t tiles = (int64_t)((a.nx + TX - 1) / TX) * ((a.ny + G::TYO - 1) / G::TYO);
     a.K = chunk_planes(tiles, a.nz, (int64_t)occ * device_sms(), 8);
     dim3 grd((a.nx + TX - 1) / TX, (a.ny + G::TYO - 1) / G::TYO, (a.nz + a.K - 1) / a.K);
-    chain3d_regw<T, TX, TY><<<grd, dim3(TX, TY), sm, st>>>(a);
-    HFAV_LAUNCHED(p->rt, "chain3d_fused", st);
+    chain3d_regw<T, TX, TY, LOAD><<<grd, dim3(TX, TY), sm, st>>>(a, map);
+    HFAV_LAUNCHED(p->rt, LOAD == 1 ? "chain3d_fused_tma" : "chain3d_fused", st);
     return HFAV_OK;
+}
+
+template <typename T, int TX, int TY>
+static int launch_c3regw(hfav_plan_t* p, C3Args& a, cudaStream_t st) {
+    using G = C3Tile<TX, TY>;
+    CUtensorMap map;
+    memset(&map, 0, sizeof map);
+    a.err = (unsigned*)(p->rt->counters + 2);
+    if (c3_tma_ok<T, TX, G::TYO>(a)) {
+        const int h0 = a.u.org[0], h1 = a.u.org[1], h2 = a.u.org[2];
+        const uint64_t dims[3] = {(uint64_t)(a.nx + 2 * h0), (uint64_t)(a.ny + 2 * h1), (uint64_t)(a.nz + 2 * h2)};
+        const uint64_t strides[2] = {(uint64_t)(a.u.pitch[1] * sizeof(T)), (uint64_t)(a.u.pitch[2] * sizeof(T))};
+        const uint32_t box[3] = {(uint32_t)G::W, (uint32_t)G::RU, 1};
+        if (encode_tensor_map_3d(&map, a.u.p, (int)sizeof(T), dims, strides, box))
+            return launch_c3regw_load<T, TX, TY, 1>(p, a, map, st);
+    }
+    return launch_c3regw_load<T, TX, TY, 0>(p, a, map, st);
 }
 
 template <typename T>
@@ -1341,7 +1489,7 @@ double chain_warps_t(const hfav_plan_t* p, const Schedule& s) {
 #define C3W(a, b)                                                                                             \
     if (TX == a && TY == b) {                                                                                 \
         using G = C3Tile<a, b>;                                                                               \
-        return warps_of(chain3d_regw<T, a, b>, NT, G::smem(es));                                              \
+        return warps_of(chain3d_regw<T, a, b, 1>, NT, G::smem_tma(es));                                       \
     }
         C3W(32, 4) C3W(64, 4) C3W(128, 2) C3W(32, 8)
 #undef C3W

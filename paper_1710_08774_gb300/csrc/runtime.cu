@@ -7,7 +7,12 @@
 #include <cstring>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace hfav {
 
@@ -88,6 +93,8 @@ int redirect_inplace(hfav_plan_t* p, void* const* ax, void* const* go, cudaStrea
 // update still needs go to temporaries before the output is written)
 int launch_once(hfav_plan_t* p, const Schedule& s, void* const* ax, void* const* go, int n_steps, cudaStream_t st) {
     const size_t na = p->dag.axioms.size(), nq = p->dag.goals.size(), ng = p->grids.size();
+    // the run's wait-timeout word (kernels with bounded waits on copies set it)
+    HFAV_CUDA(cudaMemsetAsync(p->rt->counters + 2, 0, sizeof(unsigned long long), st));
     std::vector<void*> axs(ax, ax + ng * na);
     bool copied = false;
     if (!(p->pipeline == PIPE_CODEGEN && codegen_inplace(p, s)))
@@ -147,6 +154,34 @@ void kt_mark(Runtime* rt, const char* name, cudaStream_t st) {
     rt->kname[rt->kused] = name;
     cudaEventRecord(rt->kpool[rt->kused], st);
     rt->kused++;
+}
+
+bool encode_tensor_map_3d(CUtensorMap* map, const void* base, int es, const uint64_t dims[3],
+                          const uint64_t strides_bytes[2], const uint32_t box[3]) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+        else
+            cudaGetLastError();
+    });
+    if (!encode || (es != 4 && es != 8) || ((uintptr_t)base & 15)) return false;
+    if ((strides_bytes[0] & 15) || (strides_bytes[1] & 15) || ((box[0] * (uint32_t)es) & 15)) return false;
+    for (int d = 0; d < 3; ++d)
+        if (box[d] < 1 || box[d] > 256 || dims[d] < 1) return false;
+    const cuuint64_t gdim[3] = {dims[0], dims[1], dims[2]};
+    const cuuint64_t gstr[2] = {strides_bytes[0], strides_bytes[1]};
+    const cuuint32_t bdim[3] = {box[0], box[1], box[2]};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    CUresult r = encode(map, es == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+                        const_cast<void*>(base), gdim, gstr, bdim, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
 }
 
 int device_sms() {
@@ -345,7 +380,7 @@ int status(hfav_plan_t* p, hfav_run_stats* s) {
     Runtime* rt = p->rt;
     if (!rt) return HFAV_OK;
     HFAV_CUDA(cudaStreamSynchronize(rt->last_stream));
-    unsigned long long c[2];
+    unsigned long long c[3];
     HFAV_CUDA(cudaMemcpy(c, rt->counters, sizeof c, cudaMemcpyDeviceToHost));
     s->newton_nonconverged = (int64_t)c[0];
     s->nonphysical = (int64_t)c[1];
@@ -365,6 +400,7 @@ int status(hfav_plan_t* p, hfav_run_stats* s) {
         }
         s->n_dt = n;
     }
+    if (c[2]) return set_error(HFAV_ETIMEOUT, "a kernel gave up waiting for an asynchronous copy");
     if (s->nonphysical) return set_error(HFAV_ENONPHYSICAL, "non-physical state (rho <= 0 or p <= 0) produced");
     if (s->newton_nonconverged) {
         set_error(HFAV_WARN_NEWTON, "Newton iteration hit the cap on some faces");
