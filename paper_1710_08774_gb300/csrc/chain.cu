@@ -969,6 +969,17 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// the same star summed as a tree of pairs (three dependent steps instead of
+// seven), for the FP32 quad kernel: a different rounding order, within the
+// FP32 bar
+__device__ __forceinline__ float pt7t(const float* w, float ip, float im, float jp, float jm, float kp, float km,
+                                      float c) {
+    const float a = fmaf(w[2], im, w[1] * ip);
+    const float b = fmaf(w[4], jm, w[3] * jp);
+    const float d = fmaf(w[6], km, w[5] * kp);
+    return fmaf(w[0], c, a) + (b + d);
+}
+
 // one 7-point star in the rule's summation order (+i, -i, +j, -j, +k, -k, centre)
 template <typename T>
 __device__ __forceinline__ T pt7(const T* w, T ip, T im, T jp, T jm, T kp, T km, T c) {
@@ -1006,7 +1017,7 @@ template <typename T, int TX, int TY, int LOAD>
 __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a, const __grid_constant__ CUtensorMap tmap) {
     using G = C3Tile<TX, TY>;
     using V = typename Pair<T>::type;
-    extern __shared__ __align__(128) unsigned char smem_raw[];
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     unsigned char* sbase = smem_raw;
     if constexpr (LOAD == 1) sbase += (128u - (smem_u32(smem_raw) & 127u)) & 127u;
     constexpr int PUS = LOAD == 1 ? G::pua(sizeof(T)) : G::PU;   // stride of the u plane slots
@@ -1257,6 +1268,221 @@ __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a, const __
     }
 }
 
+// FP32 register-window form on quads.  The same plane tiles, rings, skewed
+// pipeline and TMA staging as chain3d_regw (LOAD 1), with each thread
+// evaluating a stage on quads of four adjacent cells (16-byte shared loads
+// and stores, one pair of scalar i-neighbour loads per four cells) and the
+// plane loop unrolled by three so that the k windows, the s1 / s2 ring
+// slots and the patch registers rotate by index instead of by copies.
+// Output quads are stored as 16-byte vectors.  Taken for FP32 where the TMA
+// copy applies (the host's c3_tma_ok), which also makes every output quad
+// whole and aligned.
+template <int TX, int TY>
+struct C3Quad {
+    using G = C3Tile<TX, TY>;
+    static constexpr int NT = G::NT, W = G::W;
+    static constexpr int Q1 = G::P1 / 4, Q2 = G::P2 / 4, QO = TX * G::TYO / 4;
+    static constexpr int N1 = (Q1 + NT - 1) / NT, N2 = (Q2 + NT - 1) / NT, NO = (QO + NT - 1) / NT;
+    static_assert(W % 4 == 0 && TX % 4 == 0, "quads tile the plane rows");
+};
+
+template <int V>
+using IC = std::integral_constant<int, V>;
+
+template <int TX, int TY>
+__global__ void __launch_bounds__(TX * TY) chain3d_quad(const C3Args a, const __grid_constant__ CUtensorMap tmap) {
+    using G = C3Tile<TX, TY>;
+    using Q = C3Quad<TX, TY>;
+    constexpr int W = G::W;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    unsigned char* sbase = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
+    constexpr int PUS = G::pua(sizeof(float));
+    float* U = (float*)sbase;        // [NB][PUS] ring of u planes
+    float* S1 = U + G::NB * PUS;     // [3][P1] ring of s1 planes
+    float* S2 = S1 + 3 * G::P1;      // [3][P2] ring of s2 planes
+    unsigned long long* bars = (unsigned long long*)(S2 + 3 * G::P2);
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * G::TYO, k0 = blockIdx.z * a.K;
+    const float* u = (const float*)a.u.p;
+    // periodic edge tiles: the out-of-range band cells of the box, patched
+    // from registers loaded two planes ahead (as in chain3d_regw)
+    const bool iedge = a.u.wrap && (i0 == 0 || i0 + TX >= a.nx);
+    const bool jedge = a.u.wrap && (j0 == 0 || j0 + G::TYO >= a.ny);
+    const bool patch = iedge || jedge;
+    int pso[G::NF], pgo[G::NF];
+    float pv[3][G::NF];
+    {
+        const int nj = jedge ? 3 : 0, ni = iedge ? 4 : 0;
+        const int rj0 = j0 == 0 ? 0 : G::RU - 3;
+        const int ci0 = i0 == 0 ? 0 : W - 4;
+        const int ro0 = (jedge && j0 == 0) ? 3 : 0;
+        const int ncell = nj * W + ni * (G::RU - nj);
+#pragma unroll
+        for (int f = 0; f < G::NF; ++f) {
+            const int e = tid + f * G::NT;
+            pso[f] = -1;
+            pgo[f] = 0;
+            pv[0][f] = pv[1][f] = pv[2][f] = 0.f;
+            if (!patch || e >= ncell) continue;
+            int r, c;
+            if (e < nj * W) { r = rj0 + e / W; c = e % W; }
+            else { const int q = e - nj * W; r = ro0 + q / 4; c = ci0 + q % 4; }
+            const int gi = wrap_idx(i0 - 4 + c, a.nx), gj = wrap_idx(j0 - 3 + r, a.ny);
+            pso[f] = r * W + c;
+            pgo[f] = (int)((int64_t)(gj + a.u.org[1]) * a.u.pitch[1] + (gi + a.u.org[0]));
+        }
+    }
+    if (tid == 0) {
+        for (int b = 0; b < G::NB; ++b) mbar_init(bars + b, 1);
+        mbar_init_fence();
+    }
+    __syncthreads();
+    // output quads: quad o = tid + r NT is row o / (TX/4), columns 3 + 4 (o % (TX/4)) .. + 3
+    float* op[Q::NO];
+    int bo[Q::NO];
+    bool oko[Q::NO];
+#pragma unroll
+    for (int r = 0; r < Q::NO; ++r) {
+        const int o = tid + r * Q::NT;
+        oko[r] = o < Q::QO;
+        const int oc = oko[r] ? o : 0;
+        const int row = oc / (TX / 4), qc = oc - row * (TX / 4);
+        op[r] = garr_ptr<float>(a.out, i0 + 4 * qc, j0 + row, min(k0, a.nz - 1));
+        bo[r] = (row + 1) * W + 4 + 4 * qc;
+    }
+    float4 wu[Q::N1][3], w1[Q::N2][3], w2[Q::NO][3];
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int r = 0; r < Q::N1; ++r) wu[r][0] = wu[r][1] = wu[r][2] = zero;
+#pragma unroll
+    for (int r = 0; r < Q::N2; ++r) w1[r][0] = w1[r][1] = w1[r][2] = zero;
+#pragma unroll
+    for (int r = 0; r < Q::NO; ++r) w2[r][0] = w2[r][1] = w2[r][2] = zero;
+    float wa[7], wb[7];
+#pragma unroll
+    for (int x = 0; x < 7; ++x) { wa[x] = a.f1[x]; wb[x] = a.f2[x]; }
+    const int nu = a.K + 6, nit = a.K + 8;
+    const int64_t kstep = a.out.pitch[2];
+    bool timed_out = false;
+    // u plane it: one tensor copy into slot it % NB; its patch values into pv[D]
+    auto fetch = [&](int it, auto D) {
+        constexpr int d = decltype(D)::value;
+        if (it >= nu) return;
+        const int kk = k0 - 3 + it;
+        const int kw = a.u.wrap ? wrap_idx(kk, a.nz) : min(max(kk, -3), a.nz + 2);
+        if (tid == 0) {
+            unsigned long long* bar = bars + it % G::NB;
+            fence_proxy_async_smem();
+            mbar_arrive_expect_tx(bar, (unsigned)(G::PU * sizeof(float)));
+            tma_load_3d(U + (it % G::NB) * PUS, &tmap, i0 - 4 + a.u.org[0], j0 - 3 + a.u.org[1], kw + a.u.org[2],
+                        bar);
+        }
+        if (patch) {
+            const float* pl = u + (int64_t)(kw + a.u.org[2]) * a.u.pitch[2];
+#pragma unroll
+            for (int f = 0; f < G::NF; ++f)
+                if (pso[f] >= 0) pv[d][f] = pl[pgo[f]];
+        }
+    };
+    // one plane iteration; S = it % 3 selects the window slots and rings
+    auto step = [&](auto Sc, int it) {
+        constexpr int s = decltype(Sc)::value, sp = (s + 1) % 3, sm = (s + 2) % 3;
+        if (it < nu) {
+            if (!mbar_wait_bounded(bars + it % G::NB, (unsigned)(it / G::NB) & 1u, a.err)) timed_out = true;
+            if (patch) {
+                float* Ub = U + (it % G::NB) * PUS;
+#pragma unroll
+                for (int f = 0; f < G::NF; ++f)
+                    if (pso[f] >= 0) Ub[pso[f]] = pv[s][f];
+            }
+        }
+        __syncthreads();
+        fetch(it + 2, IC<sm>{});
+        // s1 at plane kk-1 (window slot s holds plane kk, sm kk-1, sp kk-2)
+        if (it < nu) {
+            const float* Ub = U + (it % G::NB) * PUS;
+            const float* Up = U + ((it + G::NB - 1) % G::NB) * PUS;
+            float* S1b = S1 + s * G::P1;
+            const bool comp = it >= 2;
+#pragma unroll
+            for (int r = 0; r < Q::N1; ++r) {
+                const int q = tid + r * Q::NT;
+                if (r == Q::N1 - 1 && q >= Q::Q1) continue;
+                const int b = 4 * q + W;
+                wu[r][s] = *(const float4*)(Ub + b);
+                if (!comp) continue;
+                const float4 n = *(const float4*)(Up + b + W), so = *(const float4*)(Up + b - W);
+                const float l = Up[b - 1], rt = Up[b + 4];
+                const float4 c = wu[r][sm], kp = wu[r][s], km = wu[r][sp];
+                float4 o;
+                o.x = pt7t(wa, c.y, l, n.x, so.x, kp.x, km.x, c.x);
+                o.y = pt7t(wa, c.z, c.x, n.y, so.y, kp.y, km.y, c.y);
+                o.z = pt7t(wa, c.w, c.y, n.z, so.z, kp.z, km.z, c.z);
+                o.w = pt7t(wa, rt, c.z, n.w, so.w, kp.w, km.w, c.w);
+                *(float4*)(S1b + 4 * q) = o;
+            }
+        }
+        // s2 at plane kk-3 from the s1 planes made at it-1 (ring slot sm)
+        // and it-2 (slot sp)
+        if (it >= 3 && it < nu + 1) {
+            const float* S1n = S1 + sm * G::P1;
+            const float* S1p = S1 + sp * G::P1;
+            float* S2b = S2 + s * G::P2;
+            const bool comp = it >= 5;
+#pragma unroll
+            for (int r = 0; r < Q::N2; ++r) {
+                const int q = tid + r * Q::NT;
+                if (r == Q::N2 - 1 && q >= Q::Q2) continue;
+                const int b = 4 * q + W;
+                w1[r][s] = *(const float4*)(S1n + b);
+                if (!comp) continue;
+                const float4 n = *(const float4*)(S1p + b + W), so = *(const float4*)(S1p + b - W);
+                const float l = S1p[b - 1], rt = S1p[b + 4];
+                const float4 c = w1[r][sm], kp = w1[r][s], km = w1[r][sp];
+                float4 o;
+                o.x = pt7t(wb, c.y, l, n.x, so.x, kp.x, km.x, c.x);
+                o.y = pt7t(wb, c.z, c.x, n.y, so.y, kp.y, km.y, c.y);
+                o.z = pt7t(wb, c.w, c.y, n.z, so.z, kp.z, km.z, c.z);
+                o.w = pt7t(wb, rt, c.z, n.w, so.w, kp.w, km.w, c.w);
+                *(float4*)(S2b + 4 * q) = o;
+            }
+        }
+        // out at plane kk-5 from the s2 planes made at it-1 (slot sm) and it-2 (slot sp)
+        if (it >= 6) {
+            const float* S2n = S2 + sm * G::P2;
+            const float* S2p = S2 + sp * G::P2;
+            const bool store = it >= 8 && k0 - 8 + it < a.nz;
+#pragma unroll
+            for (int r = 0; r < Q::NO; ++r) {
+                if (!oko[r]) continue;
+                const int b = bo[r];
+                w2[r][s] = *(const float4*)(S2n + b);
+                if (it < 8) continue;
+                const float4 n = *(const float4*)(S2p + b + W), so = *(const float4*)(S2p + b - W);
+                const float l = S2p[b - 1], rt = S2p[b + 4];
+                const float4 c = w2[r][sm], kp = w2[r][s], km = w2[r][sp];
+                float4 o;
+                o.x = chain3_out<float>(c.y - l, n.x - so.x, kp.x - km.x);
+                o.y = chain3_out<float>(c.z - c.x, n.y - so.y, kp.y - km.y);
+                o.z = chain3_out<float>(c.w - c.y, n.z - so.z, kp.z - km.z);
+                o.w = chain3_out<float>(rt - c.z, n.w - so.w, kp.w - km.w);
+                if (store) *(float4*)op[r] = o;
+                op[r] += kstep;
+            }
+        }
+    };
+    fetch(0, IC<0>{});
+    fetch(1, IC<1>{});
+    for (int it = 0; it < nit; it += 3) {
+        step(IC<0>{}, it);
+        if (it + 1 < nit) step(IC<1>{}, it + 1);
+        if (it + 2 < nit) step(IC<2>{}, it + 2);
+    }
+    if (timed_out)
+        for (int it = max(0, nu - G::NB); it < nu; ++it)
+            mbar_wait_bounded(bars + it % G::NB, (unsigned)(it / G::NB) & 1u, nullptr);
+}
+
 namespace {
 // planes per CTA for the streaming 3D kernel: with `cap` CTAs resident at a
 // time, a launch takes (waves) x (K + lead) iterations; take the K that
@@ -1313,6 +1539,27 @@ static int launch_c3regw_load(hfav_plan_t* p, C3Args& a, const CUtensorMap& map,
     return HFAV_OK;
 }
 
+template <int TX, int TY>
+static int launch_c3quad(hfav_plan_t* p, C3Args& a, const CUtensorMap& map, cudaStream_t st) {
+    using G = C3Tile<TX, TY>;
+    const size_t sm = G::smem_tma(sizeof(float));
+    cudaFuncSetAttribute(chain3d_quad<TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    static int occ = 0;
+    if (!occ) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, chain3d_quad<TX, TY>, G::NT, sm) != cudaSuccess ||
+            occ <= 0) {
+            cudaGetLastError();
+            occ = 1;
+        }
+    }
+    const int64_t tiles = (int64_t)((a.nx + TX - 1) / TX) * ((a.ny + G::TYO - 1) / G::TYO);
+    a.K = chunk_planes(tiles, a.nz, (int64_t)occ * device_sms(), 8);
+    dim3 grd((a.nx + TX - 1) / TX, (a.ny + G::TYO - 1) / G::TYO, (a.nz + a.K - 1) / a.K);
+    chain3d_quad<TX, TY><<<grd, dim3(TX, TY), sm, st>>>(a, map);
+    HFAV_LAUNCHED(p->rt, "chain3d_fused_tma", st);
+    return HFAV_OK;
+}
+
 template <typename T, int TX, int TY>
 static int launch_c3regw(hfav_plan_t* p, C3Args& a, cudaStream_t st) {
     using G = C3Tile<TX, TY>;
@@ -1324,8 +1571,12 @@ static int launch_c3regw(hfav_plan_t* p, C3Args& a, cudaStream_t st) {
         const uint64_t dims[3] = {(uint64_t)(a.nx + 2 * h0), (uint64_t)(a.ny + 2 * h1), (uint64_t)(a.nz + 2 * h2)};
         const uint64_t strides[2] = {(uint64_t)(a.u.pitch[1] * sizeof(T)), (uint64_t)(a.u.pitch[2] * sizeof(T))};
         const uint32_t box[3] = {(uint32_t)G::W, (uint32_t)G::RU, 1};
-        if (encode_tensor_map_3d(&map, a.u.p, (int)sizeof(T), dims, strides, box))
-            return launch_c3regw_load<T, TX, TY, 1>(p, a, map, st);
+        if (encode_tensor_map_3d(&map, a.u.p, (int)sizeof(T), dims, strides, box)) {
+            // quads pay off on the 32-wide tiles (measured at 512^3: 0.495 ms against
+            // 0.507 / 0.556 for pairs); the wider tiles keep the pair kernel
+            if constexpr (sizeof(T) == 4 && TX == 32) return launch_c3quad<TX, TY>(p, a, map, st);
+            else return launch_c3regw_load<T, TX, TY, 1>(p, a, map, st);
+        }
     }
     return launch_c3regw_load<T, TX, TY, 0>(p, a, map, st);
 }
@@ -1489,6 +1740,7 @@ double chain_warps_t(const hfav_plan_t* p, const Schedule& s) {
 #define C3W(a, b)                                                                                             \
     if (TX == a && TY == b) {                                                                                 \
         using G = C3Tile<a, b>;                                                                               \
+        if constexpr (sizeof(T) == 4 && a == 32) return warps_of(chain3d_quad<a, b>, NT, G::smem_tma(es));   \
         return warps_of(chain3d_regw<T, a, b, 1>, NT, G::smem_tma(es));                                       \
     }
         C3W(32, 4) C3W(64, 4) C3W(128, 2) C3W(32, 8)
