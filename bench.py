@@ -88,15 +88,29 @@ COSMO_NZ = 64            # planes of the COSMO workloads
 # ncu capture of the bench's profiling case (summaries under profiles/), with
 # the hash of the kernel sources at capture time: a changed source voids it.
 TRAFFIC = {
-    ("godunov2d_fp64_1024x1024_10steps", "gsweep_y"): (33.7e6, "6082389b4f85d2a4"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "gsweep_x"): (493.1e6, "6082389b4f85d2a4"),
-    ("chain3d_fp32_512x512x512", "chain3d_fused"): (1081.6e6, "118a7c31ec4866ea"),
-    ("chain2d_fp32_16384x16384", "chain2d_fused"): (2129.0e6, "118a7c31ec4866ea"),
-    ("cosmo_fp32_1024x1024x64", "cosmo_fused"): (527.7e6, "118a7c31ec4866ea"),
-    ("codegen_chain2d_fp32_16384x16384", "codegen_fused"): (2173.1e6, "28e0071a5db92c92"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg", "gsweep_y"): (33.65e6, "55662954019f9d94"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg", "gsweep_x"): (33.70e6, "55662954019f9d94"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:smem", "gsweep_y"): (33.61e6, "55662954019f9d94"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:smem", "gsweep_x"): (33.77e6, "55662954019f9d94"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:hbm", "gsweep_y"): (34.50e6, "55662954019f9d94"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:hbm", "gsweep_x"): (94.03e6, "55662954019f9d94"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:reg", "gsweep_x"): (494.5e6, "55662954019f9d94"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:reg", "gsweep_y"): (498.1e6, "55662954019f9d94"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:smem", "gsweep_x"): (491.3e6, "55662954019f9d94"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:smem", "gsweep_y"): (496.0e6, "55662954019f9d94"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:hbm", "gsweep_x"): (558.6e6, "55662954019f9d94"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:hbm", "gsweep_y"): (500.6e6, "55662954019f9d94"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_x"): (2387.8e6, "55662954019f9d94"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_y"): (2446.9e6, "55662954019f9d94"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_x"): (5154.9e6, "55662954019f9d94"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_y"): (2437.7e6, "55662954019f9d94"),
+    ("chain2d_fp32_16384x16384", "full:reg", "chain2d_fused"): (2128.9e6, "dd66a6f65bb32614"),
+    ("chain3d_fp32_512x512x512", "full:reg", "chain3d_fused_tma"): (1061.0e6, "dd66a6f65bb32614"),
+    ("cosmo_fp32_1024x1024x64", "full:reg", "cosmo_fused"): (513.2e6, "dd66a6f65bb32614"),
+    ("codegen_chain2d_fp32_16384x16384", "full:smem", "codegen_fused"): (2172.5e6, "8317c02f6926f6f7"),
     # two generated nests per step, each one array in and one out: the mean of the two launches
-    ("normalization2d_fp32_16384x16384", "codegen_fused"): (2103.4e6, "28e0071a5db92c92"),
-    ("inplace_chain2d_fp32_16384x16384", "codegen_fused"): (2177.5e6, "28e0071a5db92c92"),
+    ("normalization2d_fp32_16384x16384", "full:smem", "codegen_fused"): (2102.9e6, "8317c02f6926f6f7"),
+    ("inplace_chain2d_fp32_16384x16384", "full:smem", "codegen_fused"): (2177.1e6, "8317c02f6926f6f7"),
 }
 
 
@@ -113,26 +127,43 @@ def src_hash(files):
 # one ncu capture (profiles/godunov_fp64_1024_pipe_ncu.md), with the hash of
 # the kernel sources at capture time: a changed source voids it.
 FP64_SLOTS = {
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg:32x4", "gsweep_x"): (296.20e6, "55662954019f9d94"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg:32x4", "gsweep_y"): (333.78e6, "55662954019f9d94"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg:64x4", "gsweep_x"): (296.20e6, "55662954019f9d94"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg:64x4", "gsweep_y"): (333.78e6, "55662954019f9d94"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg", "gsweep_x"): (295.65e6, "55662954019f9d94"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg", "gsweep_y"): (333.76e6, "55662954019f9d94"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:smem", "gsweep_x"): (330.80e6, "55662954019f9d94"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:smem", "gsweep_y"): (400.02e6, "55662954019f9d94"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:hbm", "gsweep_x"): (328.70e6, "55662954019f9d94"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:hbm", "gsweep_y"): (400.02e6, "55662954019f9d94"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:reg", "gsweep_x"): (1921.46e6, "55662954019f9d94"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:reg", "gsweep_y"): (1943.12e6, "55662954019f9d94"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:smem", "gsweep_x"): (1975.59e6, "55662954019f9d94"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:smem", "gsweep_y"): (1959.93e6, "55662954019f9d94"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:hbm", "gsweep_x"): (1975.63e6, "55662954019f9d94"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:hbm", "gsweep_y"): (1959.93e6, "55662954019f9d94"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_x"): (9086.2e6, "55662954019f9d94"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_y"): (9018.4e6, "55662954019f9d94"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_x"): (9153.8e6, "55662954019f9d94"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_y"): (9141.3e6, "55662954019f9d94"),
 }
 
 
+def _family(schedule):
+    """'fusion:placement' of a schedule string (the tile changes neither count)."""
+    return ":".join((schedule or "").split(":")[:2])
+
+
 def fp64_slots_for(workload, schedule, kernel):
-    t = FP64_SLOTS.get((workload, schedule, kernel))
+    t = FP64_SLOTS.get((workload, _family(schedule), kernel))
     if not t:
         return None
     return t[0] if src_hash(["godunov.cu", "godunov_phys.cuh", "common.cuh"]) == t[1] else None
 
 
-def traffic_for(workload, kernel):
-    t = TRAFFIC.get((workload, kernel))
+def traffic_for(workload, schedule, kernel):
+    t = TRAFFIC.get((workload, _family(schedule), kernel))
     if not t:
         return None
     files = ["godunov.cu", "godunov_phys.cuh", "common.cuh"] if kernel.startswith("g") else \
-        ["codegen.cu", "common.cuh"] if kernel.startswith("codegen") else ["chain.cu", "common.cuh"]
+        ["codegen.cu", "common.cuh"] if kernel.startswith("codegen") else ["chain.cu", "common.cuh", "tma.cuh"]
     return t[0] if src_hash(files) == t[1] else None
 
 
@@ -782,7 +813,7 @@ def bench(args, name, torch, H, I, dev, ws, rank, local):
         bound, work, unit, peak, src = w.kernel_work(dom, it_avg, best)
         achieved = work / (dom_ms * 1e-3) / 1e9
         roof = {"bound": bound, "kernel": dom, "achieved": achieved, "peak": peak, "unit": unit,
-                "frac": achieved / peak, "traffic": traffic_for(w.name, dom), "peak_source": src,
+                "frac": achieved / peak, "traffic": traffic_for(w.name, best, dom), "peak_source": src,
                 "launch_ms": dom_ms, "work_per_launch": work}
         if bound == "alu":   # in-run probe: a pure FMA loop, and the slot cost of divide / sqrt / rsqrt
             pr = probe()
