@@ -34,6 +34,11 @@ METRIC = "Gcell-updates/s and % HBM roofline, fused vs unfused on 1 GB300 at sta
 UNIT = "Gcell-updates/s"
 CFL = 0.5
 _PROBE = {}
+# array layout of the 3D chain workloads: (halo, halo given).  The default
+# stores the periodic grid without halo; --chain3d-halo H [--chain3d-halo-given]
+# selects other layouts to compare the kernel's load paths (the same
+# arithmetic: a periodic halo is never read; a given halo holds zeros)
+CHAIN3D_HALO = [0, False]
 
 
 def probe():
@@ -406,18 +411,21 @@ class Chain(Workload):
             dag, halo = (H.chain2d_expr_dag() if expr else H.chain2d_dag()), 2
         else:   # a periodic grid stored without halo (its halo would never be read)
             import numpy as np
-            u = I.chain3d_input(n, seed=seed, dtype=np.float32 if dtype == "f32" else np.float64, halo=0)
-            dag, halo = H.chain3d_dag(), 0
+            halo = CHAIN3D_HALO[0]
+            u = I.chain3d_input(n, seed=seed, dtype=np.float32 if dtype == "f32" else np.float64, halo=halo,
+                                fill_halo=0.0)
+            dag = H.chain3d_dag()
         self.u = torch.from_numpy(u).to(dev).to(td)
         self.out = torch.empty_like(self.u)
         self.dag = dag
         self.hdt = H.HFAV_F64 if dtype == "f64" else H.HFAV_F32
         self.grids = [H.Grid.of(self.u, halo)]
-        self.plan = H.Plan(dag, self.grids, self.hdt, H.HFAV_BC_PERIODIC, "full:smem:32x8" if expr else "full:reg:32x4")
+        self.bc = H.HFAV_BC_HALO_GIVEN if (dims == 3 and CHAIN3D_HALO[1]) else H.HFAV_BC_PERIODIC
+        self.plan = H.Plan(dag, self.grids, self.hdt, self.bc, "full:smem:32x8" if expr else "full:reg:32x4")
         self.esize = 8 if dtype == "f64" else 4
 
     def unfused_plan(self, H):
-        return H.Plan(self.dag, self.grids, self.hdt, H.HFAV_BC_PERIODIC, "unfused")
+        return H.Plan(self.dag, self.grids, self.hdt, self.bc, "unfused")
 
     def run(self, plan):
         plan.run([self.u], [self.out], 1)
@@ -863,7 +871,10 @@ def main():
     ap.add_argument("--schedule", default=None, help="fixed schedule (default: autotuned among fused ones)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--once", action="store_true", help="profiling case: build the plan and run it once")
+    ap.add_argument("--chain3d-halo", type=int, default=0, help="array halo of the 3D chain workloads (layout)")
+    ap.add_argument("--chain3d-halo-given", action="store_true", help="3D chain: read the (zero) halo as given")
     args = ap.parse_args()
+    CHAIN3D_HALO[0], CHAIN3D_HALO[1] = args.chain3d_halo, args.chain3d_halo_given
     if args.impl == "reference":
         if args.workload == "all":
             args.workload = "godunov1024_f64"
