@@ -1183,11 +1183,18 @@ __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a, const __
         __syncthreads();
         // the slot of plane it + ND held plane it - 2, last read at it - 1
         fetch(it + G::ND);
+        // the planes this iteration reads and writes: distinct ring slots, so
+        // the stages' shared loads may move ahead of earlier stages' stores
+        const T* __restrict__ Ub = U + (it % G::NB) * PUS;
+        const T* __restrict__ Up = U + ((it + G::NB - 1) % G::NB) * PUS;
+        T* __restrict__ S1b = S1 + c0 * G::P1;
+        const T* __restrict__ S1n = S1 + c2 * G::P1;
+        const T* __restrict__ S1p = S1 + c1 * G::P1;
+        T* __restrict__ S2b = S2 + c0 * G::P2;
+        const T* __restrict__ S2n = S2 + c2 * G::P2;
+        const T* __restrict__ S2p = S2 + c1 * G::P2;
         // s1 at plane kk-1: window u(kk-2 .. kk), in-plane neighbours from u(kk-1)
         if (it < nu) {
-            const T* Ub = U + (it % G::NB) * PUS;
-            const T* Up = U + ((it + G::NB - 1) % G::NB) * PUS;
-            T* S1b = S1 + c0 * G::P1;
             const bool comp = it >= 2;
 #pragma unroll
             for (int r = 0; r < G::N1; ++r) {
@@ -1209,9 +1216,6 @@ __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a, const __
         // it-1) and kk-3 (in-plane, made at it-2); s1 exists from plane
         // k0-2 (it = 3) to k0+K+1 (it = K+6)
         if (it >= 3 && it < nu + 1) {
-            const T* S1n = S1 + c2 * G::P1;
-            const T* S1p = S1 + c1 * G::P1;
-            T* S2b = S2 + c0 * G::P2;
             const bool comp = it >= 5;
 #pragma unroll
             for (int r = 0; r < G::N2; ++r) {
@@ -1232,8 +1236,6 @@ __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a, const __
         // out at plane kk-5 from the s2 planes kk-4 (window push, made at
         // it-1) and kk-5 (in-plane, made at it-2); s2 exists from plane k0-1 (it = 6)
         if (it >= 6) {
-            const T* S2n = S2 + c2 * G::P2;
-            const T* S2p = S2 + c1 * G::P2;
             const bool store = it >= 8 && k0 - 8 + it < a.nz;
 #pragma unroll
             for (int r = 0; r < G::NO; ++r) {
@@ -1398,11 +1400,18 @@ __global__ void __launch_bounds__(TX * TY) chain3d_quad(const C3Args a, const __
         }
         __syncthreads();
         fetch(it + 2, IC<sm>{});
+        // the planes this iteration reads and writes: distinct ring slots, so
+        // the stages' shared loads may move ahead of earlier stages' stores
+        const float* __restrict__ Ub = U + (it % G::NB) * PUS;
+        const float* __restrict__ Up = U + ((it + G::NB - 1) % G::NB) * PUS;
+        float* __restrict__ S1b = S1 + s * G::P1;
+        const float* __restrict__ S1n = S1 + sm * G::P1;
+        const float* __restrict__ S1p = S1 + sp * G::P1;
+        float* __restrict__ S2b = S2 + s * G::P2;
+        const float* __restrict__ S2n = S2 + sm * G::P2;
+        const float* __restrict__ S2p = S2 + sp * G::P2;
         // s1 at plane kk-1 (window slot s holds plane kk, sm kk-1, sp kk-2)
         if (it < nu) {
-            const float* Ub = U + (it % G::NB) * PUS;
-            const float* Up = U + ((it + G::NB - 1) % G::NB) * PUS;
-            float* S1b = S1 + s * G::P1;
             const bool comp = it >= 2;
 #pragma unroll
             for (int r = 0; r < Q::N1; ++r) {
@@ -1425,9 +1434,6 @@ __global__ void __launch_bounds__(TX * TY) chain3d_quad(const C3Args a, const __
         // s2 at plane kk-3 from the s1 planes made at it-1 (ring slot sm)
         // and it-2 (slot sp)
         if (it >= 3 && it < nu + 1) {
-            const float* S1n = S1 + sm * G::P1;
-            const float* S1p = S1 + sp * G::P1;
-            float* S2b = S2 + s * G::P2;
             const bool comp = it >= 5;
 #pragma unroll
             for (int r = 0; r < Q::N2; ++r) {
@@ -1449,8 +1455,6 @@ __global__ void __launch_bounds__(TX * TY) chain3d_quad(const C3Args a, const __
         }
         // out at plane kk-5 from the s2 planes made at it-1 (slot sm) and it-2 (slot sp)
         if (it >= 6) {
-            const float* S2n = S2 + sm * G::P2;
-            const float* S2p = S2 + sp * G::P2;
             const bool store = it >= 8 && k0 - 8 + it < a.nz;
 #pragma unroll
             for (int r = 0; r < Q::NO; ++r) {
