@@ -1126,7 +1126,7 @@ __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a, const __
         if constexpr (LOAD == 0) {
             if (it < nu) {
                 const int kk = k0 - 3 + it;
-                const int kw = a.u.wrap ? wrap_idx(kk, a.nz) : min(max(kk, -3), a.nz + 2);
+                const int kw = a.u.wrap ? wrap1(kk, a.nz) : min(max(kk, -3), a.nz + 2);
                 const T* ub = u + (int64_t)(kw + a.u.org[2]) * a.u.pitch[2];
                 T* Ub = U + (it % G::NB) * PUS;
 #pragma unroll
@@ -1137,7 +1137,7 @@ __global__ void __launch_bounds__(TX * TY) chain3d_regw(const C3Args a, const __
         } else {
             if (it >= nu) return;
             const int kk = k0 - 3 + it;
-            const int kw = a.u.wrap ? wrap_idx(kk, a.nz) : min(max(kk, -3), a.nz + 2);
+            const int kw = a.u.wrap ? wrap1(kk, a.nz) : min(max(kk, -3), a.nz + 2);
             if (tid == 0) {
                 T* Ub = U + (it % G::NB) * PUS;
                 unsigned long long* bar = bars + it % G::NB;
@@ -1286,6 +1286,14 @@ struct C3Quad {
     static constexpr int Q1 = G::P1 / 4, Q2 = G::P2 / 4, QO = TX * G::TYO / 4;
     static constexpr int N1 = (Q1 + NT - 1) / NT, N2 = (Q2 + NT - 1) / NT, NO = (QO + NT - 1) / NT;
     static_assert(W % 4 == 0 && TX % 4 == 0, "quads tile the plane rows");
+    // u planes are copied ND planes ahead into a ring of ND + 2 slots (one
+    // plane deeper than the pair kernels: 2-3% at 512^3); the patch
+    // registers hold the ND - 1 pending planes and the current one
+    static constexpr int ND = 3, NB = ND + 2;
+    static_assert(ND >= 2 && ND <= 3, "three patch register slots");
+    static constexpr size_t smem() {
+        return (size_t)(NB * G::pua(sizeof(float)) + 3 * G::P1 + 3 * G::P2) * sizeof(float) + NB * 8 + 128;
+    }
 };
 
 template <int V>
@@ -1300,7 +1308,7 @@ __global__ void __launch_bounds__(TX * TY) chain3d_quad(const C3Args a, const __
     unsigned char* sbase = smem_raw + ((128u - (smem_u32(smem_raw) & 127u)) & 127u);
     constexpr int PUS = G::pua(sizeof(float));
     float* U = (float*)sbase;        // [NB][PUS] ring of u planes
-    float* S1 = U + G::NB * PUS;     // [3][P1] ring of s1 planes
+    float* S1 = U + Q::NB * PUS;     // [3][P1] ring of s1 planes
     float* S2 = S1 + 3 * G::P1;      // [3][P2] ring of s2 planes
     unsigned long long* bars = (unsigned long long*)(S2 + 3 * G::P2);
     const int tid = threadIdx.y * TX + threadIdx.x;
@@ -1335,7 +1343,7 @@ __global__ void __launch_bounds__(TX * TY) chain3d_quad(const C3Args a, const __
         }
     }
     if (tid == 0) {
-        for (int b = 0; b < G::NB; ++b) mbar_init(bars + b, 1);
+        for (int b = 0; b < Q::NB; ++b) mbar_init(bars + b, 1);
         mbar_init_fence();
     }
     __syncthreads();
@@ -1371,12 +1379,12 @@ __global__ void __launch_bounds__(TX * TY) chain3d_quad(const C3Args a, const __
         constexpr int d = decltype(D)::value;
         if (it >= nu) return;
         const int kk = k0 - 3 + it;
-        const int kw = a.u.wrap ? wrap_idx(kk, a.nz) : min(max(kk, -3), a.nz + 2);
+        const int kw = a.u.wrap ? wrap1(kk, a.nz) : min(max(kk, -3), a.nz + 2);
         if (tid == 0) {
-            unsigned long long* bar = bars + it % G::NB;
+            unsigned long long* bar = bars + it % Q::NB;
             fence_proxy_async_smem();
             mbar_arrive_expect_tx(bar, (unsigned)(G::PU * sizeof(float)));
-            tma_load_3d(U + (it % G::NB) * PUS, &tmap, i0 - 4 + a.u.org[0], j0 - 3 + a.u.org[1], kw + a.u.org[2],
+            tma_load_3d(U + (it % Q::NB) * PUS, &tmap, i0 - 4 + a.u.org[0], j0 - 3 + a.u.org[1], kw + a.u.org[2],
                         bar);
         }
         if (patch) {
@@ -1390,20 +1398,20 @@ __global__ void __launch_bounds__(TX * TY) chain3d_quad(const C3Args a, const __
     auto step = [&](auto Sc, int it) {
         constexpr int s = decltype(Sc)::value, sp = (s + 1) % 3, sm = (s + 2) % 3;
         if (it < nu) {
-            if (!mbar_wait_bounded(bars + it % G::NB, (unsigned)(it / G::NB) & 1u, a.err)) timed_out = true;
+            if (!mbar_wait_bounded(bars + it % Q::NB, (unsigned)(it / Q::NB) & 1u, a.err)) timed_out = true;
             if (patch) {
-                float* Ub = U + (it % G::NB) * PUS;
+                float* Ub = U + (it % Q::NB) * PUS;
 #pragma unroll
                 for (int f = 0; f < G::NF; ++f)
                     if (pso[f] >= 0) Ub[pso[f]] = pv[s][f];
             }
         }
         __syncthreads();
-        fetch(it + 2, IC<sm>{});
+        fetch(it + Q::ND, IC<(s + Q::ND) % 3>{});
         // the planes this iteration reads and writes: distinct ring slots, so
         // the stages' shared loads may move ahead of earlier stages' stores
-        const float* __restrict__ Ub = U + (it % G::NB) * PUS;
-        const float* __restrict__ Up = U + ((it + G::NB - 1) % G::NB) * PUS;
+        const float* __restrict__ Ub = U + (it % Q::NB) * PUS;
+        const float* __restrict__ Up = U + ((it + Q::NB - 1) % Q::NB) * PUS;
         float* __restrict__ S1b = S1 + s * G::P1;
         const float* __restrict__ S1n = S1 + sm * G::P1;
         const float* __restrict__ S1p = S1 + sp * G::P1;
@@ -1477,14 +1485,15 @@ __global__ void __launch_bounds__(TX * TY) chain3d_quad(const C3Args a, const __
     };
     fetch(0, IC<0>{});
     fetch(1, IC<1>{});
+    if constexpr (Q::ND == 3) fetch(2, IC<2>{});
     for (int it = 0; it < nit; it += 3) {
         step(IC<0>{}, it);
         if (it + 1 < nit) step(IC<1>{}, it + 1);
         if (it + 2 < nit) step(IC<2>{}, it + 2);
     }
     if (timed_out)
-        for (int it = max(0, nu - G::NB); it < nu; ++it)
-            mbar_wait_bounded(bars + it % G::NB, (unsigned)(it / G::NB) & 1u, nullptr);
+        for (int it = max(0, nu - Q::NB); it < nu; ++it)
+            mbar_wait_bounded(bars + it % Q::NB, (unsigned)(it / Q::NB) & 1u, nullptr);
 }
 
 namespace {
@@ -1546,7 +1555,7 @@ static int launch_c3regw_load(hfav_plan_t* p, C3Args& a, const CUtensorMap& map,
 template <int TX, int TY>
 static int launch_c3quad(hfav_plan_t* p, C3Args& a, const CUtensorMap& map, cudaStream_t st) {
     using G = C3Tile<TX, TY>;
-    const size_t sm = G::smem_tma(sizeof(float));
+    const size_t sm = C3Quad<TX, TY>::smem();
     cudaFuncSetAttribute(chain3d_quad<TX, TY>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     static int occ = 0;
     if (!occ) {
@@ -1744,7 +1753,7 @@ double chain_warps_t(const hfav_plan_t* p, const Schedule& s) {
 #define C3W(a, b)                                                                                             \
     if (TX == a && TY == b) {                                                                                 \
         using G = C3Tile<a, b>;                                                                               \
-        if constexpr (sizeof(T) == 4 && a == 32) return warps_of(chain3d_quad<a, b>, NT, G::smem_tma(es));   \
+        if constexpr (sizeof(T) == 4 && a == 32) return warps_of(chain3d_quad<a, b>, NT, C3Quad<a, b>::smem());   \
         return warps_of(chain3d_regw<T, a, b, 1>, NT, G::smem_tma(es));                                       \
     }
         C3W(32, 4) C3W(64, 4) C3W(128, 2) C3W(32, 8)
