@@ -109,9 +109,9 @@ TRAFFIC = {
     ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_y"): (2446.9e6, "55662954019f9d94"),
     ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_x"): (5154.9e6, "55662954019f9d94"),
     ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_y"): (2437.7e6, "55662954019f9d94"),
-    ("chain2d_fp32_16384x16384", "full:reg", "chain2d_fused"): (2128.6e6, "a8995591b606f249"),
-    ("chain3d_fp32_512x512x512", "full:reg", "chain3d_fused_tma"): (1058.7e6, "a8995591b606f249"),
-    ("cosmo_fp32_1024x1024x64", "full:reg", "cosmo_fused"): (527.7e6, "a8995591b606f249"),
+    ("chain2d_fp32_16384x16384", "full:reg", "chain2d_fused"): (2128.8e6, "ea75d8cb3b84e2e3"),
+    ("chain3d_fp32_512x512x512", "full:reg", "chain3d_fused_tma"): (1058.8e6, "ea75d8cb3b84e2e3"),
+    ("cosmo_fp32_1024x1024x64", "full:reg", "cosmo_fused"): (527.6e6, "ea75d8cb3b84e2e3"),
     ("codegen_chain2d_fp32_16384x16384", "full:smem", "codegen_fused"): (2172.5e6, "8317c02f6926f6f7"),
     # two generated nests per step, each one array in and one out: the mean of the two launches
     ("normalization2d_fp32_16384x16384", "full:smem", "codegen_fused"): (2102.9e6, "8317c02f6926f6f7"),
