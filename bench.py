@@ -93,22 +93,22 @@ COSMO_NZ = 64            # planes of the COSMO workloads
 # ncu capture of the bench's profiling case (summaries under profiles/), with
 # the hash of the kernel sources at capture time: a changed source voids it.
 TRAFFIC = {
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg", "gsweep_y"): (33.65e6, "55662954019f9d94"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg", "gsweep_x"): (33.70e6, "55662954019f9d94"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:smem", "gsweep_y"): (33.61e6, "55662954019f9d94"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:smem", "gsweep_x"): (33.77e6, "55662954019f9d94"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:hbm", "gsweep_y"): (34.50e6, "55662954019f9d94"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:hbm", "gsweep_x"): (94.03e6, "55662954019f9d94"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:reg", "gsweep_x"): (494.5e6, "55662954019f9d94"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:reg", "gsweep_y"): (498.1e6, "55662954019f9d94"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:smem", "gsweep_x"): (491.3e6, "55662954019f9d94"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:smem", "gsweep_y"): (496.0e6, "55662954019f9d94"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:hbm", "gsweep_x"): (558.6e6, "55662954019f9d94"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:hbm", "gsweep_y"): (500.6e6, "55662954019f9d94"),
-    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_x"): (2387.8e6, "55662954019f9d94"),
-    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_y"): (2446.9e6, "55662954019f9d94"),
-    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_x"): (5154.9e6, "55662954019f9d94"),
-    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_y"): (2437.7e6, "55662954019f9d94"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg", "gsweep_y"): (33.61e6, "a4a67d465b85d1b9"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg", "gsweep_x"): (33.68e6, "a4a67d465b85d1b9"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:smem", "gsweep_y"): (33.65e6, "a4a67d465b85d1b9"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:smem", "gsweep_x"): (33.77e6, "a4a67d465b85d1b9"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:hbm", "gsweep_y"): (34.40e6, "a4a67d465b85d1b9"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:hbm", "gsweep_x"): (94.19e6, "a4a67d465b85d1b9"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:reg", "gsweep_x"): (494.74e6, "a4a67d465b85d1b9"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:reg", "gsweep_y"): (496.47e6, "a4a67d465b85d1b9"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:smem", "gsweep_x"): (489.89e6, "a4a67d465b85d1b9"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:smem", "gsweep_y"): (495.74e6, "a4a67d465b85d1b9"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:hbm", "gsweep_x"): (557.48e6, "a4a67d465b85d1b9"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:hbm", "gsweep_y"): (500.26e6, "a4a67d465b85d1b9"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_x"): (2386.63e6, "a4a67d465b85d1b9"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_y"): (2445.02e6, "a4a67d465b85d1b9"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_x"): (5461.68e6, "a4a67d465b85d1b9"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_y"): (2440.27e6, "a4a67d465b85d1b9"),
     ("chain2d_fp32_16384x16384", "full:reg", "chain2d_fused"): (2128.8e6, "ea75d8cb3b84e2e3"),
     ("chain3d_fp32_512x512x512", "full:reg", "chain3d_fused_tma"): (1058.8e6, "ea75d8cb3b84e2e3"),
     ("cosmo_fp32_1024x1024x64", "full:reg", "cosmo_fused"): (527.6e6, "ea75d8cb3b84e2e3"),
@@ -132,22 +132,22 @@ def src_hash(files):
 # one ncu capture (profiles/godunov_fp64_1024_pipe_ncu.md), with the hash of
 # the kernel sources at capture time: a changed source voids it.
 FP64_SLOTS = {
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg", "gsweep_x"): (295.65e6, "55662954019f9d94"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg", "gsweep_y"): (333.76e6, "55662954019f9d94"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:smem", "gsweep_x"): (330.80e6, "55662954019f9d94"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:smem", "gsweep_y"): (400.02e6, "55662954019f9d94"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:hbm", "gsweep_x"): (328.70e6, "55662954019f9d94"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:hbm", "gsweep_y"): (400.02e6, "55662954019f9d94"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:reg", "gsweep_x"): (1921.46e6, "55662954019f9d94"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:reg", "gsweep_y"): (1943.12e6, "55662954019f9d94"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:smem", "gsweep_x"): (1975.59e6, "55662954019f9d94"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:smem", "gsweep_y"): (1959.93e6, "55662954019f9d94"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:hbm", "gsweep_x"): (1975.63e6, "55662954019f9d94"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:hbm", "gsweep_y"): (1959.93e6, "55662954019f9d94"),
-    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_x"): (9086.2e6, "55662954019f9d94"),
-    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_y"): (9018.4e6, "55662954019f9d94"),
-    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_x"): (9153.8e6, "55662954019f9d94"),
-    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_y"): (9141.3e6, "55662954019f9d94"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg", "gsweep_x"): (295.65e6, "a4a67d465b85d1b9"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg", "gsweep_y"): (333.76e6, "a4a67d465b85d1b9"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:smem", "gsweep_x"): (330.80e6, "a4a67d465b85d1b9"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:smem", "gsweep_y"): (400.02e6, "a4a67d465b85d1b9"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:hbm", "gsweep_x"): (328.70e6, "a4a67d465b85d1b9"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:hbm", "gsweep_y"): (400.02e6, "a4a67d465b85d1b9"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:reg", "gsweep_x"): (1352.09e6, "a4a67d465b85d1b9"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:reg", "gsweep_y"): (1369.59e6, "a4a67d465b85d1b9"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:smem", "gsweep_x"): (1401.77e6, "a4a67d465b85d1b9"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:smem", "gsweep_y"): (1403.21e6, "a4a67d465b85d1b9"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:hbm", "gsweep_x"): (1401.85e6, "a4a67d465b85d1b9"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:hbm", "gsweep_y"): (1403.21e6, "a4a67d465b85d1b9"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_x"): (6532.57e6, "a4a67d465b85d1b9"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_y"): (6360.10e6, "a4a67d465b85d1b9"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_x"): (6598.83e6, "a4a67d465b85d1b9"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_y"): (6546.65e6, "a4a67d465b85d1b9"),
 }
 
 
