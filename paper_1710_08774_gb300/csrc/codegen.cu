@@ -1059,6 +1059,243 @@ void mark_inplace(const hfav_plan_t* p, Stream* S, void* const* ax, void* const*
         }
 }
 
+// ---- fused 2D, placement reg: warp strips ------------------------------------------
+// Each warp owns a strip of 32 V columns (V consecutive cells per lane) and a
+// chunk of R rows, and streams down the chunk.  Every field the part loads or
+// stores keeps a window of its last rows in registers (Sec. 3.5
+// "Contraction", with the rolling buffer in the register file), the
+// i-neighbours cross lanes by warp shuffle (offsets up to V cells), and the
+// strips overlap by the part's footprint in x, so no lane needs data from
+// beyond its strip: no shared memory and no barrier.  A field computed at
+// step t holds row t - Y0 - lead (its lead puts every row it reads at or
+// before its inputs' current rows, so one pass over the fields in
+// topological order per step suffices); loads arrive P rows ahead.  Windows
+// are powers of two and the step loop is unrolled by the largest, so every
+// window slot is a constant of the unrolled code.  Taken for one-part DAGs
+// without reductions whose reads reach at most V cells across; a run whose
+// goal shares its array with an input (declared in/out) takes the ring
+// kernel instead.
+struct WStrip {
+    int V = 1, NT = 0, HL = 0, TXw = 0, M = 1, P = 3, Y0 = 0, fill = 0;   // P: rows a load runs ahead (at least 3)
+    std::vector<int> lead, NW, order;   // per field; order: stored fields computed here, topological
+};
+
+int wstrip_geometry(const hfav_plan_t* p, const Schedule& s, const Part& P, const Stream& S, WStrip* G) {
+    const Dag& d = p->dag;
+    const int nf = d.n_fields;
+    if (S.pointwise || !S.reds.empty() || !S.crosses.empty() || !S.scalars.empty())
+        return set_error(HFAV_EUNSUPPORTED, "warp strips take one-part DAGs without reductions or scalars");
+    const int V = p->dtype == HFAV_F64 ? 2 : 4;
+    G->V = V;
+    G->NT = s.tx * s.ty;
+    int HL = 0, HR = 0;
+    for (int f = 0; f < nf; ++f)
+        if (!S.f[f].scalar && (S.f[f].rule >= 0 || S.f[f].load >= 0)) {
+            HL = std::max(HL, S.f[f].hxlo);
+            HR = std::max(HR, S.f[f].hxhi);
+        }
+    G->HL = (HL + V - 1) / V * V;
+    G->TXw = (32 * V - G->HL - HR) / V * V;
+    if (G->TXw < 16 * V) return set_error(HFAV_EUNSUPPORTED, "this DAG's footprint is too wide for warp strips");
+    G->lead.assign(nf, 0);
+    G->NW.assign(nf, 0);
+    G->order.clear();
+    for (int r : p->an.order) {
+        if (!in_part(P, r)) continue;
+        const int f = d.rules[r].out[0];
+        if (S.f[f].inl) continue;
+        int lead = -(1 << 20);
+        for (auto& e : S.f[f].eff) {
+            if (e[1] > V || e[1] < -V) return set_error(HFAV_EUNSUPPORTED, "warp strips take reads within V cells in x");
+            lead = std::max(lead, G->lead[e[0]] + e[2]);
+        }
+        if (S.f[f].eff.empty()) lead = 0;
+        G->lead[f] = lead;
+        G->order.push_back(f);
+    }
+    // window rows: from the newest row of a field to the oldest a reader takes
+    size_t regs = 0;
+    G->M = 1;
+    G->Y0 = 0;
+    for (int f : S.loads) G->Y0 = std::max(G->Y0, S.f[f].hylo);
+    int fill = 0;
+    std::vector<int> span(nf, 1);
+    int P_max = 1 << 20;
+    for (int f = 0; f < nf; ++f) {
+        const SField& F = S.f[f];
+        if (F.scalar || (F.rule < 0 && F.load < 0) || F.inl) continue;
+        int w = 1;
+        for (int c : G->order)
+            for (auto& e : S.f[c].eff)
+                if (e[0] == f) w = std::max(w, G->lead[c] - G->lead[f] - e[2] + 1);
+        span[f] = w;
+        if (F.load >= 0) w += G->P;
+        int w2 = 1;
+        while (w2 < w) w2 *= 2;
+        G->NW[f] = w2;
+        if (F.load >= 0) P_max = std::min(P_max, w2 - span[f]);
+        G->M = std::max(G->M, w2);
+        regs += (size_t)w2 * V * (p->dtype == HFAV_F64 ? 2 : 1);
+        fill = std::max(fill, F.hyhi + G->lead[f]);
+    }
+    // loads run as far ahead as their (power-of-two) windows leave room for
+    if (!S.loads.empty()) G->P = P_max;
+    if (regs > 160) return set_error(HFAV_EUNSUPPORTED, "this DAG's row windows exceed the register budget of warp strips");
+    G->fill = G->Y0 + fill;
+    return HFAV_OK;
+}
+
+// positive remainder of a (possibly negative) row index
+int pmod(int a, int n) { return ((a % n) + n) % n; }
+
+std::string wstrip_source(const hfav_plan_t* p, const Stream& S, const Part& P, const WStrip& G, const std::string& name) {
+    const Dag& d = p->dag;
+    const bool f64 = p->dtype == HFAV_F64;
+    const int V = G.V, M = G.M;
+    const std::string VT = f64 ? "double2" : (V == 4 ? "float4" : "float2");
+    const int VB = V * (f64 ? 8 : 4);   // bytes of a lane's cells in one row
+    const char* comp[4] = {"x", "y", "z", "w"};
+    // window slot sl of field f: one vector of a lane's V cells of one row,
+    // so a load lands in it with no copy and a goal row leaves from it
+    auto wv = [](int f, int slot) { return "w" + std::to_string(f) + "_" + std::to_string(slot); };
+    auto we = [&](int f, int slot, int e) { return wv(f, slot) + "." + comp[e]; };
+    std::ostringstream c;
+    c << prelude(f64);
+    for (int r : p->an.order)
+        if (in_part(P, r)) c << rule_fn(d.rules[r], "hfav_body" + std::to_string(r));
+    c << "extern \"C\" __global__ void __launch_bounds__(" << G.NT << ") " << name << "(";
+    for (size_t a = 0; a < S.loads.size(); ++a) c << array_params("x" + std::to_string(a), false) << ", ";
+    for (size_t a = 0; a < S.goals.size(); ++a) c << array_params("y" + std::to_string(a), true) << ", ";
+    c << "int nx, int ny, int R, int nstrips, int sh) {\n"
+      << "    const int lane = threadIdx.x & 31;\n"
+      << "    const long long wid = ((long long)blockIdx.x * " << G.NT << " + threadIdx.x) >> 5;\n"
+      << "    const int strip = (int)(wid % nstrips), j0 = (int)(wid / nstrips) * R;\n"
+      << "    if (j0 >= ny) return;   // the whole warp\n"
+      << "    const int Rr = min(R, ny - j0), nstep = Rr + " << G.fill << ";\n"
+      << "    const int s0 = strip * " << G.TXw << " - " << G.HL << " - sh, c0 = s0 + " << V << " * lane;\n"
+      << "    const int lo = max(s0 + " << G.HL << ", 0), hi = min(s0 + " << G.HL + G.TXw << ", nx);\n";
+    // loads: fixed columns per lane (wrapped or clamped into the footprint);
+    // a warp whose lanes' cells all lie contiguous and 16-byte aligned in
+    // every load takes the vector loop
+    std::string vall = "true";
+    for (int f : S.loads) {
+        const SField& F = S.f[f];
+        const std::string a = std::to_string(F.load), x = "x" + a;
+        for (int e = 0; e < V; ++e)
+            c << "    int cx" << a << "_" << e << " = c0 + " << e << ";\n"
+              << "    cx" << a << "_" << e << " = " << x << "_w ? hfav_wrap(cx" << a << "_" << e << ", nx) : min(max(cx" << a
+              << "_" << e << ", -" << F.hxlo << "), nx - 1 + " << F.hxhi << ");\n";
+        c << "    const bool vx" << a << " = c0 >= 0 && c0 + " << V << " <= nx && ((" << x << "_o0 + c0) & " << V - 1
+          << ") == 0 && (" << x << "_p1 & " << V - 1 << ") == 0 && ((unsigned long long)" << x << " & " << VB - 1
+          << ") == 0;\n";
+        vall += " && vx" + a;
+    }
+    for (size_t q = 0; q < S.goals.size(); ++q) {
+        const std::string y = "y" + std::to_string(q);
+        c << "    const bool vy" << q << " = c0 >= lo && c0 + " << V << " <= hi && ((" << y << "_o0 + c0) & " << V - 1
+          << ") == 0 && (" << y << "_p1 & " << V - 1 << ") == 0 && ((unsigned long long)" << y << " & " << VB - 1
+          << ") == 0;\n";
+    }
+    for (int f = 0; f < d.n_fields; ++f)
+        for (int sl = 0; sl < G.NW[f]; ++sl) c << "    " << VT << " " << wv(f, sl) << " = {};\n";
+    // a load of row `row` (an expression; rows past the footprint are
+    // wrapped or clamped like any other, so every load is unconditional)
+    auto emit_load = [&](std::ostringstream& o, int f, const std::string& row, int sl, bool vec, const std::string& ind) {
+        const SField& F = S.f[f];
+        const std::string a = std::to_string(F.load), x = "x" + a;
+        o << ind << "{\n"
+          << ind << "    int gj = j0 + " << row << ";\n"
+          << ind << "    gj = " << x << "_w ? hfav_wrap(gj, ny) : min(max(gj, -" << F.hylo << "), ny - 1 + " << F.hyhi
+          << ");\n"
+          << ind << "    const T* rp = " << x << " + (long long)(gj + " << x << "_o1) * " << x << "_p1 + " << x << "_o0;\n";
+        if (vec) o << ind << "    " << wv(f, sl) << " = *(const " << VT << "*)(rp + c0);\n";
+        else
+            for (int e = 0; e < V; ++e) o << ind << "    " << we(f, sl, e) << " = rp[cx" << a << "_" << e << "];\n";
+        o << ind << "}\n";
+    };
+    auto emit_main = [&](std::ostringstream& o, bool vec) {
+        for (int f : S.loads)
+            for (int q = 0; q < G.P; ++q) emit_load(o, f, std::to_string(q - G.Y0), pmod(q - G.Y0, G.NW[f]), vec, "        ");
+        o << "        #pragma unroll 1\n"
+          << "        for (int t0 = 0; t0 < nstep; t0 += " << M << ") {\n";
+        for (int k = 0; k < M; ++k) {
+            o << "        if (t0 + " << k << " < nstep) {   // step t0 + " << k << "\n"
+              << "            const int t = t0 + " << k << ";\n";
+            for (int f : S.loads)
+                emit_load(o, f, "t + " + std::to_string(G.P - G.Y0), pmod(k + G.P - G.Y0, G.NW[f]), vec, "            ");
+            for (int f : G.order) {
+                const SField& F = S.f[f];
+                const Rule& R = d.rules[F.rule];
+                const int lf = G.lead[f];
+                // the value of field g, shifted by (dx, dy), at cell e of this
+                // lane; each shuffle is declared once per step
+                std::set<std::string> shuf;
+                std::ostringstream sh;
+                std::function<std::string(int, int, int, int)> read = [&](int g, int e, int dx, int dy) -> std::string {
+                    const SField& Gf = S.f[g];
+                    if (Gf.inl) {
+                        const Rule& Q = d.rules[Gf.rule];
+                        std::string val = "hfav_body" + std::to_string(Gf.rule) + "(";
+                        for (size_t q = 0; q < Q.in.size(); ++q)
+                            val += (q ? ", " : "") + read(Q.in[q].field, e, dx + Q.in[q].off[0], dy + Q.in[q].off[1]);
+                        return val + ")";
+                    }
+                    const int sl = pmod(k - G.Y0 - lf + dy, G.NW[g]);
+                    const int ee = e + dx;
+                    if (ee >= 0 && ee < V) return we(g, sl, ee);
+                    const bool left = ee < 0;
+                    const int src = left ? ee + V : ee - V;
+                    const std::string nm = std::string(left ? "sl" : "sr") + std::to_string(g) + "_" + std::to_string(sl) +
+                                           "_" + std::to_string(src);
+                    if (shuf.insert(nm).second)
+                        sh << "                const T " << nm << " = " << (left ? "__shfl_up_sync" : "__shfl_down_sync")
+                           << "(0xffffffffu, " << we(g, sl, src) << ", 1);\n";
+                    return nm;
+                };
+                std::ostringstream body;
+                const int sl_f = pmod(k - G.Y0 - lf, G.NW[f]);
+                for (int e = 0; e < V; ++e) {
+                    body << "                {\n";
+                    for (size_t q = 0; q < R.in.size(); ++q)
+                        body << "                    const T in" << q << " = "
+                             << read(R.in[q].field, e, R.in[q].off[0], R.in[q].off[1]) << ";\n";
+                    body << "                    " << we(f, sl_f, e) << " = "
+                         << rule_call(R, "hfav_body" + std::to_string(F.rule)) << ";\n"
+                         << "                }\n";
+                }
+                o << "            {\n"
+                  << "                const int row = t - " << G.Y0 + lf << ";\n"
+                  << "                if (row >= -" << F.hylo << " && row < Rr + " << F.hyhi << ") {\n"
+                  << sh.str() << body.str();
+                if (F.goal >= 0) {
+                    const std::string y = "y" + std::to_string(F.goal);
+                    o << "                if (row >= 0 && row < Rr) {\n"
+                      << "                    T* const yr = " << y << " + (long long)(j0 + row + " << y << "_o1) * " << y
+                      << "_p1 + " << y << "_o0;\n"
+                      << "                    if (vy" << F.goal << ") {\n"
+                      << "                        *(" << VT << "*)(yr + c0) = " << wv(f, sl_f) << ";\n"
+                      << "                    } else {\n";
+                    for (int e = 0; e < V; ++e)
+                        o << "                        if (c0 + " << e << " >= lo && c0 + " << e << " < hi) yr[c0 + " << e
+                          << "] = " << we(f, sl_f, e) << ";\n";
+                    o << "                    }\n"
+                      << "                }\n";
+                }
+                o << "                }\n"
+                  << "            }\n";
+            }
+            o << "        }\n";
+        }
+        o << "        }\n";
+    };
+    std::ostringstream mv, ms;
+    emit_main(mv, true);
+    emit_main(ms, false);
+    c << "    if (__all_sync(0xffffffffu, " << vall << ")) {\n" << mv.str() << "    } else {\n" << ms.str() << "    }\n"
+      << "}\n";
+    return c.str();
+}
+
 }  // namespace
 
 bool codegen_inplace(const hfav_plan_t* p, const Schedule& s) {
@@ -1066,6 +1303,18 @@ bool codegen_inplace(const hfav_plan_t* p, const Schedule& s) {
     Program G;
     if (make_program(p, true, &G)) return false;
     return G.parts.size() == 1;
+}
+
+bool codegen_wstrip_ok(const hfav_plan_t* p, const Schedule& s, std::string* why) {
+    Program G;
+    Stream S;
+    WStrip W;
+    int rc = make_program(p, true, &G);
+    if (!rc && G.parts.size() != 1) rc = set_error(HFAV_EUNSUPPORTED, "warp strips take one-part DAGs");
+    if (!rc) rc = stream_geometry(p, s, G.parts[0], &S);
+    if (!rc) rc = wstrip_geometry(p, s, G.parts[0], S, &W);
+    if (rc && why) *why = std::string("full:reg for generated kernels: ") + hfav_last_error();
+    return rc == HFAV_OK;
 }
 
 int plan_source(const hfav_plan_t* p, std::string* out) {
@@ -1079,6 +1328,12 @@ int plan_source(const hfav_plan_t* p, std::string* out) {
         for (size_t k = 0; k < G.parts.size(); ++k) {
             Stream S;
             if ((rc = stream_geometry(p, p->sched, G.parts[k], &S))) return rc;
+            if (p->sched.placement == PLACE_REG) {   // warp strips (a run whose goal aliases an input takes the ring kernel)
+                WStrip W;
+                if ((rc = wstrip_geometry(p, p->sched, G.parts[k], S, &W))) return rc;
+                o << "// ---- kernel " << k << "\n" << wstrip_source(p, S, G.parts[k], W, "hfav_cg_wstrip");
+                continue;
+            }
             if (inpl) mark_inplace(p, &S, nullptr, nullptr);   // the declared pairs, as an aliased run compiles them
             o << "// ---- kernel " << k << "\n" << stream_source(p, S, G.parts[k], "hfav_cg_part");
             if (!G.fin_reds[k].empty() || !G.fin_rules[k].empty())
@@ -1117,52 +1372,76 @@ int launch_cg_rule(hfav_plan_t* p, const Rule& R, const std::vector<int>& ref_sl
     return HFAV_OK;
 }
 
-int launch_codegen(hfav_plan_t* p, const Schedule& s, void* const* ax, void* const* go, cudaStream_t st) {
+// a part's prepared launch: its stream geometry, compiled kernels and launch shape
+struct CgLaunch {
+    Stream S;
+    cudaKernel_t kern = nullptr, fin = nullptr;
+    int CH = 0;
+    int64_t strips = 0, nblocks = 0;
+    bool ws = false;   // warp strips (placement reg)
+    WStrip W;
+    int sh = 0;        // warp strips: columns the strips start early
+};
+// everything of a run that depends only on the plan, the schedule, the
+// device and which declared in/out pairs alias: built on the first run of
+// that combination, kept with the plan
+struct CgPrepared {
+    Program G;
+    std::vector<CgLaunch> L;
+    size_t part_bytes = 0;
+};
+struct CgCache {
+    std::mutex mu;
+    std::map<std::string, std::shared_ptr<CgPrepared>> m;
+};
+
+static int cg_prepare(hfav_plan_t* p, const Schedule& s, void* const* ax, void* const* go, int dev, CgPrepared* X0) {
     const bool fused = s.fusion != FUSE_UNFUSED;
-    if (!fused && !has_scalars(p)) return launch_generic(p, ax, go, st);
     const Dag& d = p->dag;
     const hfav_grid& g = p->grids[0];
     const int nx = (int)g.extent[0], ny = (int)g.extent[1];
-    Program G;
+    const int sms = device_sms();
+    Program& G = X0->G;
     int rc = make_program(p, fused, &G);
     if (rc) return rc;
-    int dev = 0, sms = 0;
-    HFAV_CUDA(cudaGetDevice(&dev));
-    HFAV_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    // plan arrays: the fields that cross between parts, over their footprint;
-    // the scalars (FP64, by field id); the reductions' partials
-    const size_t es = p->dtype == HFAV_F64 ? 8 : 4;
-    std::vector<GArr> cross(d.n_fields);
-    for (size_t k = 0; k < G.parts.size(); ++k) {
-        Stream S;
-        if ((rc = stream_geometry(p, s, G.parts[k], &S))) return rc;
-        for (int f : S.crosses) {
-            const hfav_field_info& fi = p->an.field[f];
-            GArr a;
-            const int64_t e0 = nx + fi.halo_lo[0] + fi.halo_hi[0], e1 = ny + fi.halo_lo[1] + fi.halo_hi[1];
-            a.pitch[0] = 1; a.pitch[1] = e0; a.pitch[2] = e0 * e1;
-            a.org[0] = fi.halo_lo[0]; a.org[1] = fi.halo_lo[1]; a.org[2] = 0;
-            a.ext[0] = nx; a.ext[1] = ny; a.ext[2] = 1;
-            a.wrap = 0;
-            void* ptr;
-            if ((rc = scratch(p, "codegen_f" + std::to_string(f), (size_t)(e0 * e1) * es, &ptr))) return rc;
-            a.p = ptr;
-            cross[f] = a;
-        }
-    }
-    void* scal;
-    if ((rc = scratch(p, "codegen_scalars", sizeof(double) * d.n_fields, &scal))) return rc;
-    // every part's kernel, launch shape and partials first, so the partials
-    // buffer is sized once for the largest part
-    struct Launch { Stream S; cudaKernel_t kern, fin = nullptr; int CH; int64_t strips, nblocks; };
-    std::vector<Launch> L(G.parts.size());
+    std::vector<CgLaunch>& L = X0->L;
+    L.assign(G.parts.size(), CgLaunch());
     size_t part_bytes = 0;
     const bool inpl = fused && G.parts.size() == 1;
     for (size_t k = 0; k < G.parts.size(); ++k) {
-        Launch& X = L[k];
+        CgLaunch& X = L[k];
         if ((rc = stream_geometry(p, s, G.parts[k], &X.S))) return rc;
         if (inpl && !X.S.pointwise) mark_inplace(p, &X.S, ax, go);
         const Stream& S = X.S;
+        // placement reg: warp strips, unless this run's goal shares its array
+        // with an input (the ring kernel saves the bands that run needs)
+        if (s.placement == PLACE_REG && std::find(S.inplace.begin(), S.inplace.end(), 1) == S.inplace.end()) {
+            if ((rc = wstrip_geometry(p, s, G.parts[k], S, &X.W))) return rc;
+            X.ws = true;
+            if ((rc = compile(wstrip_source(p, S, G.parts[k], X.W, "hfav_cg_wstrip"), "hfav_cg_wstrip", &X.kern)))
+                return rc;
+            int per_sm = 0;
+            HFAV_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)X.kern, X.W.NT, 0));
+            const int64_t resident = (int64_t)std::max(1, sms) * std::max(1, per_sm) * (X.W.NT / 32);   // warps
+            // strips start sh columns early, so that a lane's cells of the
+            // first load sit on vector boundaries (the vector path)
+            X.sh = 0;
+            if (!S.loads.empty()) {
+                const auto ai = std::find(d.axioms.begin(), d.axioms.end(), S.loads[0]);
+                X.sh = pmod(caller_view_cg(p, ax[ai - d.axioms.begin()]).org[0] - X.W.HL, X.W.V);
+            }
+            X.strips = (nx + X.sh + X.W.TXw - 1) / X.W.TXw;
+            X.CH = ny;
+            double best = 1e300;
+            for (int64_t chunks = 1; chunks <= ny; chunks = chunks < 8 ? chunks + 1 : chunks * 5 / 4) {
+                const int ch = (int)((ny + chunks - 1) / chunks);
+                const int64_t warps = X.strips * ((ny + ch - 1) / ch);
+                const double cost = (double)(ch + X.W.fill) * (double)((warps + resident - 1) / resident);
+                if (cost < best) { best = cost; X.CH = ch; }
+            }
+            X.nblocks = (X.strips * ((ny + X.CH - 1) / X.CH) * 32 + X.W.NT - 1) / X.W.NT;
+            continue;
+        }
         if ((rc = compile(stream_source(p, S, G.parts[k], "hfav_cg_part"), "hfav_cg_part", &X.kern))) return rc;
         // a library kernel takes its attributes per device
         if (S.smem > kSmemDefault)
@@ -1188,11 +1467,88 @@ int launch_codegen(hfav_plan_t* p, const Schedule& s, void* const* ax, void* con
         X.nblocks = X.strips * ((ny + X.CH - 1) / X.CH);
         part_bytes = std::max(part_bytes, sizeof(double) * S.reds.size() * (size_t)X.nblocks);
     }
+    X0->part_bytes = part_bytes;
+    return HFAV_OK;
+}
+
+int launch_codegen(hfav_plan_t* p, const Schedule& s, void* const* ax, void* const* go, cudaStream_t st) {
+    const bool fused = s.fusion != FUSE_UNFUSED;
+    if (!fused && !has_scalars(p)) return launch_generic(p, ax, go, st);
+    const Dag& d = p->dag;
+    const hfav_grid& g = p->grids[0];
+    const int nx = (int)g.extent[0], ny = (int)g.extent[1];
+    int rc = HFAV_OK;
+    int dev = 0;
+    HFAV_CUDA(cudaGetDevice(&dev));
+    // the prepared kernels of this schedule, device and aliasing pattern
+    std::string key = std::to_string(dev) + "/" + std::to_string(s.fusion) + "/" + std::to_string(s.placement) + "/" +
+                      std::to_string(s.tx) + "x" + std::to_string(s.ty) + "/";
+    for (size_t k = 0; k < d.goals.size(); ++k) {
+        const int a = k < d.inout.size() ? d.inout[k] : -1;
+        key += (a >= 0 && go[k] == ax[a]) ? '1' : '0';
+    }
+    if (!p->cg_cache) p->cg_cache = std::make_shared<CgCache>();
+    CgCache* C = (CgCache*)p->cg_cache.get();
+    std::shared_ptr<CgPrepared> prep;
+    {
+        std::lock_guard<std::mutex> lock(C->mu);
+        auto it = C->m.find(key);
+        if (it != C->m.end()) prep = it->second;
+    }
+    if (!prep) {
+        auto fresh = std::make_shared<CgPrepared>();
+        if ((rc = cg_prepare(p, s, ax, go, dev, fresh.get()))) return rc;
+        std::lock_guard<std::mutex> lock(C->mu);
+        prep = C->m.emplace(key, fresh).first->second;
+    }
+    const Program& G = prep->G;
+    const std::vector<CgLaunch>& L = prep->L;
+    // plan arrays: the fields that cross between parts, over their footprint;
+    // the scalars (FP64, by field id); the reductions' partials
+    const size_t es = p->dtype == HFAV_F64 ? 8 : 4;
+    std::vector<GArr> cross(d.n_fields);
+    for (size_t k = 0; k < G.parts.size(); ++k)
+        for (int f : L[k].S.crosses) {
+            const hfav_field_info& fi = p->an.field[f];
+            GArr a;
+            const int64_t e0 = nx + fi.halo_lo[0] + fi.halo_hi[0], e1 = ny + fi.halo_lo[1] + fi.halo_hi[1];
+            a.pitch[0] = 1; a.pitch[1] = e0; a.pitch[2] = e0 * e1;
+            a.org[0] = fi.halo_lo[0]; a.org[1] = fi.halo_lo[1]; a.org[2] = 0;
+            a.ext[0] = nx; a.ext[1] = ny; a.ext[2] = 1;
+            a.wrap = 0;
+            void* ptr;
+            if ((rc = scratch(p, "codegen_f" + std::to_string(f), (size_t)(e0 * e1) * es, &ptr))) return rc;
+            a.p = ptr;
+            cross[f] = a;
+        }
+    void* scal;
+    if ((rc = scratch(p, "codegen_scalars", sizeof(double) * d.n_fields, &scal))) return rc;
     void* part = nullptr;
-    if (part_bytes && (rc = scratch(p, "codegen_partials", part_bytes, &part))) return rc;
+    if (prep->part_bytes && (rc = scratch(p, "codegen_partials", prep->part_bytes, &part))) return rc;
     for (size_t k = 0; k < G.parts.size(); ++k) {
-        const Launch& X = L[k];
+        const CgLaunch& X = L[k];
         const Stream& S = X.S;
+        if (X.ws) {
+            ArgPack A;
+            for (int f : S.loads) {
+                const auto ai = std::find(d.axioms.begin(), d.axioms.end(), f);
+                add_array(A, caller_view_cg(p, ax[ai - d.axioms.begin()]));
+            }
+            for (size_t q = 0; q < S.goals.size(); ++q) {
+                GArr y = caller_view_cg(p, go[S.goal_slot[q]]);
+                y.wrap = 0;
+                add_array(A, y);
+            }
+            A.add(nx);
+            A.add(ny);
+            A.add(X.CH);
+            A.add((int)X.strips);
+            A.add(X.sh);
+            auto args = A.ptrs();
+            HFAV_CUDA(cudaLaunchKernel((const void*)X.kern, dim3((unsigned)X.nblocks), dim3(X.W.NT), args.data(), 0, st));
+            HFAV_LAUNCHED(p->rt, "codegen_fused", st);
+            continue;
+        }
         ArgPack A;
         for (int f : S.loads) {
             const auto ai = std::find(d.axioms.begin(), d.axioms.end(), f);

@@ -4,6 +4,7 @@
 #include <array>
 #include <cstdint>
 #include <string>
+#include <memory>
 #include <vector>
 
 #include "../../include/hfav.h"
@@ -90,6 +91,7 @@ struct hfav_plan_s {
     hfav::Schedule sched;
     bool tune_first_run = false;   // schedule "tuned": autotune on the first run's arrays
     hfav::Runtime* rt = nullptr;
+    std::shared_ptr<void> cg_cache;   // generated kernels prepared per schedule (codegen.cu)
 };
 
 namespace hfav {
@@ -109,6 +111,8 @@ int set_error(int code, const std::string& msg);
 // a schedule updates declared in/out pairs in place (no full snapshot)
 int plan_source(const hfav_plan_t* p, std::string* out);
 bool codegen_inplace(const hfav_plan_t* p, const Schedule& s);
+// the generated warp-strip kernel (full:reg) applies to the plan's DAG and tile
+bool codegen_wstrip_ok(const hfav_plan_t* p, const Schedule& s, std::string* why);
 
 // runtime.cu
 int run(hfav_plan_t* p, void* const* ax, void* const* go, int n_steps, void* stream, bool graph);

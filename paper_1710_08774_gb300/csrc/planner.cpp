@@ -919,10 +919,14 @@ bool schedule_valid(const hfav_plan_t* p, const Schedule& s, std::string* why) {
         if (why) *why = "unfused implies hbm intermediates";
         return false;
     }
-    if (p->pipeline == PIPE_CODEGEN && s.fusion != FUSE_UNFUSED &&
-        (s.fusion != FUSE_FULL || s.placement != PLACE_SMEM || p->dag.ndim != 2)) {
-        if (why) *why = "generated kernels run fully fused with shared-memory tiles (full:smem, 2D DAGs) or unfused";
-        return false;
+    if (p->pipeline == PIPE_CODEGEN && s.fusion != FUSE_UNFUSED) {
+        if (s.fusion != FUSE_FULL || s.placement == PLACE_HBM || p->dag.ndim != 2) {
+            if (why)
+                *why = "generated kernels run fully fused on 2D DAGs -- shared-memory rings (full:smem) or warp strips "
+                       "(full:reg) -- or unfused";
+            return false;
+        }
+        if (s.placement == PLACE_REG && !codegen_wstrip_ok(p, s, why)) return false;
     }
     if (p->pipeline == PIPE_COSMO && s.fusion != FUSE_UNFUSED && (s.fusion != FUSE_FULL || s.placement != PLACE_REG)) {
         if (why) *why = "the COSMO pipeline runs fully fused with register windows (full:reg) or unfused";

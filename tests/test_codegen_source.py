@@ -48,10 +48,12 @@ def test_expr_dag_plans_onto_generated_kernels():
     P = H.Plan(X.to_spec(rules, axioms, goals, 2), [_grid((40, 30), 6)])
     assert P.dump()["pipeline"] == "codegen"
     assert P.schedule == "full:smem:32x8"          # the default in 2D
-    assert set(P.variants()) == {f"{f}:{t}" for f in ("full:smem", "unfused:hbm")
+    assert set(P.variants()) == {f"{f}:{t}" for f in ("full:smem", "full:reg", "unfused:hbm")
                                  for t in ("32x4", "64x4", "128x2", "32x8")}
     with pytest.raises(H.HfavError):
-        P.schedule = "full:reg:32x4"
+        P.schedule = "full:hbm:32x4"
+    with pytest.raises(H.HfavError):
+        P.schedule = "sweep:smem:32x4"
     rules3, ax3, go3 = X.random_dag(3, 3, 1)
     P3 = H.Plan(X.to_spec(rules3, ax3, go3, 3), [_grid((12, 10, 8), 4)])
     assert P3.schedule.startswith("unfused")      # 3D: one generated kernel per rule
@@ -96,7 +98,9 @@ def test_generated_source_compiles_with_nvrtc(dtype, seed):
     L = _nvrtc()
     rules, axioms, goals = X.random_dag(2, 6, seed)
     P = H.Plan(X.to_spec(rules, axioms, goals, 2), [_grid((50, 40), 8)], dtype)
-    for sched in ("full:smem:32x4", "full:smem:128x2", "unfused:hbm:32x4"):
+    for sched in ("full:smem:32x4", "full:smem:128x2", "full:reg:32x4", "unfused:hbm:32x4"):
+        if sched not in P.variants():
+            continue   # warp strips take one-part DAGs only
         P.schedule = sched
         src = P.source()
         for body in {r["c"] for r in rules}:
@@ -254,3 +258,19 @@ def test_generated_units_run_in_dependency_order(seed, schedule):
             for f in re.findall(r"\(T\)scal\[(\d+)\]", body):
                 assert int(f) in known, (k, f)
     assert len(known) == sum(1 for r in rules if r["out"].startswith(("acc", "sc")))
+
+
+def test_warp_strip_source_keeps_windows_in_registers():
+    """The warp-strip form of the 2D chain written as rule bodies: no shared
+    memory, no barrier, i-neighbours by shuffle, 16-byte loads and stores on
+    the aligned path; it compiles in both precisions."""
+    L = _nvrtc()
+    for dt in (H.HFAV_F32, H.HFAV_F64):
+        P = H.Plan(H.chain2d_expr_dag(), [_grid((256, 256), 2)], dt, H.HFAV_BC_PERIODIC, "full:reg:32x4")
+        src = P.source()
+        assert "hfav_cg_wstrip" in src and "__shared__" not in src and "__syncthreads" not in src
+        assert "__shfl_up_sync" in src and "__shfl_down_sync" in src
+        assert ("float4" if dt == H.HFAV_F32 else "double2") in src
+        for u in _units(src):
+            rc, log = _compile(L, u)
+            assert rc == 0, log

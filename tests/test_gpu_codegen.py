@@ -28,7 +28,7 @@ from tests.test_gpu_chain import _block_wrap, _sample_points
 
 pytestmark = pytest.mark.gpu
 
-SCHEDULES = [f"{f}:{t}" for f in ("full:smem", "unfused:hbm") for t in ("32x4", "64x4", "128x2", "32x8")]
+SCHEDULES = [f"{f}:{t}" for f in ("full:smem", "full:reg", "unfused:hbm") for t in ("32x4", "64x4", "128x2", "32x8")]
 
 
 def run_plan(spec, axioms, halo, schedule, dtype=np.float64, bc=H.HFAV_BC_PERIODIC, graph=False, n_goals=1):
@@ -52,8 +52,9 @@ def test_chain_as_rule_bodies_f64(schedule):
     assert normwise(got, oracle.chain2d(u)[2]) <= 1e-12
 
 
-@pytest.mark.parametrize("shape", [(13, 7), (100, 37), (130, 67), (2, 2), (257, 3)])
-@pytest.mark.parametrize("schedule", ["full:smem:32x4", "full:smem:128x2", "unfused:hbm:32x4"])
+@pytest.mark.parametrize("shape", [(13, 7), (100, 37), (130, 67), (2, 2), (257, 3), (1000, 9)])
+@pytest.mark.parametrize("schedule", ["full:smem:32x4", "full:smem:128x2", "full:reg:32x4", "full:reg:128x2",
+                                      "unfused:hbm:32x4"])
 def test_chain_as_rule_bodies_ragged(shape, schedule):
     nx, ny = shape
     u = I.chain2d_input(nx, seed=3, ny=ny)
@@ -61,7 +62,7 @@ def test_chain_as_rule_bodies_ragged(shape, schedule):
     assert normwise(got, oracle.chain2d(u)[2]) <= 1e-12
 
 
-@pytest.mark.parametrize("schedule", ["full:smem:32x8", "unfused:hbm:32x4"])
+@pytest.mark.parametrize("schedule", ["full:smem:32x8", "full:reg:32x4", "unfused:hbm:32x4"])
 def test_chain_as_rule_bodies_f32(schedule):
     u = I.chain2d_input(300, seed=4, ny=200)
     (got,), _ = run_plan(H.chain2d_expr_dag(), [u], 2, schedule, np.float32)
@@ -104,6 +105,46 @@ def test_random_dags_2d_f32(seed, schedule):
         assert normwise(v, ref[g]) <= 2e-5, g
 
 
+@pytest.mark.parametrize("seed", range(12))
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_random_dags_2d_warp_strips(seed, dtype):
+    """Generated warp-strip kernels (full:reg) on the random DAGs they take
+    (one fused part): against the oracle, and against the ring kernel to
+    rounding (a stage's value stays in a register here, so the compiler may
+    fuse its last product into a reader's sum: one rounding where the ring
+    kernel, which stores the stage, has two)."""
+    rules, axioms, goals, spec, core, padded, h = _random_case(2, seed + 80, (83, 57))
+    import torch
+    P = H.Plan(spec, [H.Grid.of(padded[0], h)])
+    regs = [v for v in P.variants() if v.startswith("full:reg")]
+    if not regs:
+        pytest.skip("a DAG of several fused parts: warp strips do not apply")
+    arrs = [p.astype(dtype) for p in padded]
+    got, _ = run_plan(spec, arrs, h, "full:reg:32x4", dtype, n_goals=len(goals))
+    ring, _ = run_plan(spec, arrs, h, "full:smem:32x4", dtype, n_goals=len(goals))
+    ref = E.evaluate(X.to_oracle(rules), {a: core[a].astype(dtype).astype(np.float64) for a in axioms})
+    for g, v, w in zip(goals, got, ring):
+        assert normwise(v, ref[g]) <= (1e-12 if dtype == np.float64 else 2e-5), g
+        assert normwise(v, w) <= (1e-13 if dtype == np.float64 else 1e-5), g
+
+
+def test_warp_strips_take_most_random_dags():
+    """Most random DAGs plan onto warp strips; the others (several fused
+    parts, or row windows beyond the register budget) are refused with a
+    reason."""
+    taken = 0
+    for seed in range(12):
+        rules, axioms, goals = X.random_dag(2, 6, seed + 80)
+        P = H.Plan(X.to_spec(rules, axioms, goals, 2), [H.Grid.of(np.zeros((60, 50)), 6)])
+        if any(v.startswith("full:reg") for v in P.variants()):
+            taken += 1
+        else:
+            with pytest.raises(H.HfavError) as e:
+                P.schedule = "full:reg:32x4"
+            assert "EUNSUPPORTED" in str(e.value) and ("one-part" in str(e.value) or "register" in str(e.value))
+    assert taken >= 6
+
+
 @pytest.mark.parametrize("seed", range(4))
 def test_random_dags_3d_unfused(seed):
     rules, axioms, goals, spec, core, padded, h = _random_case(3, seed + 40, (9, 14, 23), n_rules=4)
@@ -114,7 +155,7 @@ def test_random_dags_3d_unfused(seed):
 
 
 @pytest.mark.parametrize("seed", range(4))
-@pytest.mark.parametrize("schedule", ["full:smem:32x4", "unfused:hbm:64x4"])
+@pytest.mark.parametrize("schedule", ["full:smem:32x4", "full:reg:32x4", "unfused:hbm:64x4"])
 def test_random_dags_halo_given(seed, schedule):
     """The caller's halo is read as given: random halo values, the oracle on the
     padded arrays cropped (exact while the halo covers the footprint)."""
@@ -130,7 +171,7 @@ def test_random_dags_halo_given(seed, schedule):
         assert normwise(v, ref[g]) <= 1e-12, g
 
 
-@pytest.mark.parametrize("schedule", ["full:smem:32x4", "full:smem:128x2", "unfused:hbm:32x4"])
+@pytest.mark.parametrize("schedule", ["full:smem:32x4", "full:smem:128x2", "full:reg:32x4", "unfused:hbm:32x4"])
 @pytest.mark.parametrize("dtype", [np.float64, np.float32])
 def test_nested_pointwise_stages(schedule, dtype):
     """Stages read only at offset 0 are evaluated inside their readers (two
@@ -158,15 +199,16 @@ def test_rule_bodies_mixed_with_builtin_ops():
     D.rule("SQUASH", ["G"], ["out"])
     D.axiom("u"); D.goal("out")
     u = I.chain2d_input(77, seed=9, ny=41)
-    for sched in ("full:smem:32x4", "unfused:hbm:32x4"):
+    for sched in ("full:smem:32x4", "full:reg:32x4", "unfused:hbm:32x4"):
         (got,), _ = run_plan(D, [u], 2, sched)
         assert normwise(got, oracle.chain2d(u)[2]) <= 1e-12
 
 
-def test_graph_replay_matches():
+@pytest.mark.parametrize("schedule", ["full:smem:32x8", "full:reg:32x8"])
+def test_graph_replay_matches(schedule):
     rules, axioms, goals, spec, core, padded, h = _random_case(2, 3, (64, 40))
-    a, _ = run_plan(spec, padded, h, "full:smem:32x8", n_goals=len(goals))
-    b, _ = run_plan(spec, padded, h, "full:smem:32x8", graph=True, n_goals=len(goals))
+    a, _ = run_plan(spec, padded, h, schedule, n_goals=len(goals))
+    b, _ = run_plan(spec, padded, h, schedule, graph=True, n_goals=len(goals))
     for x, y in zip(a, b):
         assert np.array_equal(x, y)
 
@@ -187,7 +229,7 @@ def test_body_that_does_not_compile_fails_cleanly():
     assert np.all(np.isfinite(got))
 
 
-@pytest.mark.parametrize("schedule", ["full:smem:32x8", "full:smem:128x2"])
+@pytest.mark.parametrize("schedule", ["full:smem:32x8", "full:smem:128x2", "full:reg:32x4"])
 def test_chain_as_rule_bodies_16384_f32_full_size_sampled(schedule):
     """The bench's 16384^2 FP32 grid: sampled cells (tile borders among them)
     against the chain's oracle on each cell's periodic 5 x 5 neighbourhood."""

@@ -47,14 +47,20 @@ def _twice(spec, arrays, halo, schedule, dtype=np.float64, bc=H.HFAV_BC_PERIODIC
     return [r[crop].cpu().numpy() for r in ref], [o[crop].cpu().numpy() for o in outs], P2
 
 
-@pytest.mark.parametrize("schedule", ["full:smem:32x4", "full:smem:128x2", "full:smem:32x8", "unfused:hbm:32x4"])
+@pytest.mark.parametrize("schedule", ["full:smem:32x4", "full:smem:128x2", "full:smem:32x8", "full:reg:32x4",
+                                      "unfused:hbm:32x4"])
 @pytest.mark.parametrize("shape", [(1500, 700), (515, 1031), (37, 5)])
 def test_chain_as_rule_bodies_in_place(schedule, shape):
     D = H.chain2d_expr_dag()
     D.inout("out", "u")
     u = I.chain2d_input(shape[0], seed=1, ny=shape[1])
     ref, got, P = _twice(D, [u], 2, schedule)
-    assert np.array_equal(ref, got)
+    if schedule.startswith("full:reg"):
+        # the aliased run takes the ring kernel, the other the warp strips:
+        # equal to rounding (the warp strips may fuse across stages)
+        assert normwise(ref, got) <= 1e-13
+    else:
+        assert np.array_equal(ref, got)
     assert normwise(got, oracle.chain2d(u)[2]) <= 1e-12
     if schedule.startswith("full"):   # the two band kernels and the update, no snapshot copy
         assert P.status()["last_launches"] == 3
