@@ -249,6 +249,11 @@ typedef struct hfav_plan_s hfav_plan_t;
  *               runs the fastest variant), or an explicit variant
  *               "<fusion>[:<placement>][:<TX>x<TY>]" with fusion in
  *               {full, sweep, unfused}, placement in {reg, smem, hbm}.
+ *               Generated kernels (DAGs with rule bodies or reductions) in
+ *               2D take full:smem (rows in shared-memory rings), full:reg
+ *               (warp strips, rows in registers: one fused part without
+ *               reductions, reads within 4 cells (FP32) / 2 (FP64) in x;
+ *               otherwise EUNSUPPORTED with the reason) or unfused.
  *               When schedule is NULL or "auto" and the environment variable
  *               HFAV_SCHEDULE is set, its value ("auto", "tuned" or a variant)
  *               is used instead.
