@@ -1208,9 +1208,20 @@ std::string wstrip_source(const hfav_plan_t* p, const Stream& S, const Part& P, 
           << ind << "    gj = " << x << "_w ? hfav_wrap(gj, ny) : min(max(gj, -" << F.hylo << "), ny - 1 + " << F.hyhi
           << ");\n"
           << ind << "    const T* rp = " << x << " + (long long)(gj + " << x << "_o1) * " << x << "_p1 + " << x << "_o0;\n";
-        if (vec) o << ind << "    " << wv(f, sl) << " = *(const " << VT << "*)(rp + c0);\n";
-        else
-            for (int e = 0; e < V; ++e) o << ind << "    " << we(f, sl, e) << " = rp[cx" << a << "_" << e << "];\n";
+        // the loads are volatile asm, so the compiler keeps them where they
+        // are issued (rows ahead of their readers) instead of sinking them
+        // into the later step that reads them
+        if (vec) {
+            o << ind << "    asm volatile(\"ld.global.nc.v" << V << "." << (f64 ? "f64" : "f32") << " {";
+            for (int e = 0; e < V; ++e) o << (e ? ", " : "") << "%" << e;
+            o << "}, [%" << V << "];\" : ";
+            for (int e = 0; e < V; ++e) o << (e ? ", " : "") << "\"=" << (f64 ? "d" : "f") << "\"(" << we(f, sl, e) << ")";
+            o << " : \"l\"(rp + c0));\n";
+        } else {
+            for (int e = 0; e < V; ++e)
+                o << ind << "    asm volatile(\"ld.global.nc." << (f64 ? "f64" : "f32") << " %0, [%1];\" : \"="
+                  << (f64 ? "d" : "f") << "\"(" << we(f, sl, e) << ") : \"l\"(rp + cx" << a << "_" << e << "));\n";
+        }
         o << ind << "}\n";
     };
     auto emit_main = [&](std::ostringstream& o, bool vec) {
