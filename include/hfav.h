@@ -425,6 +425,22 @@ int hfav_selftest_arith(const double* x, int64_t n, double* rcp_out, double* quo
  * CUDA's rsqrt. */
 int hfav_selftest_rsqrt(const double* x, int64_t n, double* out, void* stream);
 
+/* Diagnostic: the halving of the Godunov kernels' FP64 arithmetic, done on the
+ * integer pipe (exponent field lowered by one; zeros unchanged; results that
+ * would be subnormal, infinities and NaNs through the FP64 multiply).  For n
+ * doubles x (device): out[k] = x[k] / 2 (device array).  Tests hold it bit for
+ * bit to the IEEE product x * 0.5 (NaNs: NaN). */
+int hfav_selftest_half(const double* x, int64_t n, double* out, void* stream);
+
+/* Diagnostic: the FP64 <-> FP32 conversions of the FP32-bulk Riemann solver,
+ * done on the integer pipe (exponent rebiased, significand shifted; the
+ * narrowing rounds to nearest even; zeros, subnormals, infinities and NaNs
+ * through the conversion instructions).  For n doubles x and n floats f
+ * (device): narrow_out[k] = (float)x[k], widen_out[k] = (double)f[k] (device
+ * arrays).  Tests hold both bit for bit to the IEEE conversions. */
+int hfav_selftest_convert(const double* x, const float* f, int64_t n, float* narrow_out, double* widen_out,
+                          void* stream);
+
 /* Diagnostic: measured arithmetic peaks of the current device, the
  * denominators of the ALU rooflines.  Writes rates[0] = FP64 fused
  * multiply-adds per second (one per thread per instruction, the FP64 pipe's

@@ -129,7 +129,7 @@ __device__ __forceinline__ Face4<T> shfl_face(const Face4<T>& q, int src) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(256) gsweep_xw(const GGrid<T>* __restrict__ grids, const int2* __restrict__ items,
+__global__ void __launch_bounds__(256, 2) gsweep_xw(const GGrid<T>* __restrict__ grids, const int2* __restrict__ items,
                                                  int n_items, const GCommon C) {
     // one CTA per row; its A warps split the row into A arcs of equal length
     // (rows with nx % (32 A) != 0 use one arc).  Arc w streams the faces of
@@ -398,7 +398,7 @@ __device__ __forceinline__ bool ystep(YWin<T>& w, const Face4<T>& U2, int r, int
 }
 
 template <typename T, int PL>
-__global__ void __launch_bounds__(256) gsweep_y(const GGrid<T>* __restrict__ grids, const int2* __restrict__ items,
+__global__ void __launch_bounds__(256, PL == PLACE_REG ? 2 : 1) gsweep_y(const GGrid<T>* __restrict__ grids, const int2* __restrict__ items,
                                                 int n_items, const GCommon C) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const int TX = blockDim.x, t = threadIdx.x, ty = threadIdx.y, TY = blockDim.y;
@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(256) gsweep_y(const GGrid<T>* __restrict__ gri
                     if (emit && j < G.ny) {
                         st_dst(G, 0, i, j, o.r); st_dst(G, 2, i, j, o.u);
                         st_dst(G, 1, i, j, o.v); st_dst(G, 3, i, j, o.p);
-                        smax = fmax(smax, wave_speed(o.r, o.v, o.u, o.p, g, &bad));
+                        smax = speed_max(smax, wave_speed(o.r, o.v, o.u, o.p, g, &bad));
                     }
                 }
             }
@@ -566,7 +566,7 @@ __global__ void __launch_bounds__(256) gfull(const GGrid<T>* __restrict__ grids,
                     const int i = i0 + t;
                     st_dst(G, 0, i, j, o.r); st_dst(G, 2, i, j, o.u);
                     st_dst(G, 1, i, j, o.v); st_dst(G, 3, i, j, o.p);
-                    smax = fmax(smax, wave_speed(o.r, o.v, o.u, o.p, g, &bad));
+                    smax = speed_max(smax, wave_speed(o.r, o.v, o.u, o.p, g, &bad));
                 }
             }
         }
@@ -594,7 +594,7 @@ __global__ void __launch_bounds__(256) gcfl_reduce(const GGrid<T>* __restrict__ 
         T u[4];
         for (int f = 0; f < 4; ++f)
             u[f] = use_dst ? G.dst[f][(int64_t)(j + G.dhalo) * G.dpitch + i + G.dhalo] : ldg_src(G, f, i, j);
-        smax = fmax(smax, wave_speed(u[0], u[1], u[2], u[3], (T)gamma, &bad));
+        smax = speed_max(smax, wave_speed(u[0], u[1], u[2], u[3], (T)gamma, &bad));
     }
     smax = warp_max(smax);
     const unsigned any_bad = __ballot_sync(0xffffffffu, bad);
@@ -648,7 +648,7 @@ __global__ void u_constoprim(UArrays<T> A, int dir) {
         T ir = (T)1 / r;
         T un = A.U[mn][x] * ir, ut = A.U[mt][x] * ir;
         A.r[x] = r; A.un[x] = un; A.ut[x] = ut;
-        A.e[x] = fma(A.U[3][x], ir, (T)-0.5 * fma(un, un, ut * ut));
+        A.e[x] = fma(A.U[3][x], ir, -dhalf(fma(un, un, ut * ut)));
     }
 }
 
@@ -1116,7 +1116,41 @@ __global__ void selftest_rsqrt_k(const double* __restrict__ x, int64_t n, double
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
         r[k] = newton_rsqrt<float>(x[k]);
 }
+__global__ void selftest_half_k(const double* __restrict__ x, int64_t n, double* __restrict__ r) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+        r[k] = dhalf(x[k]);
+}
+__global__ void selftest_convert_k(const double* __restrict__ x, const float* __restrict__ f, int64_t n,
+                                   float* __restrict__ nr, double* __restrict__ wd) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        nr[k] = narrow(x[k]);
+        wd[k] = widen(f[k]);
+    }
+}
 }  // namespace hfav
+
+extern "C" int hfav_selftest_convert(const double* x, const float* f, int64_t n, float* narrow_out, double* widen_out,
+                                     void* stream) {
+    using namespace hfav;
+    if (!x || !f || !narrow_out || !widen_out || n < 0) return set_error(HFAV_EINVAL, "bad argument");
+    if (n == 0) return HFAV_OK;
+    int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    selftest_convert_k<<<blocks, 256, 0, (cudaStream_t)stream>>>(x, f, n, narrow_out, widen_out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(HFAV_ECUDA, cudaGetErrorString(e));
+    return HFAV_OK;
+}
+
+extern "C" int hfav_selftest_half(const double* x, int64_t n, double* out, void* stream) {
+    using namespace hfav;
+    if (!x || !out || n < 0) return set_error(HFAV_EINVAL, "bad argument");
+    if (n == 0) return HFAV_OK;
+    int blocks = (int)std::min<int64_t>((n + 255) / 256, 4096);
+    selftest_half_k<<<blocks, 256, 0, (cudaStream_t)stream>>>(x, n, out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(HFAV_ECUDA, cudaGetErrorString(e));
+    return HFAV_OK;
+}
 
 extern "C" int hfav_selftest_rsqrt(const double* x, int64_t n, double* out, void* stream) {
     using namespace hfav;

@@ -67,6 +67,68 @@ __device__ __forceinline__ bool dposfin(double x) {
 __device__ __forceinline__ bool dposfin(float x) { return x > 0.f && x <= 3.402823466e38f; }
 __device__ __forceinline__ bool dneg(float x) { return x < 0.f; }
 
+// x / 2, bit for bit the IEEE product x * 0.5, mostly on the integer pipe:
+// when x * 0.5 is normal it is x with its exponent field lowered by one (one
+// integer subtraction on the high word), zeros pass unchanged, and only the
+// rare rest (results that would be subnormal, infinities, NaNs) takes the
+// FP64 multiply, out of line.  Every halving of the Godunov arithmetic takes
+// this form in FP64, off the FP64 pipe that bounds it.
+__device__ __noinline__ double dhalf_rare(double x) { return x * 0.5; }
+__device__ __forceinline__ double dhalf(double x) {
+    const int hi = __double2hiint(x), lo = __double2loint(x);
+    const unsigned e = ((unsigned)hi >> 20) & 0x7ffu;
+    if (e - 2u < 2045u) return __hiloint2double(hi - (1 << 20), lo);   // 2 <= e <= 2046
+    if (((hi & 0x7fffffff) | lo) == 0) return x;                         // +-0
+    return dhalf_rare(x);
+}
+__device__ __forceinline__ float dhalf(float x) { return 0.5f * x; }
+
+// FP32 -> FP64 widening on the integer pipe, bit for bit the conversion:
+// a normal float keeps its sign, its exponent rebiased (+896) and its
+// significand shifted into place; zeros keep their sign; subnormals,
+// infinities and NaNs take the conversion instruction, out of line.
+__device__ __noinline__ double widen_rare(float x) { return (double)x; }
+__device__ __forceinline__ double widen(float x) {
+    const unsigned b = __float_as_uint(x);
+    const unsigned e = (b >> 23) & 0xffu;
+    if (e - 1u < 254u)
+        return __hiloint2double((int)((b & 0x80000000u) | ((e + 896u) << 20) | ((b & 0x7fffffu) >> 3)), (int)(b << 29));
+    if ((b & 0x7fffffffu) == 0) return __hiloint2double((int)(b & 0x80000000u), 0);
+    return widen_rare(x);
+}
+__device__ __forceinline__ double widen(double x) { return x; }
+// FP64 -> FP32 narrowing on the integer pipe, bit for bit the conversion
+// (round to nearest even): a double whose float is normal keeps its sign,
+// its exponent rebiased (-896) and its significand's top 23 bits rounded on
+// the 29 dropped (a carry into the exponent, up to infinity, is the
+// conversion's own); the rest (zeros, float subnormals and underflow,
+// infinities, NaNs) takes the conversion instruction, out of line.
+__device__ __noinline__ float narrow_rare(double x) { return (float)x; }
+__device__ __forceinline__ float narrow(double x) {
+    const unsigned hi = (unsigned)__double2hiint(x), lo = (unsigned)__double2loint(x);
+    const unsigned e = (hi >> 20) & 0x7ffu;
+    if (e - 897u < 254u) {   // 897 <= e <= 1150: float exponent 1 .. 254
+        unsigned m = ((hi & 0xfffffu) << 3) | (lo >> 29);
+        const unsigned rem = lo & 0x1fffffffu;
+        m += (rem > 0x10000000u) | ((rem == 0x10000000u) & (m & 1u));
+        return __uint_as_float((hi & 0x80000000u) | (((e - 896u) << 23) + m));
+    }
+    return narrow_rare(x);
+}
+// the bulk precision's value of an FP64 intermediate
+template <typename T>
+__device__ __forceinline__ T to_bulk(double x) {
+    if constexpr (sizeof(T) == 4) return narrow(x);
+    else return x;
+}
+// max of a running wave speed and a new one, both non-negative doubles, as
+// integers (their order is that of their bits); a NaN speed is passed over,
+// as fmax does
+__device__ __forceinline__ double speed_max(double a, double b) {
+    const long long ia = __double_as_longlong(a), ib = __double_as_longlong(b);
+    return (ib > ia && ib <= 0x7ff0000000000000LL) ? b : a;
+}
+
 
 // Primitive state of a cell in the frame of a sweep: rho, u_normal,
 // u_transverse, p, sound speed c, 1/c and c/rho.
@@ -84,7 +146,7 @@ __device__ __forceinline__ Prim<T> cons_to_prim(T U0, T Un, T Ut, T E, T g) {
     w.r = r;
     w.un = Un * ir;
     w.ut = Ut * ir;
-    T e = fma(E, ir, (T)-0.5 * fma(w.un, w.un, w.ut * w.ut));
+    T e = fma(E, ir, -dhalf(fma(w.un, w.un, w.ut * w.ut)));
     T p = (g - (T)1) * r * e;
     p = dfloor(p, (T)G_P_FLOOR);
     w.p = p;
@@ -114,16 +176,16 @@ __device__ __forceinline__ void trace(const Prim<T>& w0, T dr, T du, T dv, T dp,
                                       Face4<T>& qp) {
     const T ic = w0.ic, c = w0.c, r = w0.r, u = w0.un;
     const T dpc = dp * ic;
-    const T a1 = (T)0.5 * ic * fma(-r, du, dpc);
+    const T a1 = dhalf(ic) * fma(-r, du, dpc);
     const T a2 = fma(-dpc, ic, dr);
     const T a3 = dv;
-    const T a4 = (T)0.5 * ic * fma(r, du, dpc);
+    const T a4 = dhalf(ic) * fma(r, du, dpc);
     const T n1 = (u - c) * dtdx, n2 = u * dtdx, n4 = (u + c) * dtdx;
     // b+ = (1 - nu) a / 2, b- = (1 + nu) a / 2
-    const T p1 = (T)0.5 * (a1 - n1 * a1), m1 = (T)0.5 * fma(n1, a1, a1);
-    const T p2 = (T)0.5 * (a2 - n2 * a2), m2 = (T)0.5 * fma(n2, a2, a2);
-    const T p3 = (T)0.5 * (a3 - n2 * a3), m3 = (T)0.5 * fma(n2, a3, a3);
-    const T p4 = (T)0.5 * (a4 - n4 * a4), m4 = (T)0.5 * fma(n4, a4, a4);
+    const T p1 = dhalf(a1 - n1 * a1), m1 = dhalf(fma(n1, a1, a1));
+    const T p2 = dhalf(a2 - n2 * a2), m2 = dhalf(fma(n2, a2, a2));
+    const T p3 = dhalf(a3 - n2 * a3), m3 = dhalf(fma(n2, a3, a3));
+    const T p4 = dhalf(a4 - n4 * a4), m4 = dhalf(fma(n4, a4, a4));
     const T c2 = c * c;
     qp.r = w0.r + ((p1 + p2) + p4);
     qp.u = fma(w0.cr, p4 - p1, u);
@@ -158,7 +220,7 @@ __device__ __forceinline__ double newton_rsqrt(double x) {
         double y;
         asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
         const double e = fma(-x * y, y, 1.0);   // 1 - x y^2
-        return fma(0.5 * y, e, y);
+        return fma(dhalf(y), e, y);
     }
 }
 
@@ -167,9 +229,9 @@ __device__ __forceinline__ double newton_rsqrt(double x) {
 template <typename T>
 __device__ __forceinline__ Face4<T> riemann(const Face4<T>& L, const Face4<T>& R, T g, double ashk, int nmax,
                                              int* nonconv) {
-    const double gd = (double)g;
-    const double pl = (double)L.p, pr = (double)R.p, rl = (double)L.r, rr = (double)R.r;
-    const double ul = (double)L.u, ur = (double)R.u;
+    const double gd = widen(g);
+    const double pl = widen(L.p), pr = widen(R.p), rl = widen(L.r), rr = widen(R.r);
+    const double ul = widen(L.u), ur = widen(R.u);
     const double xl = gd * pl * rl, xr = gd * pr * rr;
     const double sl = newton_rsqrt<T>(xl), sr = newton_rsqrt<T>(xr);   // 1 / C_k
     const double cl = xl * sl, cr = xr * sr;               // C_k = sqrt(g p_k rho_k)
@@ -193,8 +255,8 @@ __device__ __forceinline__ Face4<T> riemann(const Face4<T>& L, const Face4<T>& R
         const double ql = newton_rsqrt<T>(fma(al, ps - pl, 1.0));
         const double qr = newton_rsqrt<T>(fma(ar, ps - pr, 1.0));
         const double iwl = ql * sl, iwr = qr * sr;         // 1 / W_k
-        const double izl = 0.5 * iwl * fma(cl * cl, iwl * iwl, 1.0);   // 1 / Z_k
-        const double izr = 0.5 * iwr * fma(cr * cr, iwr * iwr, 1.0);
+        const double izl = dhalf(iwl) * fma(cl * cl, iwl * iwl, 1.0);   // 1 / Z_k
+        const double izr = dhalf(iwr) * fma(cr * cr, iwr * iwr, 1.0);
         const double usl = fma(-(ps - pl), iwl, ul);
         const double usr = fma(ps - pr, iwr, ur);
         // the Newton correction itself needs no last-bit accuracy: one
@@ -211,12 +273,12 @@ __device__ __forceinline__ Face4<T> riemann(const Face4<T>& L, const Face4<T>& R
     }
     if (!conv) *nonconv = 1;
     // star state at the converged p*, in the bulk precision
-    const T pst = (T)ps;
-    const T tl = fma((T)al, pst - L.p, (T)1), tr = fma((T)ar, pst - R.p, (T)1);
+    const T pst = to_bulk<T>(ps);
+    const T tl = fma(to_bulk<T>(al), pst - L.p, (T)1), tr = fma(to_bulk<T>(ar), pst - R.p, (T)1);
     const T qlt = rsqrt(tl), qrt = rsqrt(tr);
-    const T Cl = (T)cl, Cr = (T)cr;
+    const T Cl = to_bulk<T>(cl), Cr = to_bulk<T>(cr);
     const T wl = Cl * tl * qlt, wr = Cr * tr * qrt;        // W_k = C_k sqrt(t_k)
-    const T iwl = qlt * (T)sl, iwr = qrt * (T)sr;
+    const T iwl = qlt * to_bulk<T>(sl), iwr = qrt * to_bulk<T>(sr);
     const T ust = div_nr(fma(wl, L.u, wr * R.u) + (L.p - R.p), wl + wr);
     const bool left = dpos(ust);
     const Face4<T>& S = left ? L : R;
@@ -269,7 +331,7 @@ __device__ __forceinline__ Face4<T> flux(const Face4<T>& q, T ig1) {
     F.r = m;
     F.u = fma(m, q.u, q.p);
     F.v = m * q.v;
-    const T et = fma(q.p, ig1, (T)0.5 * q.r * fma(q.u, q.u, q.v * q.v));
+    const T et = fma(q.p, ig1, dhalf(q.r) * fma(q.u, q.u, q.v * q.v));
     F.p = q.u * (et + q.p);
     return F;
 }
@@ -279,7 +341,7 @@ __device__ __forceinline__ Face4<T> flux(const Face4<T>& q, T ig1) {
 __device__ __forceinline__ double wave_speed(double U0, double U1, double U2, double U3, double g, int* bad) {
     const double ir = rcp_nr(U0);
     const double u = U1 * ir, v = U2 * ir;
-    const double e = fma(U3, ir, -0.5 * fma(u, u, v * v));
+    const double e = fma(U3, ir, -dhalf(fma(u, u, v * v)));
     double p = (g - 1.0) * U0 * e;
     if (!dposfin(U0) || !dposfin(p)) *bad = 1;   // also NaN and infinite states
     p = dfloor(p, G_P_FLOOR);
@@ -296,7 +358,7 @@ __device__ __forceinline__ double wave_speed(float U0, float U1, float U2, float
     if (!dposfin(U0) || !dposfin(p)) *bad = 1;
     p = fmaxf(p, (float)G_P_FLOOR);
     const float c = g * p * rsqrtf(g * p * U0);
-    return (double)(fmaxf(fabsf(u), fabsf(v)) + c);
+    return widen(fmaxf(fabsf(u), fabsf(v)) + c);
 }
 
 }  // namespace hfav

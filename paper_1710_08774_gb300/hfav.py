@@ -33,7 +33,7 @@ SYMBOLS = ["hfav_plan", "hfav_analyze", "hfav_plan_groups", "hfav_plan_field", "
            "hfav_run_graph", "hfav_status", "hfav_autotune", "hfav_plan_variants", "hfav_free", "hfav_last_error",
            "hfav_version", "hfav_mlp_n_params", "hfav_mlp_forward", "hfav_mlp_work_floats", "hfav_mlp_loss_grad",
            "hfav_mlp_adam", "hfav_mlp_train", "hfav_model_choose", "hfav_plan_timing", "hfav_kernel_times",
-           "hfav_chain2d_static", "hfav_selftest_arith", "hfav_selftest_rsqrt", "hfav_inject_alloc_failure",
+           "hfav_chain2d_static", "hfav_selftest_arith", "hfav_selftest_rsqrt", "hfav_selftest_half", "hfav_selftest_convert", "hfav_inject_alloc_failure",
            "hfav_probe_peaks"]
 
 
@@ -149,6 +149,8 @@ def load(path=None):
         "hfav_plan_timing": ([P, ctypes.c_int], ctypes.c_int),
         "hfav_selftest_arith": ([P, ctypes.c_int64, P, P, P], ctypes.c_int),
         "hfav_selftest_rsqrt": ([P, ctypes.c_int64, P, P], ctypes.c_int),
+        "hfav_selftest_half": ([P, ctypes.c_int64, P, P], ctypes.c_int),
+        "hfav_selftest_convert": ([P, P, ctypes.c_int64, P, P, P], ctypes.c_int),
         "hfav_chain2d_static": ([P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int,
                                  ctypes.POINTER(ctypes.c_double), P, P], ctypes.c_int),
         "hfav_kernel_times": ([P, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double), ip,
