@@ -93,29 +93,29 @@ COSMO_NZ = 64            # planes of the COSMO workloads
 # ncu capture of the bench's profiling case (summaries under profiles/), with
 # the hash of the kernel sources at capture time: a changed source voids it.
 TRAFFIC = {
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg", "gsweep_y"): (33.61e6, "a4a67d465b85d1b9"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg", "gsweep_x"): (33.68e6, "a4a67d465b85d1b9"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:smem", "gsweep_y"): (33.65e6, "a4a67d465b85d1b9"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:smem", "gsweep_x"): (33.77e6, "a4a67d465b85d1b9"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:hbm", "gsweep_y"): (34.40e6, "a4a67d465b85d1b9"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:hbm", "gsweep_x"): (94.19e6, "a4a67d465b85d1b9"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:reg", "gsweep_x"): (494.74e6, "a4a67d465b85d1b9"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:reg", "gsweep_y"): (496.47e6, "a4a67d465b85d1b9"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:smem", "gsweep_x"): (489.89e6, "a4a67d465b85d1b9"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:smem", "gsweep_y"): (495.74e6, "a4a67d465b85d1b9"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:hbm", "gsweep_x"): (557.48e6, "a4a67d465b85d1b9"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:hbm", "gsweep_y"): (500.26e6, "a4a67d465b85d1b9"),
-    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_x"): (2386.63e6, "a4a67d465b85d1b9"),
-    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_y"): (2445.02e6, "a4a67d465b85d1b9"),
-    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_x"): (5461.68e6, "a4a67d465b85d1b9"),
-    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_y"): (2440.27e6, "a4a67d465b85d1b9"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg", "gsweep_y"): (33.64e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg", "gsweep_x"): (33.71e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:smem", "gsweep_y"): (33.63e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:smem", "gsweep_x"): (33.77e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:hbm", "gsweep_y"): (34.59e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:hbm", "gsweep_x"): (95.28e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:reg", "gsweep_x"): (494.02e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:reg", "gsweep_y"): (495.85e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:smem", "gsweep_x"): (489.64e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:smem", "gsweep_y"): (495.88e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:hbm", "gsweep_x"): (555.51e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:hbm", "gsweep_y"): (499.63e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_x"): (2382.95e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_y"): (2446.19e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_x"): (5561.84e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_y"): (2408.09e6, "d44c8d6f2115ee9b"),
     ("chain2d_fp32_16384x16384", "full:reg", "chain2d_fused"): (2128.8e6, "ea75d8cb3b84e2e3"),
     ("chain3d_fp32_512x512x512", "full:reg", "chain3d_fused_tma"): (1058.8e6, "ea75d8cb3b84e2e3"),
     ("cosmo_fp32_1024x1024x64", "full:reg", "cosmo_fused"): (527.6e6, "ea75d8cb3b84e2e3"),
-    ("codegen_chain2d_fp32_16384x16384", "full:smem", "codegen_fused"): (2172.5e6, "8317c02f6926f6f7"),
+    ("codegen_chain2d_fp32_16384x16384", "full:smem", "codegen_fused"): (2172.6e6, "2a4a0934d71f84e5"),
     # two generated nests per step, each one array in and one out: the mean of the two launches
-    ("normalization2d_fp32_16384x16384", "full:smem", "codegen_fused"): (2102.9e6, "8317c02f6926f6f7"),
-    ("inplace_chain2d_fp32_16384x16384", "full:smem", "codegen_fused"): (2177.1e6, "8317c02f6926f6f7"),
+    ("normalization2d_fp32_16384x16384", "full:smem", "codegen_fused"): (2103.2e6, "2a4a0934d71f84e5"),
+    ("inplace_chain2d_fp32_16384x16384", "full:smem", "codegen_fused"): (2177.3e6, "2a4a0934d71f84e5"),
 }
 
 
@@ -132,22 +132,22 @@ def src_hash(files):
 # one ncu capture (profiles/godunov_fp64_1024_pipe_ncu.md), with the hash of
 # the kernel sources at capture time: a changed source voids it.
 FP64_SLOTS = {
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg", "gsweep_x"): (295.65e6, "a4a67d465b85d1b9"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg", "gsweep_y"): (333.76e6, "a4a67d465b85d1b9"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:smem", "gsweep_x"): (330.80e6, "a4a67d465b85d1b9"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:smem", "gsweep_y"): (400.02e6, "a4a67d465b85d1b9"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:hbm", "gsweep_x"): (328.70e6, "a4a67d465b85d1b9"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:hbm", "gsweep_y"): (400.02e6, "a4a67d465b85d1b9"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:reg", "gsweep_x"): (1352.09e6, "a4a67d465b85d1b9"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:reg", "gsweep_y"): (1369.59e6, "a4a67d465b85d1b9"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:smem", "gsweep_x"): (1401.77e6, "a4a67d465b85d1b9"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:smem", "gsweep_y"): (1403.21e6, "a4a67d465b85d1b9"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:hbm", "gsweep_x"): (1401.85e6, "a4a67d465b85d1b9"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:hbm", "gsweep_y"): (1403.21e6, "a4a67d465b85d1b9"),
-    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_x"): (6532.57e6, "a4a67d465b85d1b9"),
-    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_y"): (6360.10e6, "a4a67d465b85d1b9"),
-    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_x"): (6598.83e6, "a4a67d465b85d1b9"),
-    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_y"): (6546.65e6, "a4a67d465b85d1b9"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg", "gsweep_x"): (285.68e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg", "gsweep_y"): (321.63e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:smem", "gsweep_x"): (320.12e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:smem", "gsweep_y"): (313.70e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:hbm", "gsweep_x"): (318.02e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:hbm", "gsweep_y"): (313.70e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:reg", "gsweep_x"): (1046.67e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:reg", "gsweep_y"): (1031.83e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:smem", "gsweep_x"): (1092.42e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:smem", "gsweep_y"): (1031.83e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:hbm", "gsweep_x"): (1092.42e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:hbm", "gsweep_y"): (1031.83e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_x"): (5104.69e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_y"): (4799.88e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_x"): (5170.14e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_y"): (4821.20e6, "d44c8d6f2115ee9b"),
 }
 
 
