@@ -248,7 +248,17 @@ __device__ __forceinline__ Face4<T> riemann(const Face4<T>& L, const Face4<T>& R
         al = ashk * pr * ipp;
         ar = ashk * pl * ipp;
     }
-    double ps = div_nr(cr * pl + cl * pr - cl * cr * (ur - ul), cl + cr);
+    // initial guess: the acoustic (linearised) star pressure.  The FP32-bulk
+    // form takes it in FP32 from its FP32 states: the guess only sets where
+    // the FP64 iteration starts, not the root it converges to
+    double ps;
+    if constexpr (sizeof(T) == 4) {
+        const float xlf = g * L.p * L.r, xrf = g * R.p * R.r;
+        const float clf = xlf * rsqrtf(xlf), crf = xrf * rsqrtf(xrf);
+        ps = widen(fmaxf((crf * L.p + clf * R.p - clf * crf * (R.u - L.u)) / (clf + crf), (float)G_P_FLOOR));
+    } else {
+        ps = div_nr(cr * pl + cl * pr - cl * cr * (ur - ul), cl + cr);
+    }
     ps = dfloor(ps, G_P_FLOOR);
     bool conv = false;
     for (int it = 0; it < nmax; ++it) {
