@@ -93,22 +93,22 @@ COSMO_NZ = 64            # planes of the COSMO workloads
 # ncu capture of the bench's profiling case (summaries under profiles/), with
 # the hash of the kernel sources at capture time: a changed source voids it.
 TRAFFIC = {
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg", "gsweep_y"): (33.64e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg", "gsweep_x"): (33.71e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:smem", "gsweep_y"): (33.63e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:smem", "gsweep_x"): (33.77e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:hbm", "gsweep_y"): (34.59e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:hbm", "gsweep_x"): (95.28e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:reg", "gsweep_x"): (494.02e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:reg", "gsweep_y"): (495.85e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:smem", "gsweep_x"): (489.64e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:smem", "gsweep_y"): (495.88e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:hbm", "gsweep_x"): (555.51e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:hbm", "gsweep_y"): (499.63e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_x"): (2382.95e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_y"): (2446.19e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_x"): (5561.84e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_y"): (2408.09e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg", "gsweep_y"): (33.62e6, "5eae599fa7469c3a"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg", "gsweep_x"): (33.67e6, "5eae599fa7469c3a"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:smem", "gsweep_y"): (33.61e6, "5eae599fa7469c3a"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:smem", "gsweep_x"): (33.79e6, "5eae599fa7469c3a"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:hbm", "gsweep_y"): (34.38e6, "5eae599fa7469c3a"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:hbm", "gsweep_x"): (95.01e6, "5eae599fa7469c3a"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:reg", "gsweep_x"): (494.60e6, "5eae599fa7469c3a"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:reg", "gsweep_y"): (495.71e6, "5eae599fa7469c3a"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:smem", "gsweep_x"): (489.89e6, "5eae599fa7469c3a"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:smem", "gsweep_y"): (495.24e6, "5eae599fa7469c3a"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:hbm", "gsweep_x"): (555.34e6, "5eae599fa7469c3a"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:hbm", "gsweep_y"): (499.66e6, "5eae599fa7469c3a"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_x"): (2382.88e6, "5eae599fa7469c3a"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_y"): (2443.73e6, "5eae599fa7469c3a"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_x"): (5528.04e6, "5eae599fa7469c3a"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_y"): (2408.79e6, "5eae599fa7469c3a"),
     ("chain2d_fp32_16384x16384", "full:reg", "chain2d_fused"): (2128.8e6, "ea75d8cb3b84e2e3"),
     ("chain3d_fp32_512x512x512", "full:reg", "chain3d_fused_tma"): (1058.8e6, "ea75d8cb3b84e2e3"),
     ("cosmo_fp32_1024x1024x64", "full:reg", "cosmo_fused"): (527.6e6, "ea75d8cb3b84e2e3"),
@@ -132,22 +132,22 @@ def src_hash(files):
 # one ncu capture (profiles/godunov_fp64_1024_pipe_ncu.md), with the hash of
 # the kernel sources at capture time: a changed source voids it.
 FP64_SLOTS = {
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg", "gsweep_x"): (285.68e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg", "gsweep_y"): (321.63e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:smem", "gsweep_x"): (320.12e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:smem", "gsweep_y"): (313.70e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:hbm", "gsweep_x"): (318.02e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_fp64_1024x1024_10steps", "sweep:hbm", "gsweep_y"): (313.70e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:reg", "gsweep_x"): (1046.67e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:reg", "gsweep_y"): (1031.83e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:smem", "gsweep_x"): (1092.42e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:smem", "gsweep_y"): (1031.83e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:hbm", "gsweep_x"): (1092.42e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:hbm", "gsweep_y"): (1031.83e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_x"): (5104.69e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_y"): (4799.88e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_x"): (5170.14e6, "d44c8d6f2115ee9b"),
-    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_y"): (4821.20e6, "d44c8d6f2115ee9b"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg", "gsweep_x"): (285.68e6, "5eae599fa7469c3a"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:reg", "gsweep_y"): (321.63e6, "5eae599fa7469c3a"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:smem", "gsweep_x"): (320.12e6, "5eae599fa7469c3a"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:smem", "gsweep_y"): (313.70e6, "5eae599fa7469c3a"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:hbm", "gsweep_x"): (318.02e6, "5eae599fa7469c3a"),
+    ("godunov2d_fp64_1024x1024_10steps", "sweep:hbm", "gsweep_y"): (313.70e6, "5eae599fa7469c3a"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:reg", "gsweep_x"): (828.57e6, "5eae599fa7469c3a"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:reg", "gsweep_y"): (812.28e6, "5eae599fa7469c3a"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:smem", "gsweep_x"): (872.61e6, "5eae599fa7469c3a"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:smem", "gsweep_y"): (812.28e6, "5eae599fa7469c3a"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:hbm", "gsweep_x"): (872.61e6, "5eae599fa7469c3a"),
+    ("godunov2d_fp32bulk_4096x4096_10steps", "sweep:hbm", "gsweep_y"): (812.28e6, "5eae599fa7469c3a"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_x"): (4126.67e6, "5eae599fa7469c3a"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:reg", "gsweep_y"): (3782.16e6, "5eae599fa7469c3a"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_x"): (4191.57e6, "5eae599fa7469c3a"),
+    ("godunov2d_batch64_fp32bulk_100steps_graph", "sweep:hbm", "gsweep_y"): (3797.75e6, "5eae599fa7469c3a"),
 }
 
 
